@@ -1,0 +1,143 @@
+"""Pins of the oracle's method coefficients by the order conditions.
+
+Tsit5 (paper Sec. 2.1, Tsitouras 2011): all 17 rooted trees up to order 5 for b,
+all 8 up to order 4 for bhat. Rodas5P (paper Sec. 3.2, Steinebach 2023): the
+Rosenbrock order conditions (Hairer & Wanner II, Sec. IV.7) after converting the
+transformed (a, C, m) form back to (alpha, Gamma, b). The elementary weights
+are computed here from the trees, independently of the oracle's step code.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+TOL = 5e-14  # the published tables carry ~16 significant digits
+
+
+def _trees(n, memo={}):
+    if n in memo:
+        return memo[n]
+    if n == 1:
+        memo[1] = [()]
+        return memo[1]
+    out = set()
+
+    def rec(rem, acc):
+        if rem == 0:
+            out.add(tuple(sorted(acc)))
+            return
+        for m in range(1, rem + 1):
+            for t in _trees(m):
+                rec(rem - m, acc + [(m, t)])
+
+    rec(n - 1, [])
+    memo[n] = sorted(out)
+    return memo[n]
+
+
+def _order(t):
+    return 1 + sum(m for m, _ in t)
+
+
+def _density(t):
+    return _order(t) * np.prod([_density(c) for _, c in t]) if t else 1.0
+
+
+def _phi(t, alpha, B):
+    """Elementary weight of tree t. Single-child nodes couple through B = alpha + Gamma
+    (the Rosenbrock Jacobian term), multi-child nodes through alpha alone."""
+    s = alpha.shape[0]
+    if not t:
+        return np.ones(s)
+    if len(t) == 1:
+        return B @ _phi(t[0][1], alpha, B)
+    out = np.ones(s)
+    for _, c in t:
+        out = out * (alpha @ _phi(c, alpha, B))
+    return out
+
+
+def residuals(alpha, Gam, b, p):
+    B = alpha + Gam
+    return [(t, float(b @ _phi(t, alpha, B) - 1.0 / _density(t))) for n in range(1, p + 1) for t in _trees(n)]
+
+
+def rodas_standard(tab):
+    """(a, C, m, gamma) transformed form -> (alpha, Gamma, b):
+    Gamma^{-1} = diag(1/gamma) - C, alpha = a Gamma, b = m Gamma."""
+    g = tab["gamma"]
+    Ginv = np.diag(np.full(8, 1.0 / g)) - tab["C"]
+    G = np.linalg.inv(Ginv)
+    return tab["a"] @ G, G, tab["m"] @ G
+
+
+def test_tree_counts():
+    # 1, 1, 2, 4, 9 rooted trees of orders 1..5 (Butcher).
+    assert [len(_trees(n)) for n in range(1, 6)] == [1, 1, 2, 4, 9]
+
+
+def test_tsit5_order_conditions():
+    tab = oracle.tableau(oracle.METHOD_TSIT5)
+    A, b, bh, c = tab["A"], tab["b"], tab["bhat"], tab["c"]
+    Z = np.zeros_like(A)
+    r5 = residuals(A, Z, b, 5)
+    r4 = residuals(A, Z, bh, 4)
+    assert len(r5) == 17 and len(r4) == 8
+    assert max(abs(r) for _, r in r5) < TOL
+    assert max(abs(r) for _, r in r4) < TOL
+    # bhat is a genuinely lower-order solution: some order-5 condition fails for it
+    assert max(abs(r) for _, r in residuals(A, Z, bh, 5)) > 1e-4
+    np.testing.assert_allclose(A.sum(1), c, atol=1e-15)
+    # FSAL: the last stage is evaluated at y_new (row 7 of A equals b, b_7 = 0)
+    np.testing.assert_array_equal(A[6], b)
+    assert b[6] == 0.0
+    assert np.allclose(np.tril(A, -1), A)  # explicit
+
+
+def test_rodas5p_order_conditions():
+    tab = oracle.tableau(oracle.METHOD_RODAS5P)
+    alpha, G, b = rodas_standard(tab)
+    mh = tab["m"].copy()
+    mh[7] = 0.0  # embedded solution: y_new - U_8
+    bh = mh @ G
+    r5 = residuals(alpha, G, b, 5)
+    r4 = residuals(alpha, G, bh, 4)
+    assert max(abs(r) for _, r in r5) < TOL
+    assert max(abs(r) for _, r in r4) < TOL
+    assert max(abs(r) for _, r in residuals(alpha, G, bh, 5)) > 1e-6
+    assert np.allclose(np.diag(G), tab["gamma"])
+
+
+def _rosenbrock_R(alpha, G, b, z):
+    # Scalar stability function: R(z) = 1 + z b^T (I - z (alpha + Gamma))^{-1} 1
+    B = alpha + G
+    s = B.shape[0]
+    return 1.0 + z * b @ np.linalg.solve(np.eye(s) - z * B, np.ones(s))
+
+
+def test_rodas5p_stiffly_accurate():
+    tab = oracle.tableau(oracle.METHOD_RODAS5P)
+    alpha, G, b = rodas_standard(tab)
+    mh = tab["m"].copy()
+    mh[7] = 0.0
+    bh = mh @ G
+    for z in (-1e8, -1e12):
+        assert abs(_rosenbrock_R(alpha, G, b, z)) < 1e-6
+        assert abs(_rosenbrock_R(alpha, G, bh, z)) < 1e-6
+    # A-stability spot check on the negative real axis and the imaginary axis
+    for z in np.concatenate([-np.logspace(-3, 6, 60), 1j * np.logspace(-3, 6, 60)]):
+        assert abs(_rosenbrock_R(alpha, G, b, z)) <= 1.0 + 1e-12
+
+
+def test_planted_coefficient_error_is_detected():
+    # A perturbation in the 9th digit of one coefficient must break a condition.
+    tab = oracle.tableau(oracle.METHOD_TSIT5)
+    A = tab["A"].copy()
+    A[4, 2] *= 1 + 1e-9
+    bad = residuals(A, np.zeros_like(A), A[6], 5)
+    assert max(abs(r) for _, r in bad) > 10 * TOL
+    rt = oracle.tableau(oracle.METHOD_RODAS5P)
+    rt["C"] = rt["C"].copy()
+    rt["C"][5, 2] *= 1 + 1e-9
+    alpha, G, b = rodas_standard(rt)
+    assert max(abs(r) for _, r in residuals(alpha, G, b, 5)) > 10 * TOL
