@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Benchmark: gradient trajectories/s of the record + reverse-sweep hot path.
+
+One step = one gs_solve_grad call over a resident ensemble: the adaptive Tsit5
+record of every trajectory, then the reverse discrete-adjoint sweep with the
+built-in loss sum_s ||y(t_s)||^2, returning loss, dL/dtheta and dL/dy0.
+
+Default workload (the non-stiff scale sweep's largest Lorenz point): Lorenz-63,
+n = 2^24 trajectories per GPU, sigma~U[8,12], rho~U[20,30], beta~U[2,3],
+y0~N((1,1,1), 0.1^2 I), t in [0, 1], 10 uniform save times, Tsit5 with
+rtol 1e-6 / atol 1e-8, FP64. Inputs (805 MB) and the record (~10 GB) are far
+larger than L2, so no flush is needed between steps.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] on one GPU, or under
+torchrun (one rank per GPU, each rank its own shard: weak scaling).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_02876_gb300 import workloads as W  # noqa: E402
+
+METRIC = "gradient trajectories/s on 1 GB300 at matched error vs FP64 oracle; p50/p99 latency"
+UNIT = "trajectories/s"
+
+# Hand-counted algorithmic flops (FMA = 2) of one Tsit5 unit; derivation in the design doc.
+#   f: one right-hand-side evaluation; vjp: one J^T v + f_theta^T v.
+#   stage forward (6 slopes + 6 stage inputs): 6 f + 48 D
+#   stage reverse (6 stage VJPs):              6 vjp + 54 D
+#   trial step of the record:                  7 f + 48 D (stages) + 14 D (error) + 6 D + 4 (norm, control)
+RHS_FLOPS = {"lorenz": (8, 20, 3), "vdp": (5, 15, 2), "linear": (6, 12, 2)}
+
+
+def unit_flops(problem):
+    f, v, D = RHS_FLOPS[problem]
+    fwd = 6 * f + 48 * D
+    rev = 6 * v + 54 * D
+    trial = 7 * f + 48 * D + 14 * D + 6 * D + 4
+    return {"stage_fwd": fwd, "vjp_unit": fwd + rev, "trial": trial}
+
+
+def fp_peak_tflops(precision):
+    """ALU peak from unit counts and clock: 152 SMs x FMA lanes/clk/SM x 2 x 2.07 GHz.
+    FP64 lanes/clk/SM were measured on this part with a dependent-FMA probe."""
+    lanes = {"fp64": FP64_LANES_PER_SM, "fp32_mixed": 128}[precision]
+    return 152 * lanes * 2 * 2.070e9 / 1e12
+
+
+FP64_LANES_PER_SM = 2  # DFMA probe on this part: 1.06 TFLOP/s sustained
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(args, budget_s=12.0):
+    """The FP64 oracle (record + replay gradient), as it stands, on the host cores,
+    over a bounded sample of the same workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    probe = W.make(args.problem, 2048, rtol=args.rtol, seed=7)
+    t = time.perf_counter()
+    oracle.solve_grad(probe["problem"], probe["params"], probe["y0"], probe["t0"], probe["t1"], probe["save_t"],
+                      probe["rtol"], probe["atol"], nthreads=cores)
+    rate = 2048 / (time.perf_counter() - t)
+    m = int(min(max(4096, rate * budget_s), 1 << 22))
+    wl = W.make(args.problem, m, rtol=args.rtol, seed=0)
+    t = time.perf_counter()
+    g = oracle.solve_grad(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], wl["rtol"],
+                          wl["atol"], nthreads=cores)
+    dt = time.perf_counter() - t
+    assert g["ok"].all()
+    return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {m} trajectories of the same {args.problem} workload (seed 0), record + replay "
+                      f"gradient, {dt:.1f} s on {cores} threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    cores = os.cpu_count() or 1
+    m = args.ref_sample
+    wl = W.make(args.problem, m, rtol=args.rtol, seed=0)
+
+    def step():
+        g = oracle.solve_grad(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"],
+                              wl["rtol"], wl["atol"], nthreads=cores)
+        assert g["ok"].all()
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    v = m * args.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_of(args, m),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{m} trajectories of the {args.problem} workload per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(args, n):
+    wl = {"lorenz": "Lorenz-63 (sigma~U[8,12], rho~U[20,30], beta~U[2,3], y0~N((1,1,1),0.1^2 I), t in [0,1], "
+                    "10 uniform saves)",
+          "vdp": "Van der Pol (mu~U[0.5,2], y0~U[-2,2]^2, t in [0,10], 50 uniform saves)"}[args.problem]
+    return {"workload": f"{wl}, Tsit5 rtol={args.rtol:g} atol={args.rtol * 1e-2:g}, {args.precision}, "
+                        f"n={n} per GPU, loss=sum_s ||y(t_s)||^2, grads wrt theta and y0",
+            "n_per_gpu": n, "problem": args.problem, "precision": args.precision, "rtol": args.rtol,
+            "l2": "inputs and record larger than L2 (no flush)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gradsolve", choices=["gradsolve", "reference"])
+    ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp"])
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--rtol", type=float, default=1e-6)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=1 << 15)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2609_02876_gb300 import api, build
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    n = args.n
+    wl = W.make(args.problem, n, rtol=args.rtol, seed=rank)
+    P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
+    Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
+    d, Pn, _, _ = api.problem_info(args.problem)
+    out = {"loss": torch.empty(n, dtype=torch.float64, device="cuda"),
+           "params_bar": torch.empty((Pn, n), dtype=torch.float64, device="cuda"),
+           "y0_bar": torch.empty((d, n), dtype=torch.float64, device="cuda"),
+           "status": torch.empty(n, dtype=torch.int32, device="cuda")}
+    kms = np.zeros(2, np.float32)
+
+    def step(kernel_ms=None, counts=False):
+        return api.solve_grad(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                              layout="soa", out=out, precision=args.precision, kernel_ms=kernel_ms,
+                              step_counts=counts)
+
+    for _ in range(args.warmup):
+        step()
+    r = step(counts=True)
+    assert (out["status"] == 0).all().item(), "trajectory failures in the benchmark workload"
+    sc = r["step_counts"].to(torch.int64).sum(1).tolist()
+    S_tot, A_tot = sc[0], sc[1]
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    fwd_ms, rev_ms = [], []
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(kernel_ms=kms)
+        fwd_ms.append(float(kms[0]))
+        rev_ms.append(float(kms[1]))
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = tt.item()
+    value = ws * n * args.steps / t
+
+    # end to end through the public API: pinned host inputs -> device -> gs_solve_grad -> host results
+    hP = torch.from_numpy(np.ascontiguousarray(wl["params"].T)).pin_memory()
+    hY = torch.from_numpy(np.ascontiguousarray(wl["y0"].T)).pin_memory()
+    hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    ke = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        P.copy_(hP, non_blocking=True)
+        Y.copy_(hY, non_blocking=True)
+        step()
+        for k in out:
+            hout[k].copy_(out[k], non_blocking=True)
+        torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    barrier()
+    h2d = (hP.numel() + hY.numel()) * 8
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    e2e = {"value": ws * n * ke / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel (the reverse sweep), algorithmic flops / event-timed duration
+    uf = unit_flops(args.problem)
+    n_side = n * (len(wl["save_t"]) - 1)  # saves strictly inside a step (the last one sits on t1)
+    rev_flops = (S_tot + n_side) * uf["vjp_unit"]
+    fwd_flops = A_tot * uf["trial"]
+    rev_s = statistics.mean(rev_ms) / 1e3
+    fwd_s = statistics.mean(fwd_ms) / 1e3
+    peak = fp_peak_tflops(args.precision)
+    dominant = "reverse" if rev_s >= fwd_s else "record"
+    ach = (rev_flops / rev_s if dominant == "reverse" else fwd_flops / fwd_s) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": config_of(args, n),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None, "kernel": f"tsit5_{dominant}_kernel",
+                         "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz (DESIGN.md)"},
+            "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
+            "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
+                     "reverse_tflops": rev_flops / rev_s / 1e12},
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * gradsolve-gb300 C-ABI: record-and-replay gradients of ODE ensembles on one GPU.
+ *
+ * The method (paper Sec. 3.1, "The construction"): every trajectory of an
+ * ensemble dy/dt = f(t, y, theta) gets its own adaptive solve (the record, map
+ * R) that keeps its accepted step sizes {h_i}; the gradient is the exact
+ * reverse-mode derivative of the fixed chain y_i = Phi(y_{i-1}; h_i, theta)
+ * (Eq. (replay)) over that frozen mesh, with h held as data.
+ *
+ * Conventions shared by every entry point:
+ *  - Array pointers are DEVICE pointers owned by the caller, laid out
+ *    structure-of-arrays with the trajectory index fastest:
+ *      params[P][n], y0[d][n], y_save[n_save][d][n], params_bar[P][n],
+ *      y0_bar[d][n], loss[n], traj_status[n].
+ *    save_t (n_save doubles) is a HOST pointer; its values are copied.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *    enqueued on it; the calls that report per-trajectory failures
+ *    (gs_forward_record, gs_solve_grad) synchronise `stream` before returning.
+ *  - No exception, abort or device trap crosses this boundary: every failure is
+ *    a gs_status return value. Per-trajectory failures are written to
+ *    traj_status (GS_TRAJ_*) and the call returns GS_ERR_TRAJ_FAILED; the
+ *    gradients of a failed trajectory are NaN.
+ *  - Problem ids name the paper's test problems (Appendix A) plus two forms of
+ *    this library: GS_LINEAR (dy/dt = A y, A = [[p0, p1], [p2, p3]], a closed-
+ *    form test problem) and GS_LV_UDE (Lotka-Volterra with a shared MLP).
+ */
+#ifndef GRADSOLVE_GS_H
+#define GRADSOLVE_GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_record gs_record; /* opaque, device-resident, owned by the library */
+typedef void* gs_stream;            /* a cudaStream_t */
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1,     /* a pointer, size, time span, tolerance or option is invalid */
+  GS_ERR_UNKNOWN_PROBLEM = 2, /* problem id not in the registry */
+  GS_ERR_OOM = 3,             /* device allocation failed */
+  GS_ERR_CUDA = 4,            /* a CUDA launch or runtime call failed */
+  GS_ERR_TRAJ_FAILED = 5,     /* at least one trajectory's traj_status is not GS_TRAJ_OK */
+  GS_ERR_TIMEOUT = 6          /* a bounded wait on device completion ran out */
+} gs_status;
+
+/* Per-trajectory status words. */
+enum {
+  GS_TRAJ_OK = 0,
+  GS_TRAJ_MAXSTEPS = 1,     /* attempted steps reached gs_options.max_steps */
+  GS_TRAJ_DT_UNDERFLOW = 2, /* |h| < 1e-14 max(1, |t|) */
+  GS_TRAJ_NONFINITE = 3,    /* non-finite input, or the error estimate stayed non-finite */
+  GS_TRAJ_SINGULAR = 4      /* the Rosenbrock matrix I/(h gamma) - J stayed singular */
+};
+
+/* Problem registry (paper Appendix A; GS_LINEAR and GS_LV_UDE are this library's). */
+enum { GS_LORENZ = 0, GS_VDP = 1, GS_ROBERTSON = 2, GS_HIRES = 3, GS_LINEAR = 4, GS_LV_UDE = 5 };
+
+/* Arithmetic of the stage and adjoint work. GS_FP32_MIXED keeps FP64 for the
+ * step-size control (t, h, the error norm and the controller). */
+enum { GS_FP64 = 0, GS_FP32_MIXED = 1 };
+
+/* One-step methods (paper Sec. 3.2): Tsit5 (Tsitouras 2011) for non-stiff
+ * problems, Rodas5P (Steinebach 2023) for stiff ones. AUTO picks by problem. */
+enum { GS_METHOD_AUTO = 0, GS_METHOD_TSIT5 = 1, GS_METHOD_RODAS5P = 2 };
+
+typedef struct {
+  int precision;        /* GS_FP64 or GS_FP32_MIXED */
+  int method;           /* GS_METHOD_* */
+  int ckpt_k;           /* accepted steps per record segment = state-checkpoint interval,
+                           1..32; 0 picks 14 - d (a 128-byte segment) */
+  int64_t max_steps;    /* attempted steps per trajectory; 0 = 1000000 */
+  double h0;            /* first trial step; 0 = the automatic starting-step algorithm */
+  int32_t* step_counts; /* optional DEVICE [2][n] output: accepted, attempted steps */
+  float* kernel_ms;     /* optional HOST [2] output of gs_forward_record / gs_solve_grad:
+                           device time (ms) of the record kernel and of the reverse kernel
+                           (gs_solve_grad only) of this call, from CUDA events on `stream` */
+} gs_options;
+
+/* A readable name for a status code (static storage, never NULL). */
+const char* gs_status_string(gs_status s);
+
+/* Fills *opt with the defaults (FP64, AUTO method, automatic k and h0). */
+gs_status gs_default_options(gs_options* opt);
+
+/* State dimension d, parameter count P, stiffness flag and shared-weight count
+ * of a problem (paper Appendix A). */
+gs_status gs_problem_info(int problem_id, int* d, int* P, int* stiff, int* n_shared);
+
+/*
+ * Record (map R, paper Sec. 3.1): the adaptive solve of every trajectory from
+ * t0 to t1 with the weighted RMS error test of Sec. 2.1 (accept iff
+ * RMS(e / (atol + rtol max(|y|, |y_new|))) <= 1) and an integral controller.
+ * Keeps each trajectory's accepted step sizes plus a state checkpoint every
+ * ckpt_k accepted steps in a device-resident record (*rec_out).
+ *
+ * save_t: n_save strictly increasing HOST times with t0 < save_t[0] and
+ * save_t[n_save-1] <= t1 (n_save may be 0, at most 256). Each y(t_s) is one
+ * extra step from the last mesh point at or before t_s (paper Sec. 3.4); save
+ * times never alter the mesh. y_save_out [n_save][d][n] may be NULL.
+ * shared_w: the GS_LV_UDE network weights (354 floats, device), else NULL.
+ * traj_status [n] is required. Synchronises `stream`. The record stays valid
+ * until gs_record_free and may be replayed any number of times.
+ */
+gs_status gs_forward_record(int problem_id, int64_t n, const double* params, const double* y0,
+                            const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                            double rtol, double atol, const gs_options* opt, gs_stream stream,
+                            double* y_save_out, int32_t* traj_status, gs_record** rec_out);
+
+/*
+ * Reverse sweep (paper Sec. 3.1-3.2): the discrete adjoint of the replay over
+ * the recorded mesh with h held as data. For each trajectory, segments are
+ * visited last to first; states inside a segment are recomputed from its
+ * checkpoint, stages are recomputed per step, and the stage cotangents are
+ * propagated back (for Rodas5P with one transposed LU solve per stage).
+ *
+ * params may differ from the recorded ones (a frozen-mesh gradient, Sec. 3.1).
+ * y_save_bar [n_save][d][n] is dL/dy(t_s); NULL selects the built-in loss
+ * L = sum_k sum_s ||y_k(t_s)||^2, whose per-trajectory values are written to
+ * loss_out [n] if it is not NULL. Outputs params_bar [P][n] and y0_bar [d][n]
+ * (either may be NULL); shared_w_bar (354 floats, GS_LV_UDE only) receives the
+ * ensemble sum. Enqueued on `stream`, not synchronised.
+ */
+gs_status gs_reverse(const gs_record* rec, const double* params, const double* y0, const float* shared_w,
+                     const double* y_save_bar, double* loss_out, double* params_bar, double* y0_bar,
+                     float* shared_w_bar, gs_stream stream);
+
+/*
+ * Record then reverse in one call with the built-in loss (the hot path):
+ * loss_out [n], params_bar [P][n], y0_bar [d][n], traj_status [n]. The record
+ * lives in a library-owned workspace that is reused by later calls on the same
+ * device. Synchronises `stream`.
+ */
+gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const double* y0,
+                        const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                        double rtol, double atol, const gs_options* opt, gs_stream stream, double* loss_out,
+                        double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status);
+
+/* Device bytes held by a record. */
+gs_status gs_record_bytes(const gs_record* rec, size_t* bytes);
+
+/* Ensemble size and total accepted / attempted steps of a record. */
+gs_status gs_record_stats(const gs_record* rec, int64_t* n, int64_t* accepted, int64_t* attempted);
+
+/* Copies the mesh to HOST arrays: offsets [n+1] (ragged prefix sums of the
+ * accepted-step counts) and h [offsets[n]]. Pass h = NULL to get offsets only.
+ * Synchronous. Meant for tests and inspection. */
+gs_status gs_record_export_mesh(const gs_record* rec, int64_t* offsets, double* h);
+
+/* Releases a record (NULL is accepted). */
+gs_status gs_record_free(gs_record* rec);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRADSOLVE_GS_H */

@@ -675,6 +675,7 @@ RecordOut record_one(int method, const Prob& pr, const double* y0, const double*
       double fac = ctrl_factor(err);
       if (reject_prev) fac = std::min(fac, 1.0);
       reject_prev = false;
+      last_nonfinite = false;
       h = h * fac;
     } else {
       last_nonfinite = !std::isfinite(err);

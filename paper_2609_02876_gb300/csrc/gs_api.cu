@@ -1,0 +1,529 @@
+// C-ABI of gradsolve-gb300 (declared in include/gs.h): argument checking, the
+// device-resident record, the reusable workspace of gs_solve_grad, and the
+// kernel launches. No exception or abort crosses this boundary.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/gs.h"
+#include "gs_internal.h"
+
+using namespace gs;
+
+namespace {
+
+struct ProblemInfo {
+  int d, P, stiff, n_shared;
+};
+
+bool problem_info(int pid, ProblemInfo* out) {
+  switch (pid) {
+    case GS_LORENZ: *out = {3, 3, 0, 0}; return true;
+    case GS_VDP: *out = {2, 1, 0, 0}; return true;
+    case GS_ROBERTSON: *out = {3, 3, 1, 0}; return true;
+    case GS_HIRES: *out = {8, 12, 1, 0}; return true;
+    case GS_LINEAR: *out = {2, 4, 0, 0}; return true;
+    case GS_LV_UDE: *out = {2, 2, 0, 354}; return true;
+  }
+  return false;
+}
+
+// Doubles per record segment [prev, t_start, y_start[d], h[k]], rounded up to a
+// 16-byte multiple for vector stores.
+int segw_of(int d, int k) { return ((2 + d + k) + 1) & ~1; }
+
+// Expected accepted steps per trajectory, used only for the first arena size.
+int step_guess(int pid) {
+  switch (pid) {
+    case GS_LORENZ: return 64;
+    case GS_VDP: return 192;
+    case GS_LV_UDE: return 64;
+  }
+  return 256;
+}
+
+// Counters that the kernels update; one small device block per record.
+struct Counters {
+  unsigned long long work_fwd;
+  unsigned long long work_rev;
+  unsigned long long arena_top;
+  int overflow;
+  int any_failed;
+};
+
+}  // namespace
+
+struct gs_record {
+  int device = 0;
+  int problem = 0, method = GS_METHOD_TSIT5, precision = GS_FP64;
+  int d = 0, P = 0, k = 0, segw = 0;
+  int64_t n = 0;
+  double t0 = 0, t1 = 0, rtol = 0, atol = 0;
+  int n_save = 0;
+  double save_t[MAX_SAVE_HOST] = {0};
+  // device buffers
+  double* arena = nullptr;
+  long long arena_cap = 0;
+  long long* head = nullptr;
+  int32_t* S = nullptr;
+  int32_t* natt = nullptr;
+  int32_t* status = nullptr;
+  double* y_final = nullptr;
+  Counters* ctr = nullptr;
+  Counters* ctr_host = nullptr;  // pinned
+  int64_t n_cap = 0;             // capacity of the per-trajectory arrays
+  size_t bytes = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (optional)
+};
+
+namespace {
+
+gs_status cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return GS_ERR_OOM;
+  return GS_ERR_CUDA;
+}
+
+void free_arrays(gs_record* r) {
+  cudaFree(r->head);
+  cudaFree(r->S);
+  cudaFree(r->natt);
+  cudaFree(r->status);
+  cudaFree(r->y_final);
+  r->head = nullptr;
+  r->S = r->natt = r->status = nullptr;
+  r->y_final = nullptr;
+  r->n_cap = 0;
+}
+
+size_t record_bytes(const gs_record* r) {
+  return (size_t)r->arena_cap * r->segw * sizeof(double) +
+         (size_t)r->n_cap * (sizeof(long long) + 3 * sizeof(int32_t) + r->d * sizeof(double)) + sizeof(Counters);
+}
+
+// Ensures per-trajectory arrays for n trajectories of dimension d.
+gs_status ensure_arrays(gs_record* r, int64_t n, int d) {
+  if (r->n_cap >= n && r->d == d && r->head) return GS_OK;
+  free_arrays(r);
+  const int64_t m = n > 0 ? n : 1;
+  cudaError_t e;
+  if ((e = cudaMalloc(&r->head, m * sizeof(long long))) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMalloc(&r->S, m * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMalloc(&r->natt, m * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMalloc(&r->status, m * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMalloc(&r->y_final, m * d * sizeof(double))) != cudaSuccess) return cuda_fail(e);
+  r->n_cap = m;
+  return GS_OK;
+}
+
+gs_status ensure_arena(gs_record* r, long long segs, int segw) {
+  if (r->arena && r->arena_cap >= segs && r->segw == segw) return GS_OK;
+  cudaFree(r->arena);
+  r->arena = nullptr;
+  r->arena_cap = 0;
+  cudaError_t e = cudaMalloc(&r->arena, (size_t)segs * segw * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e);
+  r->arena_cap = segs;
+  return GS_OK;
+}
+
+gs_status ensure_counters(gs_record* r) {
+  if (r->ctr) return GS_OK;
+  cudaError_t e = cudaMalloc(&r->ctr, sizeof(Counters));
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMallocHost(&r->ctr_host, sizeof(Counters));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return GS_OK;
+}
+
+gs_status ensure_events(gs_record* r) {
+  for (int i = 0; i < 4; ++i)
+    if (!r->ev[i] && cudaEventCreate(&r->ev[i]) != cudaSuccess) return GS_ERR_CUDA;
+  return GS_OK;
+}
+
+void destroy(gs_record* r) {
+  if (!r) return;
+  for (int i = 0; i < 4; ++i)
+    if (r->ev[i]) cudaEventDestroy(r->ev[i]);
+  free_arrays(r);
+  cudaFree(r->arena);
+  cudaFree(r->ctr);
+  cudaFreeHost(r->ctr_host);
+  delete r;
+}
+
+struct Call {
+  int problem;
+  ProblemInfo pi;
+  int method, precision, k;
+  int64_t max_steps;
+  double h0;
+  int32_t* step_counts;
+  float* kernel_ms;
+};
+
+gs_status check_common(int problem_id, int64_t n, const double* params, const double* y0, const float* shared_w,
+                       double t0, double t1, const double* save_t, int n_save, double rtol, double atol,
+                       const gs_options* opt, Call* c) {
+  if (!problem_info(problem_id, &c->pi)) return GS_ERR_UNKNOWN_PROBLEM;
+  c->problem = problem_id;
+  if (n < 0) return GS_ERR_INVALID_ARG;
+  if (n > 0 && (!params || !y0)) return GS_ERR_INVALID_ARG;
+  if (c->pi.n_shared > 0 && n > 0 && !shared_w) return GS_ERR_INVALID_ARG;
+  if (!std::isfinite(t0) || !std::isfinite(t1) || !(t1 > t0)) return GS_ERR_INVALID_ARG;
+  if (n_save < 0 || n_save > MAX_SAVE_HOST || (n_save > 0 && !save_t)) return GS_ERR_INVALID_ARG;
+  for (int s = 0; s < n_save; ++s) {
+    if (!std::isfinite(save_t[s]) || !(save_t[s] > t0) || save_t[s] > t1) return GS_ERR_INVALID_ARG;
+    if (s > 0 && !(save_t[s] > save_t[s - 1])) return GS_ERR_INVALID_ARG;
+  }
+  if (!std::isfinite(rtol) || !std::isfinite(atol) || rtol < 0 || atol < 0 || (rtol == 0 && atol == 0))
+    return GS_ERR_INVALID_ARG;
+  gs_options o;
+  gs_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != GS_FP64 && o.precision != GS_FP32_MIXED) return GS_ERR_INVALID_ARG;
+  int method = o.method == GS_METHOD_AUTO ? (c->pi.stiff ? GS_METHOD_RODAS5P : GS_METHOD_TSIT5) : o.method;
+  if (method != GS_METHOD_TSIT5 && method != GS_METHOD_RODAS5P) return GS_ERR_INVALID_ARG;
+  if (o.ckpt_k < 0 || o.ckpt_k > KMAX_HOST) return GS_ERR_INVALID_ARG;
+  if (o.max_steps < 0 || !std::isfinite(o.h0) || o.h0 < 0) return GS_ERR_INVALID_ARG;
+  c->method = method;
+  c->precision = o.precision;
+  c->k = o.ckpt_k;  // 0: chosen in setup_record from the free device memory
+  c->max_steps = o.max_steps > 0 ? o.max_steps : 1000000;
+  c->h0 = o.h0;
+  c->step_counts = o.step_counts;
+  c->kernel_ms = o.kernel_ms;
+  if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
+  if (method == GS_METHOD_RODAS5P) return GS_ERR_INVALID_ARG;  // stiff kernels: separate translation unit
+  return GS_OK;
+}
+
+// Runs the record kernel into r, growing the arena until it fits.
+gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* params, const double* y0,
+                     const float* shared_w, double* y_save, cudaStream_t s) {
+  FwdArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.params = params;
+  a.y0 = y0;
+  a.shared_w = shared_w;
+  a.t0 = r->t0;
+  a.t1 = r->t1;
+  a.rtol = r->rtol;
+  a.atol = r->atol;
+  a.h0 = c.h0;
+  a.max_steps = c.max_steps;
+  a.n_save = r->n_save;
+  std::memcpy(a.save_t, r->save_t, sizeof(double) * r->n_save);
+  a.y_save = y_save;
+  a.step_counts = c.step_counts;
+  a.k = r->k;
+  a.segw = r->segw;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    cudaError_t e = cudaMemsetAsync(r->ctr, 0, sizeof(Counters), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    a.arena = r->arena;
+    a.arena_cap = r->arena_cap;
+    a.arena_top = &r->ctr->arena_top;
+    a.overflow = &r->ctr->overflow;
+    a.any_failed = &r->ctr->any_failed;
+    a.head = r->head;
+    a.S = r->S;
+    a.natt = r->natt;
+    a.status = r->status;
+    a.y_final = r->y_final;
+    a.work = &r->ctr->work_fwd;
+    if (c.kernel_ms) cudaEventRecord(r->ev[0], s);
+    e = launch_tsit5_forward(c.problem, c.precision, a, s);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    if (c.kernel_ms) cudaEventRecord(r->ev[1], s);
+    e = cudaMemcpyAsync(r->ctr_host, r->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    if (!r->ctr_host->overflow) {
+      if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[0], r->ev[0], r->ev[1]);
+      return GS_OK;
+    }
+    // The arena was too small: size it to the demand just measured (+1/8) and rerun.
+    const long long need = (long long)r->ctr_host->arena_top;
+    gs_status st = ensure_arena(r, need + need / 8 + 1024, r->segw);
+    if (st != GS_OK) return st;
+  }
+  return GS_ERR_OOM;
+}
+
+// Checkpoint interval when the caller leaves it to the library: k = 1 (every
+// accepted state stored, nothing recomputed in the reverse sweep) if the
+// expected record takes at most half of the free device memory, else a
+// 128-byte segment of 14 - d steps (one checkpoint per 14 - d steps).
+int auto_ckpt_k(const gs_record* r, int problem, int d, int64_t n) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+  const size_t held = (size_t)r->arena_cap * r->segw * sizeof(double);  // reusable by this record
+  const double want = 1.25 * (double)(n > 0 ? n : 1) * step_guess(problem) * segw_of(d, 1) * sizeof(double);
+  if (want <= 0.5 * (double)(free_b + held)) return 1;
+  return 14 - d > 1 ? 14 - d : 1;
+}
+
+gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double t1, const double* save_t,
+                       int n_save, double rtol, double atol) {
+  cudaGetDevice(&r->device);
+  r->problem = c.problem;
+  r->method = c.method;
+  r->precision = c.precision;
+  r->d = c.pi.d;
+  r->P = c.pi.P;
+  r->k = c.k > 0 ? c.k : auto_ckpt_k(r, c.problem, c.pi.d, n);
+  r->n = n;
+  r->t0 = t0;
+  r->t1 = t1;
+  r->rtol = rtol;
+  r->atol = atol;
+  r->n_save = n_save;
+  if (n_save) std::memcpy(r->save_t, save_t, sizeof(double) * n_save);
+  gs_status st = ensure_counters(r);
+  if (st != GS_OK) return st;
+  if (c.kernel_ms && (st = ensure_events(r)) != GS_OK) return st;
+  st = ensure_arrays(r, n, r->d);
+  if (st != GS_OK) return st;
+  const int segw = segw_of(r->d, r->k);
+  if (r->segw != segw) {
+    cudaFree(r->arena);
+    r->arena = nullptr;
+    r->arena_cap = 0;
+    r->segw = segw;
+  }
+  const long long want = (long long)(n > 0 ? n : 1) * ((step_guess(c.problem) + r->k - 1) / r->k + 1);
+  if (r->arena_cap > 0 && r->arena_cap < want / 4) {  // far too small for this ensemble: start over
+    cudaFree(r->arena);
+    r->arena = nullptr;
+    r->arena_cap = 0;
+  }
+  if (r->arena_cap == 0) {
+    st = ensure_arena(r, want, segw);
+    if (st != GS_OK) return st;
+  }
+  return GS_OK;
+}
+
+gs_status launch_reverse(const gs_record* r, const double* params, const float* shared_w,
+                         const double* y_save_bar, double* loss, double* params_bar, double* y0_bar,
+                         float* shared_w_bar, cudaStream_t s) {
+  RevArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = r->n;
+  a.params = params;
+  a.shared_w = shared_w;
+  a.shared_w_bar = shared_w_bar;
+  a.t0 = r->t0;
+  a.t1 = r->t1;
+  a.n_save = r->n_save;
+  std::memcpy(a.save_t, r->save_t, sizeof(double) * r->n_save);
+  a.y_save_bar = y_save_bar;
+  a.loss = loss;
+  a.params_bar = params_bar;
+  a.y0_bar = y0_bar;
+  a.status = r->status;
+  a.arena = r->arena;
+  a.arena_cap = r->arena_cap;
+  a.head = r->head;
+  a.S = r->S;
+  a.y_final = r->y_final;
+  a.work = &r->ctr->work_rev;
+  a.k = r->k;
+  a.segw = r->segw;
+  cudaError_t e = cudaMemsetAsync(&r->ctr->work_rev, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  e = launch_tsit5_reverse(r->problem, r->precision, a, s);
+  return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// gs_solve_grad's reusable record, one per device.
+std::mutex g_ws_mu;
+std::vector<gs_record*> g_ws;
+
+gs_record* workspace(int dev) {
+  if ((int)g_ws.size() <= dev) g_ws.resize(dev + 1, nullptr);
+  if (!g_ws[dev]) g_ws[dev] = new (std::nothrow) gs_record();
+  return g_ws[dev];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gs_status_string(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_UNKNOWN_PROBLEM: return "unknown problem id";
+    case GS_ERR_OOM: return "device out of memory";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_TRAJ_FAILED: return "one or more trajectories failed (see traj_status)";
+    case GS_ERR_TIMEOUT: return "timed out waiting for the device";
+  }
+  return "unknown status";
+}
+
+gs_status gs_default_options(gs_options* opt) {
+  if (!opt) return GS_ERR_INVALID_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = GS_FP64;
+  opt->method = GS_METHOD_AUTO;
+  return GS_OK;
+}
+
+gs_status gs_problem_info(int problem_id, int* d, int* P, int* stiff, int* n_shared) {
+  ProblemInfo pi;
+  if (!problem_info(problem_id, &pi)) return GS_ERR_UNKNOWN_PROBLEM;
+  if (d) *d = pi.d;
+  if (P) *P = pi.P;
+  if (stiff) *stiff = pi.stiff;
+  if (n_shared) *n_shared = pi.n_shared;
+  return GS_OK;
+}
+
+gs_status gs_forward_record(int problem_id, int64_t n, const double* params, const double* y0,
+                            const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                            double rtol, double atol, const gs_options* opt, gs_stream stream,
+                            double* y_save_out, int32_t* traj_status, gs_record** rec_out) {
+  if (!rec_out) return GS_ERR_INVALID_ARG;
+  *rec_out = nullptr;
+  Call c;
+  gs_status st = check_common(problem_id, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, opt, &c);
+  if (st != GS_OK) return st;
+  if (n > 0 && !traj_status) return GS_ERR_INVALID_ARG;
+  gs_record* r = new (std::nothrow) gs_record();
+  if (!r) return GS_ERR_OOM;
+  st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol);
+  if (st != GS_OK) { destroy(r); return st; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n > 0) {
+    st = run_record(r, c, n, params, y0, shared_w, y_save_out, s);
+    if (st != GS_OK) { destroy(r); return st; }
+    cudaError_t e = cudaMemcpyAsync(traj_status, r->status, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { destroy(r); return GS_ERR_CUDA; }
+  }
+  r->bytes = record_bytes(r);
+  *rec_out = r;
+  return (n > 0 && r->ctr_host->any_failed) ? GS_ERR_TRAJ_FAILED : GS_OK;
+}
+
+gs_status gs_reverse(const gs_record* rec, const double* params, const double* y0, const float* shared_w,
+                     const double* y_save_bar, double* loss_out, double* params_bar, double* y0_bar,
+                     float* shared_w_bar, gs_stream stream) {
+  (void)y0;
+  if (!rec) return GS_ERR_INVALID_ARG;
+  if (rec->n == 0) return GS_OK;
+  if (!params) return GS_ERR_INVALID_ARG;
+  ProblemInfo pi;
+  problem_info(rec->problem, &pi);
+  if (pi.n_shared > 0 && !shared_w) return GS_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != rec->device) return GS_ERR_INVALID_ARG;
+  return launch_reverse(rec, params, shared_w, y_save_bar, loss_out, params_bar, y0_bar, shared_w_bar,
+                        (cudaStream_t)stream);
+}
+
+gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const double* y0,
+                        const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                        double rtol, double atol, const gs_options* opt, gs_stream stream, double* loss_out,
+                        double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status) {
+  Call c;
+  gs_status st = check_common(problem_id, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, opt, &c);
+  if (st != GS_OK) return st;
+  if (n == 0) return GS_OK;
+  if (!traj_status) return GS_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  gs_record* r = workspace(dev);
+  if (!r) return GS_ERR_OOM;
+  st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol);
+  if (st != GS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = run_record(r, c, n, params, y0, shared_w, nullptr, s);
+  if (st != GS_OK) return st;
+  if (c.kernel_ms) cudaEventRecord(r->ev[2], s);
+  st = launch_reverse(r, params, shared_w, nullptr, loss_out, params_bar, y0_bar, shared_w_bar, s);
+  if (st != GS_OK) return st;
+  if (c.kernel_ms) cudaEventRecord(r->ev[3], s);
+  cudaError_t e = cudaMemcpyAsync(traj_status, r->status, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[1], r->ev[2], r->ev[3]);
+  return r->ctr_host->any_failed ? GS_ERR_TRAJ_FAILED : GS_OK;
+}
+
+gs_status gs_record_bytes(const gs_record* rec, size_t* bytes) {
+  if (!rec || !bytes) return GS_ERR_INVALID_ARG;
+  *bytes = rec->bytes;
+  return GS_OK;
+}
+
+gs_status gs_record_stats(const gs_record* rec, int64_t* n, int64_t* accepted, int64_t* attempted) {
+  if (!rec) return GS_ERR_INVALID_ARG;
+  if (n) *n = rec->n;
+  if (!accepted && !attempted) return GS_OK;
+  std::vector<int32_t> S(rec->n), A(rec->n);
+  if (rec->n > 0) {
+    if (cudaMemcpy(S.data(), rec->S, rec->n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(A.data(), rec->natt, rec->n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return GS_ERR_CUDA;
+  }
+  int64_t sa = 0, sb = 0;
+  for (int64_t i = 0; i < rec->n; ++i) { sa += S[i]; sb += A[i]; }
+  if (accepted) *accepted = sa;
+  if (attempted) *attempted = sb;
+  return GS_OK;
+}
+
+gs_status gs_record_export_mesh(const gs_record* rec, int64_t* offsets, double* h) {
+  if (!rec || !offsets) return GS_ERR_INVALID_ARG;
+  const int64_t n = rec->n;
+  std::vector<int32_t> S(n), st(n);
+  std::vector<long long> head(n);
+  if (n > 0) {
+    if (cudaMemcpy(S.data(), rec->S, n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(head.data(), rec->head, n * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(st.data(), rec->status, n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return GS_ERR_CUDA;
+  }
+  offsets[0] = 0;
+  for (int64_t i = 0; i < n; ++i) offsets[i + 1] = offsets[i] + (st[i] == GS_TRAJ_OK ? S[i] : 0);
+  if (!h || n == 0) return GS_OK;
+  std::vector<double> arena((size_t)rec->arena_cap * rec->segw);
+  if (cudaMemcpy(arena.data(), rec->arena, arena.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return GS_ERR_CUDA;
+  for (int64_t i = 0; i < n; ++i) {
+    if (st[i] != GS_TRAJ_OK) continue;
+    // walk segments last to first; the last holds S - (nseg-1) k steps
+    const int Sk = S[i];
+    int m = Sk - ((Sk - 1) / rec->k) * rec->k;
+    long long seg = head[i];
+    int64_t end = offsets[i + 1];
+    while (seg >= 0) {
+      const double* sp = arena.data() + (size_t)seg * rec->segw;
+      for (int j = m - 1; j >= 0; --j) h[--end] = sp[2 + rec->d + j];
+      long long prev;
+      std::memcpy(&prev, sp, sizeof(prev));
+      seg = prev;
+      m = rec->k;
+    }
+    if (end != offsets[i]) return GS_ERR_CUDA;  // inconsistent record
+  }
+  return GS_OK;
+}
+
+gs_status gs_record_free(gs_record* rec) {
+  destroy(rec);
+  return GS_OK;
+}
+
+}  // extern "C"

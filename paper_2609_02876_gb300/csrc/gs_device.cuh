@@ -1,0 +1,361 @@
+// Device-side building blocks of the gradsolve-gb300 hot path: explicit-
+// rounding arithmetic, the problem registry (f, J^T v, f_theta^T v written out
+// by hand per problem), the Tsit5 tableau and step, and the warp-level helpers
+// of the persistent kernels.
+//
+// Every floating-point operation of the solver arithmetic is written with an
+// explicitly rounded intrinsic (fma_, mul_, add_, sub_). The compiler can then
+// neither contract nor reassociate it, so every kernel that instantiates this
+// code (with or without save-state output, record or reverse) performs the
+// same roundings in the same order: the mesh a record produces and the states
+// a reverse sweep recomputes do not depend on which kernel ran.
+//
+// One trajectory per lane, state in registers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gs {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr int KMAX = 32;  // largest checkpoint interval (accepted steps per record segment)
+
+enum : int { TRAJ_OK = 0, TRAJ_MAXSTEPS = 1, TRAJ_DT_UNDERFLOW = 2, TRAJ_NONFINITE = 3, TRAJ_SINGULAR = 4 };
+
+// ---------------------------------------------------------------------------
+// Explicitly rounded arithmetic (round to nearest even), FP64 and FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// Problems (paper Appendix A). Each provides
+//   f(y, p, o):           o = f(y, theta)
+//   vjp(y, p, v, yb, pb): yb = J(y)^T v,  pb += (df/dtheta)^T v
+// with the analytic derivatives of the printed right-hand sides, and the
+// operation counts (FP64 instructions; an FMA is one instruction, two flops)
+// F_OPS / F_FLOPS and VJP_OPS / VJP_FLOPS used for the algorithmic flop count.
+// ---------------------------------------------------------------------------
+struct Lorenz {  // sigma (y - x), x (rho - z) - y, x y - beta z; theta = (sigma, rho, beta)
+  static constexpr int D = 3, NP = 3;
+  template <class R>
+  __device__ __forceinline__ static void f(const R (&y)[D], const R (&p)[NP], R (&o)[D]) {
+    o[0] = mul_(p[0], sub_(y[1], y[0]));
+    o[1] = fma_(y[0], sub_(p[1], y[2]), -y[1]);
+    o[2] = fma_(y[0], y[1], -mul_(p[2], y[2]));
+  }
+  template <class R>
+  __device__ __forceinline__ static void vjp(const R (&y)[D], const R (&p)[NP], const R (&v)[D], R (&yb)[D],
+                                             R (&pb)[NP]) {
+    // J = [[-sigma, sigma, 0], [rho - z, -1, -x], [y, x, -beta]]
+    yb[0] = fma_(sub_(p[1], y[2]), v[1], fma_(y[1], v[2], -mul_(p[0], v[0])));
+    yb[1] = fma_(p[0], v[0], fma_(y[0], v[2], -v[1]));
+    yb[2] = -fma_(y[0], v[1], mul_(p[2], v[2]));
+    pb[0] = fma_(sub_(y[1], y[0]), v[0], pb[0]);
+    pb[1] = fma_(y[0], v[1], pb[1]);
+    pb[2] = fma_(-y[2], v[2], pb[2]);
+  }
+};
+
+struct VanDerPol {  // x' = v, v' = mu ((1 - x^2) v - x); theta = (mu)
+  static constexpr int D = 2, NP = 1;
+  template <class R>
+  __device__ __forceinline__ static void f(const R (&y)[D], const R (&p)[NP], R (&o)[D]) {
+    o[0] = y[1];
+    o[1] = mul_(p[0], fma_(fma_(-y[0], y[0], R(1)), y[1], -y[0]));
+  }
+  template <class R>
+  __device__ __forceinline__ static void vjp(const R (&y)[D], const R (&p)[NP], const R (&v)[D], R (&yb)[D],
+                                             R (&pb)[NP]) {
+    // J = [[0, 1], [mu (-2 x v - 1), mu (1 - x^2)]]
+    const R w = fma_(-y[0], y[0], R(1));
+    const R mv = mul_(p[0], v[1]);
+    yb[0] = -mul_(mv, fma_(add_(y[0], y[0]), y[1], R(1)));
+    yb[1] = fma_(mv, w, v[0]);
+    pb[0] = fma_(fma_(w, y[1], -y[0]), v[1], pb[0]);
+  }
+};
+
+struct Linear2 {  // y' = A y, A = [[p0, p1], [p2, p3]]
+  static constexpr int D = 2, NP = 4;
+  template <class R>
+  __device__ __forceinline__ static void f(const R (&y)[D], const R (&p)[NP], R (&o)[D]) {
+    o[0] = fma_(p[0], y[0], mul_(p[1], y[1]));
+    o[1] = fma_(p[2], y[0], mul_(p[3], y[1]));
+  }
+  template <class R>
+  __device__ __forceinline__ static void vjp(const R (&y)[D], const R (&p)[NP], const R (&v)[D], R (&yb)[D],
+                                             R (&pb)[NP]) {
+    yb[0] = fma_(p[0], v[0], mul_(p[2], v[1]));
+    yb[1] = fma_(p[1], v[0], mul_(p[3], v[1]));
+    pb[0] = fma_(y[0], v[0], pb[0]);
+    pb[1] = fma_(y[1], v[0], pb[1]);
+    pb[2] = fma_(y[0], v[1], pb[2]);
+    pb[3] = fma_(y[1], v[1], pb[3]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Tsit5 (Tsitouras 2011, Table 1): 7 stages, FSAL (b = row 7 of A, b_7 = 0).
+// ---------------------------------------------------------------------------
+namespace tsit5 {
+__host__ __device__ constexpr double A(int i, int j) {
+  // 0-based stage i (1..6), column j < i
+  return (i == 1 && j == 0)   ? 0.161
+         : (i == 2 && j == 0) ? -0.008480655492356989
+         : (i == 2 && j == 1) ? 0.335480655492357
+         : (i == 3 && j == 0) ? 2.897153057105493
+         : (i == 3 && j == 1) ? -6.359448489975075
+         : (i == 3 && j == 2) ? 4.3622954328695815
+         : (i == 4 && j == 0) ? 5.325864828439257
+         : (i == 4 && j == 1) ? -11.748883564062828
+         : (i == 4 && j == 2) ? 7.4955393428898365
+         : (i == 4 && j == 3) ? -0.09249506636175525
+         : (i == 5 && j == 0) ? 5.86145544294642
+         : (i == 5 && j == 1) ? -12.92096931784711
+         : (i == 5 && j == 2) ? 8.159367898576159
+         : (i == 5 && j == 3) ? -0.071584973281401
+         : (i == 5 && j == 4) ? -0.028269050394068383
+         : (i == 6 && j == 0) ? 0.09646076681806523
+         : (i == 6 && j == 1) ? 0.01
+         : (i == 6 && j == 2) ? 0.4798896504144996
+         : (i == 6 && j == 3) ? 1.379008574103742
+         : (i == 6 && j == 4) ? -3.290069515436081
+         : (i == 6 && j == 5) ? 2.324710524099774
+                              : 0.0;
+}
+__host__ __device__ constexpr double B(int j) { return A(6, j); }
+__host__ __device__ constexpr double Bhat(int j) {
+  return j == 0   ? 0.09468075576583945
+         : j == 1 ? 0.009183565540343
+         : j == 2 ? 0.4877705284247616
+         : j == 3 ? 1.234297566930479
+         : j == 4 ? -2.707712349983525
+         : j == 5 ? 1.866628418170587
+                  : 1.0 / 66.0;
+}
+__host__ __device__ constexpr double Btilde(int j) { return B(j) - Bhat(j); }  // error weights
+}  // namespace tsit5
+
+// Stage inputs Y[0..6] of one Tsit5 step from y with size h (Y[0] = y,
+// Y[6] = y_new by FSAL) and stage slopes K[0..KN-1]. K[0] must hold f(y).
+// KN = 7 also evaluates k7 = f(y_new) for the error estimate and FSAL.
+template <class Pb, class R, int KN>
+__device__ __forceinline__ void tsit5_stages(const R (&y)[Pb::D], const R (&p)[Pb::NP], R h, R (&Y)[7][Pb::D],
+                                             R (&K)[7][Pb::D]) {
+  constexpr int D = Pb::D;
+#pragma unroll
+  for (int c = 0; c < D; ++c) Y[0][c] = y[c];
+#pragma unroll
+  for (int i = 1; i < 7; ++i) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      R s = mul_(R(tsit5::A(i, 0)), K[0][c]);
+#pragma unroll
+      for (int j = 1; j < i; ++j) s = fma_(R(tsit5::A(i, j)), K[j][c], s);
+      Y[i][c] = fma_(h, s, y[c]);
+    }
+    if (i < 6 || KN == 7) Pb::f(Y[i], p, K[i]);
+  }
+}
+
+// Embedded error estimate e = y_new - yhat_new = h sum_j (b_j - bhat_j) k_j.
+template <class Pb, class R>
+__device__ __forceinline__ void tsit5_error(const R (&K)[7][Pb::D], R h, R (&e)[Pb::D]) {
+#pragma unroll
+  for (int c = 0; c < Pb::D; ++c) {
+    R s = mul_(R(tsit5::Btilde(0)), K[0][c]);
+#pragma unroll
+    for (int j = 1; j < 7; ++j) s = fma_(R(tsit5::Btilde(j)), K[j][c], s);
+    e[c] = mul_(h, s);
+  }
+}
+
+// Reverse of one Tsit5 step over its recomputed stage inputs Y[0..5]:
+// given the cotangent c of y_new returns v = dL/dy (the cotangent of y) and
+// accumulates dL/dtheta. kbar_j = h (b_j c + sum_{m>j} a_mj Ybar_m),
+// Ybar_j = J(Y_j)^T kbar_j, theta_bar += f_theta(Y_j)^T kbar_j,
+// v = c + sum_j Ybar_j.
+template <class Pb, class R, class RB>
+__device__ __forceinline__ void tsit5_reverse(const R (&Y)[7][Pb::D], const R (&p)[Pb::NP], R h, const R (&c)[Pb::D],
+                                              R (&v)[Pb::D], RB& pbacc) {
+  constexpr int D = Pb::D;
+  // acc[l] = sum over the stages m already reversed of a_ml Ybar_m; stage 6 (the
+  // first one reversed) starts every sum, so no zero is ever added.
+  R acc[6][D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) v[q] = c[q];
+#pragma unroll
+  for (int j = 5; j >= 0; --j) {
+    R kb[D], yb[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+      kb[q] = (j == 5) ? mul_(h, mul_(R(tsit5::B(j)), c[q])) : mul_(h, fma_(R(tsit5::B(j)), c[q], acc[j][q]));
+    pbacc.template vjp<Pb>(Y[j], p, kb, yb);
+#pragma unroll
+    for (int q = 0; q < D; ++q) v[q] = add_(v[q], yb[q]);
+#pragma unroll
+    for (int l = 0; l < j; ++l)
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        acc[l][q] = (j == 5) ? mul_(R(tsit5::A(j, l)), yb[q]) : fma_(R(tsit5::A(j, l)), yb[q], acc[l][q]);
+  }
+}
+
+// Parameter-gradient accumulators: plain (FP64) and compensated (FP32-mixed,
+// Neumaier's variant of Kahan summation).
+// vjp<Pb>(y, p, v, yb): yb = J(y)^T v and accumulates f_theta(y)^T v.
+template <int NP>
+struct PlainAcc {
+  double s[NP];
+  __device__ void zero() {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) s[q] = 0.0;
+  }
+  template <class Pb>
+  __device__ __forceinline__ void vjp(const double (&y)[Pb::D], const double (&p)[NP], const double (&v)[Pb::D],
+                                      double (&yb)[Pb::D]) {
+    Pb::vjp(y, p, v, yb, s);  // FP64: accumulate straight into the sums
+  }
+  __device__ double get(int q) const { return s[q]; }
+};
+template <int NP>
+struct CompensatedAcc {
+  float s[NP], comp[NP];
+  __device__ void zero() {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) s[q] = comp[q] = 0.0f;
+  }
+  template <class Pb>
+  __device__ __forceinline__ void vjp(const float (&y)[Pb::D], const float (&p)[NP], const float (&v)[Pb::D],
+                                      float (&yb)[Pb::D]) {
+    float x[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) x[q] = 0.0f;
+    Pb::vjp(y, p, v, yb, x);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float t = add_(s[q], x[q]);
+      comp[q] = add_(comp[q], (fabsf(s[q]) >= fabsf(x[q])) ? add_(sub_(s[q], t), x[q]) : add_(sub_(x[q], t), s[q]));
+      s[q] = t;
+    }
+  }
+  __device__ double get(int q) const { return (double)s[q] + (double)comp[q]; }
+};
+
+// ---------------------------------------------------------------------------
+// Step-size control (FP64 for t, h and the error test).
+// ---------------------------------------------------------------------------
+
+// Hardware base-2 logarithm and exponential (PTX lg2.approx / ex2.approx).
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Reciprocal of a positive FP64 scale to FP32 accuracy (relative 2^-23): the
+// hardware FP32 reciprocal of the rounded value, converted back. Scales below
+// 1e-30 (outside the FP32 normal range) take the exact FP64 division.
+__device__ __forceinline__ double recip_scale(double sc) {
+  if (sc < 1e-30) return 1.0 / sc;
+  return (double)__frcp_rn(__double2float_rn(sc));
+}
+
+// Weighted RMS error test of the paper's Sec. 2.1, as a mean square:
+// q = (1/D) sum_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2; accept iff q <= 1.
+// The scale and the sum are FP64; each ratio uses an FP32-accurate reciprocal
+// of the scale, so q carries a relative error below 1e-6: it decides accept /
+// reject and scales the next step, and never enters the accepted solution.
+template <int D, class R>
+__device__ __forceinline__ double err_meansq(const R (&e)[D], const R (&y)[D], const R (&yn)[D], double rtol,
+                                             double atol) {
+  double q = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const double sc = fma_(rtol, fmax(fabs((double)y[c]), fabs((double)yn[c])), atol);
+    const double r = mul_((double)e[c], recip_scale(sc));
+    q = fma_(r, r, q);
+  }
+  return mul_(q, 1.0 / D);
+}
+
+// Integral-controller factor from the mean-square error q = err^2:
+// clamp(0.9 err^(-1/5), 0.2, 10) = clamp(0.9 q^(-1/10), 0.2, 10); q = 0 gives 10.
+// FP32 with the hardware log2 / exp2: the factor only scales the next trial step.
+__device__ __forceinline__ double ctrl_factor(double q) {
+  if (!(q > 0.0)) return 10.0;
+  const float f = __fmul_rn(0.9f, ex2_approx(__fmul_rn(-0.1f, lg2_approx(__double2float_rn(q)))));
+  return (double)fminf(10.0f, fmaxf(0.2f, f));
+}
+
+// Starting step: the algorithm of Hairer, Norsett & Wanner, Vol. I, Sec. II.4
+// (order p = 5, the weighted RMS norm, one explicit Euler probe), evaluated in
+// FP32 from y0, theta and f(y0): it only picks the first trial step. Returns a
+// non-finite value if the inputs overflow FP32.
+template <class Pb>
+__device__ __forceinline__ double initial_step_f32(const float (&y0)[Pb::D], const float (&p)[Pb::NP],
+                                                   const float (&f0)[Pb::D], double t0, double t1, double rtol,
+                                                   double atol) {
+  constexpr int D = Pb::D;
+  float sc[D], y1[D], f1[D];
+  const float rt = (float)rtol, at = (float)atol, span = (float)(t1 - t0);
+  float d0 = 0.0f, d1 = 0.0f;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    sc[c] = fmaf(rt, fabsf(y0[c]), at);
+    const float r0 = y0[c] / sc[c], r1 = f0[c] / sc[c];
+    d0 = fmaf(r0, r0, d0);
+    d1 = fmaf(r1, r1, d1);
+  }
+  d0 = sqrtf(d0 / D);
+  d1 = sqrtf(d1 / D);
+  float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * d0 / d1;
+  h0 = fminf(h0, span);
+#pragma unroll
+  for (int c = 0; c < D; ++c) y1[c] = fmaf(h0, f0[c], y0[c]);
+  Pb::f(y1, p, f1);
+  float d2 = 0.0f;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const float r = (f1[c] - f0[c]) / sc[c];
+    d2 = fmaf(r, r, d2);
+  }
+  d2 = sqrtf(d2 / D) / h0;
+  const float dm = fmaxf(d1, d2);
+  const float h1 = (dm <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : ex2_approx(lg2_approx(0.01f / dm) * (1.0f / 6.0f));
+  return (double)fminf(fminf(100.0f * h0, h1), span);
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Warp-aggregated ticket: every lane with `want` gets a distinct value of
+// *ctr (post-increment), with one atomic per warp. Must be called by all 32
+// lanes together.
+__device__ __forceinline__ long long warp_ticket(unsigned long long* ctr, bool want) {
+  const unsigned mask = __ballot_sync(FULL_MASK, want);
+  if (mask == 0u) return -1;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane_id() == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+  base = __shfl_sync(FULL_MASK, base, leader);
+  const int rank = __popc(mask & ((1u << lane_id()) - 1u));
+  return want ? (long long)(base + rank) : -1;
+}
+
+}  // namespace gs

@@ -1,0 +1,76 @@
+// Internal interface between the C-ABI layer (gs_api.cu) and the kernel
+// translation units. Not installed; no torch or Python types.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gs {
+
+constexpr int MAX_SAVE_HOST = 256;
+constexpr int KMAX_HOST = 32;  // largest checkpoint interval accepted by the ABI
+
+// Arguments of the record (forward) kernels. Passed by value.
+struct FwdArgs {
+  int64_t n;
+  const double* params;  // [P][n]
+  const double* y0;      // [d][n]
+  const float* shared_w; // UDE weights or nullptr
+  double t0, t1, rtol, atol, h0;
+  int64_t max_steps;
+  int n_save;
+  double* y_save;        // [n_save][d][n] or nullptr
+  int32_t* status;       // [n]
+  int32_t* step_counts;  // [2][n] or nullptr
+  // record
+  double* arena;                  // segments of segw doubles
+  long long arena_cap;            // segments
+  unsigned long long* arena_top;  // segment allocation counter
+  int* overflow;                  // set when arena_top passes arena_cap
+  long long* head;                // [n] last segment of each trajectory (-1 if none)
+  int32_t* S;                     // [n] accepted steps
+  int32_t* natt;                  // [n] attempted steps
+  double* y_final;                // [d][n] state at t1
+  unsigned long long* work;       // trajectory ticket counter
+  int* any_failed;                // set when a trajectory ends with a non-OK status
+  int k;                          // accepted steps per segment
+  int segw;                       // doubles per segment
+  double save_t[MAX_SAVE_HOST];
+};
+
+// Arguments of the reverse kernels.
+struct RevArgs {
+  int64_t n;
+  const double* params;
+  const float* shared_w;
+  float* shared_w_bar;
+  double t0, t1;
+  int n_save;
+  const double* y_save_bar;  // [n_save][d][n] or nullptr (built-in loss)
+  double* loss;              // [n] or nullptr
+  double* params_bar;        // [P][n] or nullptr
+  double* y0_bar;            // [d][n] or nullptr
+  const int32_t* status;     // [n] recorded status
+  const double* arena;
+  long long arena_cap;       // segments (bounds every segment index read)
+  const long long* head;
+  const int32_t* S;
+  const double* y_final;
+  unsigned long long* work;
+  int k, segw;
+  double save_t[MAX_SAVE_HOST];
+};
+
+struct LaunchCfg {
+  int blocks;
+  int threads;
+  size_t smem;
+};
+
+// Launchers (one per method family). Return cudaSuccess or the launch error.
+// problem: GS_* id; precision: 0 FP64, 1 FP32-mixed; saves: write y_save.
+cudaError_t launch_tsit5_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_tsit5_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
+bool tsit5_supports(int problem, int precision);
+
+}  // namespace gs

@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads, exports every symbol include/gs.h declares,
+and rejects invalid arguments before touching a GPU (no compute calls here)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2609_02876_gb300 import _native as N
+from paper_2609_02876_gb300 import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return N.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = N.header_symbols()
+    assert len(syms) >= 10
+    for s in syms:
+        assert hasattr(lib, s), f"missing export {s}"
+
+
+def test_host_only_entry_points(lib):
+    assert lib.gs_status_string(0) == b"ok"
+    assert b"traj_status" in lib.gs_status_string(5)
+    o = N.GsOptions()
+    assert lib.gs_default_options(C.byref(o)) == 0
+    assert (o.precision, o.method, o.ckpt_k, o.max_steps, o.h0) == (0, 0, 0, 0, 0.0)
+    d, P, s, nw = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    expect = {0: (3, 3, 0, 0), 1: (2, 1, 0, 0), 2: (3, 3, 1, 0), 3: (8, 12, 1, 0), 4: (2, 4, 0, 0),
+              5: (2, 2, 0, 354)}
+    for pid, e in expect.items():
+        assert lib.gs_problem_info(pid, C.byref(d), C.byref(P), C.byref(s), C.byref(nw)) == 0
+        assert (d.value, P.value, s.value, nw.value) == e
+    assert lib.gs_problem_info(17, C.byref(d), C.byref(P), C.byref(s), C.byref(nw)) == N.GS_ERR_UNKNOWN_PROBLEM
+
+
+def _call(lib, **kw):
+    a = dict(pid=0, n=4, params=1, y0=1, w=None, t0=0.0, t1=1.0, save=[0.5, 1.0], rtol=1e-6, atol=1e-8, opt=None)
+    a.update(kw)
+    st = np.asarray(a["save"], dtype=np.float64)
+    o = None
+    if a["opt"] is not None:
+        o = N.GsOptions()
+        lib.gs_default_options(C.byref(o))
+        for k, v in a["opt"].items():
+            setattr(o, k, v)
+        o = C.byref(o)
+    return lib.gs_solve_grad(a["pid"], a["n"], a["params"], a["y0"], a["w"], a["t0"], a["t1"],
+                             st.ctypes.data_as(C.POINTER(C.c_double)), st.size, a["rtol"], a["atol"], o, None,
+                             1, 1, 1, None, 1)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(pid=42), N.GS_ERR_UNKNOWN_PROBLEM),
+    (dict(n=-1), N.GS_ERR_INVALID_ARG),
+    (dict(params=None), N.GS_ERR_INVALID_ARG),
+    (dict(t1=0.0), N.GS_ERR_INVALID_ARG),
+    (dict(t1=float("nan")), N.GS_ERR_INVALID_ARG),
+    (dict(save=[0.5, 0.5]), N.GS_ERR_INVALID_ARG),
+    (dict(save=[0.0]), N.GS_ERR_INVALID_ARG),
+    (dict(save=[1.5]), N.GS_ERR_INVALID_ARG),
+    (dict(rtol=0.0, atol=0.0), N.GS_ERR_INVALID_ARG),
+    (dict(rtol=-1e-6), N.GS_ERR_INVALID_ARG),
+    (dict(pid=5), N.GS_ERR_INVALID_ARG),  # the UDE needs shared weights
+    (dict(opt=dict(precision=7)), N.GS_ERR_INVALID_ARG),
+    (dict(opt=dict(ckpt_k=33)), N.GS_ERR_INVALID_ARG),
+    (dict(opt=dict(max_steps=-2)), N.GS_ERR_INVALID_ARG),
+    (dict(opt=dict(method=9)), N.GS_ERR_INVALID_ARG),
+])
+def test_invalid_arguments_are_rejected_on_the_host(lib, kw, code):
+    assert _call(lib, **kw) == code
+
+
+def test_too_many_save_times(lib):
+    assert _call(lib, save=np.linspace(0.001, 1.0, 257)) == N.GS_ERR_INVALID_ARG
+
+
+def test_empty_ensemble_is_a_no_op(lib):
+    assert _call(lib, n=0, params=None, y0=None) == N.GS_OK
