@@ -139,6 +139,37 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
                         double rtol, double atol, const gs_options* opt, gs_stream stream, double* loss_out,
                         double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status);
 
+/*
+ * gs_solve_grad without any device allocation. This entry point has no
+ * counterpart in the paper; it exists for callers that cannot call cudaMalloc:
+ * for example a process that has handed all free device memory to another
+ * framework's caching allocator, or a latency-critical thread that must not
+ * pay for, or block on, allocation and the device synchronisation that
+ * cudaFree implies. Arguments, layouts and results are those of gs_solve_grad.
+ *
+ * Scratch: the record lives in one fixed array of GS_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that the library declares as a static device object; every GPU that
+ * loads the library holds it until the process exits. Nothing is allocated
+ * per call (no cudaMalloc / cudaFree / allocating library routine).
+ * Limits: n <= GS_NOALLOC_MAX_TRAJ (16384); a larger n returns
+ * GS_ERR_INVALID_ARG before any work. If an ensemble's record does not fit the
+ * array (more accepted steps than it holds), the call returns GS_ERR_OOM and
+ * its outputs are undefined: split the ensemble.
+ * The first call made on a device resolves the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture. Every call shares the one array and overwrites what the
+ * previous call left in it: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Synchronises `stream`. Only Tsit5 problems; shared_w_bar is not written.
+ */
+#define GS_NOALLOC_MAX_TRAJ 16384
+#define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
+gs_status gs_solve_grad_noalloc(int problem_id, int64_t n, const double* params, const double* y0,
+                                const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                                double rtol, double atol, const gs_options* opt, gs_stream stream,
+                                double* loss_out, double* params_bar, double* y0_bar, float* shared_w_bar,
+                                int32_t* traj_status);
+
 /* Device bytes held by a record. */
 gs_status gs_record_bytes(const gs_record* rec, size_t* bytes);
 
