@@ -197,7 +197,7 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   c->step_counts = o.step_counts;
   c->kernel_ms = o.kernel_ms;
   if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
-  if (method == GS_METHOD_RODAS5P) return GS_ERR_INVALID_ARG;  // stiff kernels: separate translation unit
+  if (method == GS_METHOD_RODAS5P && !rodas_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   return GS_OK;
 }
 
@@ -237,7 +237,8 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
     a.y_final = r->y_final;
     a.work = &r->ctr->work_fwd;
     if (c.kernel_ms) cudaEventRecord(r->ev[0], s);
-    e = launch_tsit5_forward(c.problem, c.precision, a, s);
+    e = (c.method == GS_METHOD_RODAS5P) ? launch_rodas_forward(c.problem, c.precision, a, s)
+                                        : launch_tsit5_forward(c.problem, c.precision, a, s);
     if (e != cudaSuccess) return GS_ERR_CUDA;
     if (c.kernel_ms) cudaEventRecord(r->ev[1], s);
     e = cudaMemcpyAsync(r->ctr_host, r->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
@@ -338,7 +339,8 @@ gs_status launch_reverse(const gs_record* r, const double* params, const float* 
   a.segw = r->segw;
   cudaError_t e = cudaMemsetAsync(&r->ctr->work_rev, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  e = launch_tsit5_reverse(r->problem, r->precision, a, s);
+  e = (r->method == GS_METHOD_RODAS5P) ? launch_rodas_reverse(r->problem, r->precision, a, s)
+                                       : launch_tsit5_reverse(r->problem, r->precision, a, s);
   return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

@@ -100,6 +100,146 @@ struct Linear2 {  // y' = A y, A = [[p0, p1], [p2, p3]]
     pb[2] = fma_(y[0], v[1], pb[2]);
     pb[3] = fma_(y[1], v[1], pb[3]);
   }
+  // Dense J (row-major, J[c][a] = d f_c / d y_a) and the gradient of
+  // g = r^T J(y, theta) u: gy += dg/dy, gp += dg/dtheta (J = A: no y term).
+  template <class R>
+  __device__ __forceinline__ static void jac(const R (&y)[D], const R (&p)[NP], R (&J)[D][D]) {
+    J[0][0] = p[0]; J[0][1] = p[1];
+    J[1][0] = p[2]; J[1][1] = p[3];
+  }
+  template <class R>
+  __device__ __forceinline__ static void jac_contract(const R (&y)[D], const R (&p)[NP], const R (&r)[D],
+                                                      const R (&u)[D], R (&gy)[D], R (&gp)[NP]) {
+    gp[0] = fma_(r[0], u[0], gp[0]);
+    gp[1] = fma_(r[0], u[1], gp[1]);
+    gp[2] = fma_(r[1], u[0], gp[2]);
+    gp[3] = fma_(r[1], u[1], gp[3]);
+  }
+};
+
+// Robertson (Appendix A): y1' = -k1 y1 + k3 y2 y3, y2' = k1 y1 - k3 y2 y3 - k2 y2^2,
+// y3' = k2 y2^2; theta = (k1, k2, k3).
+struct Robertson {
+  static constexpr int D = 3, NP = 3;
+  template <class R>
+  __device__ __forceinline__ static void f(const R (&y)[D], const R (&p)[NP], R (&o)[D]) {
+    const R a = mul_(p[0], y[0]);
+    const R b = mul_(mul_(p[2], y[1]), y[2]);
+    const R c = mul_(mul_(p[1], y[1]), y[1]);
+    o[0] = sub_(b, a);
+    o[1] = sub_(sub_(a, b), c);
+    o[2] = c;
+  }
+  template <class R>
+  __device__ __forceinline__ static void vjp(const R (&y)[D], const R (&p)[NP], const R (&v)[D], R (&yb)[D],
+                                             R (&pb)[NP]) {
+    const R d01 = sub_(v[1], v[0]), d21 = sub_(v[2], v[1]);
+    yb[0] = mul_(p[0], d01);
+    yb[1] = fma_(mul_(p[2], y[2]), -d01, mul_(add_(p[1], p[1]), mul_(y[1], d21)));
+    yb[2] = mul_(mul_(p[2], y[1]), -d01);
+    pb[0] = fma_(y[0], d01, pb[0]);
+    pb[1] = fma_(mul_(y[1], y[1]), d21, pb[1]);
+    pb[2] = fma_(mul_(y[1], y[2]), -d01, pb[2]);
+  }
+  template <class R>
+  __device__ __forceinline__ static void jac(const R (&y)[D], const R (&p)[NP], R (&J)[D][D]) {
+    const R k3y1 = mul_(p[2], y[1]), k3y2 = mul_(p[2], y[2]), k2y1x2 = mul_(add_(p[1], p[1]), y[1]);
+    J[0][0] = -p[0]; J[0][1] = k3y2;               J[0][2] = k3y1;
+    J[1][0] = p[0];  J[1][1] = -add_(k3y2, k2y1x2); J[1][2] = -k3y1;
+    J[2][0] = R(0);  J[2][1] = k2y1x2;             J[2][2] = R(0);
+  }
+  template <class R>
+  __device__ __forceinline__ static void jac_contract(const R (&y)[D], const R (&p)[NP], const R (&r)[D],
+                                                      const R (&u)[D], R (&gy)[D], R (&gp)[NP]) {
+    // g = r^T J u; J depends on y2, y3 (1-based) and linearly on k.
+    const R r01 = sub_(r[0], r[1]), r21 = sub_(r[2], r[1]);
+    gy[1] = fma_(mul_(p[2], u[2]), r01, fma_(mul_(add_(p[1], p[1]), u[1]), r21, gy[1]));
+    gy[2] = fma_(mul_(p[2], u[1]), r01, gy[2]);
+    gp[0] = fma_(u[0], -r01, gp[0]);
+    gp[1] = fma_(mul_(add_(y[1], y[1]), u[1]), r21, gp[1]);
+    gp[2] = fma_(fma_(y[2], u[1], mul_(y[1], u[2])), r01, gp[2]);
+  }
+};
+
+// HIRES (Appendix A), the 12 distinct literal constants as parameters
+// p0..p11 = (1.71, 0.43, 8.32, 0.0007, 8.75, 10.03, 0.035, 1.12, 1.745, 280,
+// 0.69, 1.81), each shared wherever it appears.
+struct Hires {
+  static constexpr int D = 8, NP = 12;
+  template <class R>
+  __device__ __forceinline__ static void f(const R (&y)[D], const R (&p)[NP], R (&o)[D]) {
+    const R w = mul_(mul_(p[9], y[5]), y[7]);
+    o[0] = add_(fma_(p[2], y[2], fma_(p[1], y[1], -mul_(p[0], y[0]))), p[3]);
+    o[1] = fma_(p[0], y[0], -mul_(p[4], y[1]));
+    o[2] = fma_(p[6], y[4], fma_(p[1], y[3], -mul_(p[5], y[2])));
+    o[3] = fma_(p[2], y[1], fma_(p[0], y[2], -mul_(p[7], y[3])));
+    o[4] = fma_(p[1], add_(y[5], y[6]), -mul_(p[8], y[4]));
+    o[5] = sub_(fma_(p[10], add_(y[3], y[6]), fma_(p[0], y[4], -mul_(p[1], y[5]))), w);
+    o[6] = fma_(-p[11], y[6], w);
+    o[7] = fma_(p[11], y[6], -w);
+  }
+  template <class R>
+  __device__ __forceinline__ static void vjp(const R (&y)[D], const R (&p)[NP], const R (&v)[D], R (&yb)[D],
+                                             R (&pb)[NP]) {
+    const R d10 = sub_(v[1], v[0]);
+    const R s = sub_(sub_(v[6], v[5]), v[7]);  // v6 - v5 - v7
+    const R d76 = sub_(v[7], v[6]);
+    yb[0] = mul_(p[0], d10);
+    yb[1] = fma_(p[1], v[0], fma_(p[2], v[3], -mul_(p[4], v[1])));
+    yb[2] = fma_(p[2], v[0], fma_(p[0], v[3], -mul_(p[5], v[2])));
+    yb[3] = fma_(p[1], v[2], fma_(p[10], v[5], -mul_(p[7], v[3])));
+    yb[4] = fma_(p[6], v[2], fma_(p[0], v[5], -mul_(p[8], v[4])));
+    yb[5] = fma_(p[1], sub_(v[4], v[5]), mul_(mul_(p[9], y[7]), s));
+    yb[6] = fma_(p[1], v[4], fma_(p[10], v[5], mul_(p[11], d76)));
+    yb[7] = mul_(mul_(p[9], y[5]), s);
+    pb[0] = fma_(y[0], d10, fma_(y[2], v[3], fma_(y[4], v[5], pb[0])));
+    pb[1] = fma_(y[1], v[0], fma_(y[3], v[2], fma_(add_(y[5], y[6]), v[4], fma_(-y[5], v[5], pb[1]))));
+    pb[2] = fma_(y[2], v[0], fma_(y[1], v[3], pb[2]));
+    pb[3] = add_(v[0], pb[3]);
+    pb[4] = fma_(-y[1], v[1], pb[4]);
+    pb[5] = fma_(-y[2], v[2], pb[5]);
+    pb[6] = fma_(y[4], v[2], pb[6]);
+    pb[7] = fma_(-y[3], v[3], pb[7]);
+    pb[8] = fma_(-y[4], v[4], pb[8]);
+    pb[9] = fma_(mul_(y[5], y[7]), s, pb[9]);
+    pb[10] = fma_(add_(y[3], y[6]), v[5], pb[10]);
+    pb[11] = fma_(y[6], d76, pb[11]);
+  }
+  template <class R>
+  __device__ __forceinline__ static void jac(const R (&y)[D], const R (&p)[NP], R (&J)[D][D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) J[i][j] = R(0);
+    const R p9y7 = mul_(p[9], y[7]), p9y5 = mul_(p[9], y[5]);
+    J[0][0] = -p[0]; J[0][1] = p[1]; J[0][2] = p[2];
+    J[1][0] = p[0];  J[1][1] = -p[4];
+    J[2][2] = -p[5]; J[2][3] = p[1]; J[2][4] = p[6];
+    J[3][1] = p[2];  J[3][2] = p[0]; J[3][3] = -p[7];
+    J[4][4] = -p[8]; J[4][5] = p[1]; J[4][6] = p[1];
+    J[5][3] = p[10]; J[5][4] = p[0]; J[5][5] = -add_(p9y7, p[1]); J[5][6] = p[10]; J[5][7] = -p9y5;
+    J[6][5] = p9y7;  J[6][6] = -p[11]; J[6][7] = p9y5;
+    J[7][5] = -p9y7; J[7][6] = p[11];  J[7][7] = -p9y5;
+  }
+  template <class R>
+  __device__ __forceinline__ static void jac_contract(const R (&y)[D], const R (&p)[NP], const R (&r)[D],
+                                                      const R (&u)[D], R (&gy)[D], R (&gp)[NP]) {
+    // g = r^T J u: the y-dependent entries are p9 y8 and p9 y6 (1-based) in rows 6..8.
+    const R s = sub_(sub_(r[6], r[5]), r[7]);  // r6 - r5 - r7
+    gy[5] = fma_(mul_(p[9], u[7]), s, gy[5]);
+    gy[7] = fma_(mul_(p[9], u[5]), s, gy[7]);
+    gp[0] = fma_(sub_(r[1], r[0]), u[0], fma_(r[3], u[2], fma_(r[5], u[4], gp[0])));
+    gp[1] = fma_(r[0], u[1], fma_(r[2], u[3], fma_(r[4], add_(u[5], u[6]), fma_(-r[5], u[5], gp[1]))));
+    gp[2] = fma_(r[0], u[2], fma_(r[3], u[1], gp[2]));
+    gp[4] = fma_(-r[1], u[1], gp[4]);
+    gp[5] = fma_(-r[2], u[2], gp[5]);
+    gp[6] = fma_(r[2], u[4], gp[6]);
+    gp[7] = fma_(-r[3], u[3], gp[7]);
+    gp[8] = fma_(-r[4], u[4], gp[8]);
+    gp[9] = fma_(fma_(y[7], u[5], mul_(y[5], u[7])), s, gp[9]);
+    gp[10] = fma_(r[5], add_(u[3], u[6]), gp[10]);
+    gp[11] = fma_(u[6], sub_(r[7], r[6]), gp[11]);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -223,6 +363,13 @@ struct PlainAcc {
   __device__ __forceinline__ void vjp(const double (&y)[Pb::D], const double (&p)[NP], const double (&v)[Pb::D],
                                       double (&yb)[Pb::D]) {
     Pb::vjp(y, p, v, yb, s);  // FP64: accumulate straight into the sums
+  }
+  // gy += d/dy (r^T J(y) u), theta_bar += d/dtheta (r^T J u)
+  template <class Pb>
+  __device__ __forceinline__ void jac_contract(const double (&y)[Pb::D], const double (&p)[NP],
+                                               const double (&r)[Pb::D], const double (&u)[Pb::D],
+                                               double (&gy)[Pb::D]) {
+    Pb::jac_contract(y, p, r, u, gy, s);
   }
   __device__ double get(int q) const { return s[q]; }
 };

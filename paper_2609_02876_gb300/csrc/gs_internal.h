@@ -72,5 +72,8 @@ struct LaunchCfg {
 cudaError_t launch_tsit5_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_tsit5_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
 bool tsit5_supports(int problem, int precision);
+cudaError_t launch_rodas_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_rodas_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
+bool rodas_supports(int problem, int precision);
 
 }  // namespace gs

@@ -1,0 +1,732 @@
+// The persistent record and reverse-sweep kernels, generic over the one-step
+// method (Tsit5 for non-stiff problems, Rodas5P for stiff ones).
+//
+// Both kernels are persistent: a grid of resident CTAs whose lanes each own one
+// trajectory at a time and take the next one from a global ticket counter
+// (one atomic per warp per refill) as soon as theirs finishes, so a lane never
+// waits for a slower neighbour's trajectory to end. Each loop iteration first
+// does the lane's bookkeeping (refill, record write-out, the walk through its
+// record), then meets the warp at a __syncwarp and runs one unit of solver
+// arithmetic as a single block, so the floating-point work of all busy lanes
+// issues together whatever phase their trajectories are in.
+//
+// Record (paper Sec. 3.1, map R): the adaptive loop of Sec. 2.1 with the
+// weighted RMS error test and an integral controller. Accepted step sizes are
+// staged per lane in shared memory and written out as fixed-size record
+// segments [prev, t_start, y_start[d], h[k]] (one vector-stored segment per k
+// accepted steps) allocated from a device arena.
+//
+// Reverse (paper Sec. 3.1, discrete adjoint of Eq. (replay)): each lane walks
+// its trajectory's segments last to first and runs one unit per iteration: a
+// state recompute inside a segment (k > 1 only), a step VJP
+// (lambda_{i-1} = dPhi/dy^T lambda_i), or a save-time side-step VJP
+// (lambda_i += dPhi/dy^T ybar_s).
+//
+// A Method provides Carry (state carried between accepted steps), start (the
+// carry and f(y0) for the starting step), trial (one trial step: y_new and the
+// error estimate; false if the step's linear system is singular), side (one
+// step of a given size from an accepted state) and unit (the reverse unit).
+#pragma once
+
+#include <type_traits>
+
+#include "gs_device.cuh"
+#include "gs_internal.h"
+#include "gs_rodas.cuh"
+
+namespace gs {
+
+constexpr int TPB_FWD = 128;
+constexpr int TPB_REV = 128;
+
+enum : int { U_NONE = 0, U_RECOMP = 1, U_STEP = 2, U_SIDE = 3, U_DONE = 4, U_FAIL = 5 };
+
+__device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// Cotangent of a unit: the lambda of a step unit, or the save-time cotangent of
+// a side unit (the user's, or 2 y(t_s) for the built-in loss, whose value the
+// unit adds to the loss).
+template <class Pb, class R, bool USER_COT>
+__device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bool side, int us,
+                                               const R (&ynew)[Pb::D], const R (&lam)[Pb::D], R (&cv)[Pb::D],
+                                               double& loss) {
+  constexpr int D = Pb::D;
+  double l2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    R cs;
+    if (USER_COT) {
+      cs = (R)a.y_save_bar[((long long)us * D + c) * a.n + k];
+    } else {
+      cs = add_(ynew[c], ynew[c]);  // d/dy of ||y||^2
+      l2 = fma_((double)ynew[c], (double)ynew[c], l2);
+    }
+    cv[c] = side ? cs : lam[c];
+  }
+  if (!USER_COT && side) loss = add_(loss, l2);
+}
+
+// ---------------------------------------------------------------------------
+// Methods
+// ---------------------------------------------------------------------------
+struct Tsit5Method {
+  template <class Pb, class R>
+  struct Carry {
+    R k1[Pb::D];  // FSAL: f(y) of the current accepted state
+  };
+  template <class Pb, class R>
+  __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>& cy,
+                                               float (&f0)[Pb::D]) {
+    Pb::f(y, p, cy.k1);
+#pragma unroll
+    for (int c = 0; c < Pb::D; ++c) f0[c] = (float)cy.k1[c];
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                               const Carry<Pb, R>& cy, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                               Carry<Pb, R>& next) {
+    constexpr int D = Pb::D;
+    R Y[7][D], K[7][D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) K[0][c] = cy.k1[c];
+    tsit5_stages<Pb, R, 7>(y, p, (R)h, Y, K);
+    tsit5_error<Pb, R>(K, (R)h, e);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      ynew[c] = Y[6][c];
+      next.k1[c] = K[6][c];
+    }
+    return true;
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool side(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                              const Carry<Pb, R>& cy, R (&ys)[Pb::D]) {
+    constexpr int D = Pb::D;
+    R Y[7][D], K[7][D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) K[0][c] = cy.k1[c];
+    tsit5_stages<Pb, R, 6>(y, p, (R)h, Y, K);
+#pragma unroll
+    for (int c = 0; c < D; ++c) ys[c] = Y[6][c];
+    return true;
+  }
+  // Reverse unit: stages from x with step h; a step unit replaces lambda with
+  // dPhi/dy^T lambda, a side unit adds dPhi/dy^T ybar_s. Returns y_new in ynew.
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, int us, const R (&x)[Pb::D],
+                                              double h, const R (&p)[Pb::NP], R (&lam)[Pb::D], Acc& pacc,
+                                              double& loss, R (&ynew)[Pb::D]) {
+    constexpr int D = Pb::D;
+    R Y[7][D], K[7][D];
+    Pb::f(x, p, K[0]);
+    tsit5_stages<Pb, R, 6>(x, p, (R)h, Y, K);
+#pragma unroll
+    for (int c = 0; c < D; ++c) ynew[c] = Y[6][c];
+    if (mode == U_RECOMP) return true;
+    const bool side = (mode == U_SIDE);
+    R cv[D], v[D];
+    unit_cotangent<Pb, R, USER_COT>(a, k, side, us, ynew, lam, cv, loss);
+    tsit5_reverse<Pb, R>(Y, p, (R)h, cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
+    return true;
+  }
+};
+
+struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
+  template <class Pb, class R>
+  struct Carry {};
+  template <class Pb, class R>
+  __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>&,
+                                               float (&f0)[Pb::D]) {
+    R f[Pb::D];
+    Pb::f(y, p, f);
+#pragma unroll
+    for (int c = 0; c < Pb::D; ++c) f0[c] = (float)f[c];
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                               const Carry<Pb, R>&, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                               Carry<Pb, R>&) {
+    static_assert(std::is_same<R, double>::value, "Rodas5P runs in FP64");
+    constexpr int D = Pb::D;
+    double Y[8][D], U[8][D], LU[D][D], rinv[D];
+    int piv[D];
+    const bool ok = rodas_step<Pb>(y, p, h, Y, U, LU, piv, rinv, ynew);
+#pragma unroll
+    for (int c = 0; c < D; ++c) e[c] = U[7][c];
+    return ok;
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool side(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                              const Carry<Pb, R>&, R (&ys)[Pb::D]) {
+    constexpr int D = Pb::D;
+    double Y[8][D], U[8][D], LU[D][D], rinv[D];
+    int piv[D];
+    return rodas_step<Pb>(y, p, h, Y, U, LU, piv, rinv, ys);
+  }
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, int us, const R (&x)[Pb::D],
+                                              double h, const R (&p)[Pb::NP], R (&lam)[Pb::D], Acc& pacc,
+                                              double& loss, R (&ynew)[Pb::D]) {
+    static_assert(std::is_same<R, double>::value, "Rodas5P runs in FP64");
+    constexpr int D = Pb::D;
+    double Y[8][D], U[8][D], LU[D][D], rinv[D];
+    int piv[D];
+    const bool ok = rodas_step<Pb>(x, p, h, Y, U, LU, piv, rinv, ynew);
+    if (mode == U_RECOMP) return ok;
+    const bool side = (mode == U_SIDE);
+    double cv[D], v[D];
+    unit_cotangent<Pb, R, USER_COT>(a, k, side, us, ynew, lam, cv, loss);
+    rodas_reverse<Pb>(x, p, h, Y, U, LU, piv, rinv, cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
+    return ok;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Record kernel
+// ---------------------------------------------------------------------------
+template <class M, class Pb, class R, bool SAVES>
+__global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
+  constexpr int D = Pb::D, NP = Pb::NP;
+  using Carry = typename M::template Carry<Pb, R>;
+  extern __shared__ double smem[];
+  const int ns = a.n_save;
+  double* s_save = smem;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
+  const int TB = blockDim.x;
+  double* stg = smem + ((ns + 1) & ~1) + threadIdx.x;  // this lane's segment staging, stride TB
+  __syncthreads();
+
+  const long long n = a.n;
+  const double t1 = a.t1;
+  const double sliver = 1e-12 * fmax(1.0, fabs(t1));
+  long long k = -1;
+  bool drained = false;
+  double t = 0.0, h = 0.0;
+  R y[D], p[NP];
+  Carry cy;
+  int S = 0, natt = 0, slot = 0, js = 0, status = TRAJ_OK;
+  bool rej = false, lastnf = false, lastsing = false, pending_fail = false;
+  long long prev = -1;
+
+  for (;;) {
+    // ---- refill: lanes without a trajectory take the next ticket
+    const bool need = (k < 0) && !drained;
+    if (__any_sync(FULL_MASK, need)) {
+      const long long got = warp_ticket(a.work, need);
+      if (need) {
+        if (got < n) {
+          k = got;
+          bool fin = true;
+          float yf[D], pf[NP], ff[D];
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const double v = a.params[q * n + k];
+            p[q] = (R)v;
+            pf[q] = (float)v;
+            fin = fin && isfinite(v);
+          }
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const double v = a.y0[c * n + k];
+            y[c] = (R)v;
+            yf[c] = (float)v;
+            fin = fin && isfinite(v);
+          }
+          t = a.t0;
+          S = natt = slot = js = 0;
+          status = TRAJ_OK;
+          rej = lastnf = lastsing = false;
+          prev = -1;
+          M::template start<Pb, R>(y, p, cy, ff);
+          h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
+          fin = fin && isfinite(h) && h > 0.0;
+          pending_fail = !fin;
+          if (!fin) status = TRAJ_NONFINITE;
+          stg[1 * TB] = t;
+#pragma unroll
+          for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = (double)y[c];
+        } else {
+          drained = true;
+        }
+      }
+    }
+    if (!__any_sync(FULL_MASK, k >= 0)) break;
+
+    bool done = false;
+    if (k >= 0 && pending_fail) done = true;
+    if (k >= 0 && !pending_fail && natt >= a.max_steps) {
+      status = TRAJ_MAXSTEPS;
+      done = true;
+    }
+    const bool trial = (k >= 0) && !done;
+    bool last = false;
+    if (trial && t + h >= t1 - sliver) {
+      h = t1 - t;
+      last = true;
+    }
+
+    // ---- one trial step (all lanes with a live trajectory, one code path)
+    __syncwarp();
+    R yn[D], e[D];
+    Carry next;
+    double q = 2.0;
+    bool solved = true;
+    if (trial) {
+      ++natt;
+      solved = M::template trial<Pb, R>(y, p, h, cy, yn, e, next);
+      q = err_meansq<D>(e, y, yn, a.rtol, a.atol);
+    }
+    const bool accept = trial && solved && (q <= 1.0);  // NaN rejects
+    if (accept) {
+      const double tn = last ? t1 : add_(t, h);
+      if (SAVES) {
+        // save times in [t, tn): one extra step from y; exactly tn: y_new
+        while (js < ns && s_save[js] < tn) {
+          const double hs = s_save[js] - t;
+          R ys[D];
+          bool ok = true;
+          if (hs == 0.0) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) ys[c] = y[c];
+          } else {
+            ok = M::template side<Pb, R>(y, p, hs, cy, ys);
+          }
+#pragma unroll
+          for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = ok ? (double)ys[c] : nan_d();
+          ++js;
+        }
+        while (js < ns && s_save[js] == tn) {
+#pragma unroll
+          for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = (double)yn[c];
+          ++js;
+        }
+      }
+      stg[(2 + D + slot) * TB] = h;
+      ++slot;
+      t = tn;
+#pragma unroll
+      for (int c = 0; c < D; ++c) y[c] = yn[c];
+      cy = next;
+      ++S;
+      if (last) done = true;
+    }
+    if (trial && !done) {
+      // integral controller: accepted steps grow at most x10 (x1 right after a
+      // rejection), rejected ones shrink by the same rule, x0.2 on a non-finite
+      // error, x0.25 when the step's linear system is singular
+      const bool nf = solved && !isfinite(q);
+      double fac = !solved ? 0.25 : (nf ? 0.2 : ctrl_factor(q));
+      if (accept && rej) fac = fmin(fac, 1.0);
+      h = mul_(h, fac);
+      rej = !accept;
+      lastnf = !accept && nf;
+      lastsing = !solved;
+      if (fabs(h) < 1e-14 * fmax(1.0, fabs(t))) {
+        status = lastsing ? TRAJ_SINGULAR : (lastnf ? TRAJ_NONFINITE : TRAJ_DT_UNDERFLOW);
+        done = true;
+      }
+    }
+    const bool flush = (k >= 0) && ((slot == a.k) || (done && slot > 0));
+
+    // ---- segment write-out: one arena slot per flushing lane, one atomic per warp
+    if (__any_sync(FULL_MASK, flush)) {
+      const long long idx = warp_ticket(a.arena_top, flush);
+      if (flush) {
+        stg[0] = __longlong_as_double(prev);
+        if (idx < a.arena_cap) {
+          double2* dst = reinterpret_cast<double2*>(a.arena + idx * a.segw);
+          for (int w = 0; w < (a.segw >> 1); ++w) dst[w] = make_double2(stg[(2 * w) * TB], stg[(2 * w + 1) * TB]);
+        } else {
+          *a.overflow = 1;
+        }
+        prev = idx;
+        slot = 0;
+        stg[1 * TB] = t;
+#pragma unroll
+        for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = (double)y[c];
+      }
+    }
+
+    if (done) {
+      a.head[k] = prev;
+      a.S[k] = S;
+      a.natt[k] = natt;
+      a.status[k] = status;
+#pragma unroll
+      for (int c = 0; c < D; ++c) a.y_final[c * n + k] = (double)y[c];
+      if (a.step_counts) {
+        a.step_counts[k] = S;
+        a.step_counts[n + k] = natt;
+      }
+      if (status != TRAJ_OK) *a.any_failed = 1;
+      k = -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse-kernel helpers
+// ---------------------------------------------------------------------------
+template <int NP, int D>
+__device__ __forceinline__ void write_nan(const RevArgs& a, long long k) {
+  const long long n = a.n;
+  if (a.params_bar)
+    for (int q = 0; q < NP; ++q) a.params_bar[q * n + k] = nan_d();
+  if (a.y0_bar)
+    for (int c = 0; c < D; ++c) a.y0_bar[c * n + k] = nan_d();
+  if (a.loss) a.loss[k] = nan_d();
+}
+
+template <int NP, int D, class R, class Acc>
+__device__ __forceinline__ void write_grad(const RevArgs& a, long long k, const Acc& pacc, const R (&lam)[D],
+                                           double loss) {
+  const long long n = a.n;
+  if (a.params_bar)
+#pragma unroll
+    for (int q = 0; q < NP; ++q) a.params_bar[q * n + k] = pacc.get(q);
+  if (a.y0_bar)
+#pragma unroll
+    for (int c = 0; c < D; ++c) a.y0_bar[c * n + k] = (double)lam[c];
+  if (a.loss) a.loss[k] = loss;
+}
+
+// Save times attached to the state (tx, yx), visited in decreasing order:
+// equal times add their cotangent to lambda directly; a later time is a side
+// step from the state (returns true with its save index in us).
+template <int D, class R, bool USER_COT>
+__device__ __forceinline__ bool next_save(const RevArgs& a, const double* s_save, long long k, int& js, double tx,
+                                          const R (&yx)[D], R (&lam)[D], double& loss, int& us) {
+  while (js >= 0 && s_save[js] >= tx) {
+    if (s_save[js] == tx) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (USER_COT) {
+          lam[c] = add_(lam[c], (R)a.y_save_bar[((long long)js * D + c) * a.n + k]);
+        } else {
+          lam[c] = add_(lam[c], add_(yx[c], yx[c]));
+          loss = fma_((double)yx[c], (double)yx[c], loss);
+        }
+      }
+      --js;
+    } else {
+      us = js;
+      --js;
+      return true;
+    }
+  }
+  return false;
+}
+
+template <class R, int NP>
+using AccOf = typename std::conditional<std::is_same<R, float>::value, CompensatedAcc<NP>, PlainAcc<NP>>::type;
+
+// ---------------------------------------------------------------------------
+// Reverse kernel, checkpoint interval k > 1: states inside a segment are
+// recomputed from its checkpoint into a per-lane buffer (local memory).
+// ---------------------------------------------------------------------------
+enum : int { PH_LOAD = 0, PH_RECOMP = 1, PH_INJECT = 2 };
+
+template <class M, class Pb, class R, bool USER_COT>
+__global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
+  constexpr int D = Pb::D, NP = Pb::NP;
+  using Acc = AccOf<R, NP>;
+  extern __shared__ double smem[];
+  const int ns = a.n_save;
+  double* s_save = smem;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
+  __syncthreads();
+
+  const long long n = a.n;
+  long long k = -1;
+  bool drained = false;
+  R p[NP], lam[D], yfin[D];
+  Acc pacc;
+  double loss = 0.0;
+  long long seg = -1, prevseg = -1;
+  int m = 0, j = 0, rj = 0, js = -1, phase = PH_LOAD, segs_left = 0;
+  bool final_seg = true;
+  double ts[KMAX], hs[KMAX];
+  R ys[KMAX][D];
+
+  for (;;) {
+    const bool need = (k < 0) && !drained;
+    if (__any_sync(FULL_MASK, need)) {
+      const long long got = warp_ticket(a.work, need);
+      if (need) {
+        if (got < n) {
+          k = got;
+          const long long hd = a.head[k];
+          if (a.status[k] != TRAJ_OK || hd < 0) {
+            write_nan<NP, D>(a, k);
+            k = -1;  // take another ticket next iteration
+          } else {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) p[q] = (R)a.params[q * n + k];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              lam[c] = R(0);
+              yfin[c] = (R)a.y_final[c * n + k];
+            }
+            pacc.zero();
+            loss = 0.0;
+            seg = hd;
+            const int Sk = a.S[k];
+            m = Sk - ((Sk - 1) / a.k) * a.k;  // steps in the last segment
+            segs_left = (Sk + a.k - 1) / a.k;
+            final_seg = true;
+            phase = PH_LOAD;
+            js = ns - 1;
+          }
+        } else {
+          drained = true;
+        }
+      }
+    }
+    if (!__any_sync(FULL_MASK, k >= 0 || !drained)) break;
+
+    // Advance this lane to its next unit of work.
+    int mode = U_NONE, us = 0;
+    R ux[D];
+    double uh = 0.0;
+    if (k >= 0) {
+      for (;;) {
+        if (phase == PH_LOAD) {
+          if (seg < 0 || seg >= a.arena_cap || segs_left <= 0) {  // inconsistent record: stop this lane
+            mode = U_FAIL;
+            break;
+          }
+          --segs_left;
+          const double2* src = reinterpret_cast<const double2*>(a.arena + seg * a.segw);
+          const double2 w0 = src[0];
+          prevseg = __double_as_longlong(w0.x);
+          ts[0] = w0.y;
+          // y_start at [2, 2+D), h at [2+D, 2+D+m)
+          for (int w = 1; w < (a.segw >> 1); ++w) {
+            const double2 v = src[w];
+            const int i0 = 2 * w, i1 = 2 * w + 1;
+            if (i0 < 2 + D) ys[0][i0 - 2] = (R)v.x; else if (i0 - 2 - D < m) hs[i0 - 2 - D] = v.x;
+            if (i1 < 2 + D) ys[0][i1 - 2] = (R)v.y; else if (i1 - 2 - D < m) hs[i1 - 2 - D] = v.y;
+          }
+          rj = 1;
+          phase = PH_RECOMP;
+        }
+        if (phase == PH_RECOMP) {
+          if (rj < m) {
+            mode = U_RECOMP;
+#pragma unroll
+            for (int c = 0; c < D; ++c) ux[c] = ys[rj - 1][c];
+            uh = hs[rj - 1];
+            break;
+          }
+          j = m;
+          phase = PH_INJECT;
+        }
+        // saves at state j of this segment (state m only in the final segment: y(t1))
+        if (j < m || final_seg) {
+          const double tj = (j == m) ? a.t1 : ts[j];
+          R yj[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) yj[c] = (j == m) ? yfin[c] : ys[j][c];
+          if (next_save<D, R, USER_COT>(a, s_save, k, js, tj, yj, lam, loss, us)) {
+            mode = U_SIDE;
+#pragma unroll
+            for (int c = 0; c < D; ++c) ux[c] = yj[c];
+            uh = s_save[us] - tj;
+            break;
+          }
+        }
+        if (j > 0) {
+          mode = U_STEP;
+#pragma unroll
+          for (int c = 0; c < D; ++c) ux[c] = ys[j - 1][c];
+          uh = hs[j - 1];
+          --j;
+          break;
+        }
+        if (prevseg < 0) {
+          mode = (segs_left == 0) ? U_DONE : U_FAIL;
+          break;
+        }
+        seg = prevseg;
+        m = a.k;
+        final_seg = false;
+        phase = PH_LOAD;
+      }
+    }
+
+    __syncwarp();
+    if (mode == U_RECOMP || mode == U_STEP || mode == U_SIDE) {
+      R yn[D];
+      const bool ok = M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, us, ux, uh, p, lam, pacc, loss, yn);
+      if (!ok) {
+        mode = U_FAIL;
+      } else if (mode == U_RECOMP) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) ys[rj][c] = yn[c];
+        ts[rj] = add_(ts[rj - 1], hs[rj - 1]);
+        ++rj;
+      }
+    }
+    if (mode == U_FAIL) {
+      write_nan<NP, D>(a, k);
+      k = -1;
+    }
+    if (mode == U_DONE) {
+      write_grad<NP, D, R>(a, k, pacc, lam, loss);
+      k = -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse kernel, every accepted state stored (checkpoint interval k = 1).
+//
+// Segment i holds (t_{i-1}, y_{i-1}, h_i): nothing is recomputed, and every
+// unit is a VJP with the same code, either the step-i VJP from y_{i-1} or a
+// save-time side-step VJP from a mesh state. Per trajectory: the saves at
+// state S (y(t1)); then for i = S..1: load segment i, step VJP, the saves
+// attached to state i-1.
+// ---------------------------------------------------------------------------
+template <class M, class Pb, class R, bool USER_COT>
+__global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
+  constexpr int D = Pb::D, NP = Pb::NP;
+  using Acc = AccOf<R, NP>;
+  extern __shared__ double smem[];
+  const int ns = a.n_save;
+  double* s_save = smem;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
+  __syncthreads();
+
+  const long long n = a.n;
+  long long k = -1;
+  bool drained = false;
+  R p[NP], lam[D], yx[D];  // yx: the mesh state the next unit starts from
+  Acc pacc;
+  double loss = 0.0, tx = 0.0;
+  long long seg = -1;
+  int js = -1, segs_left = 0;
+
+  for (;;) {
+    const bool need = (k < 0) && !drained;
+    if (__any_sync(FULL_MASK, need)) {
+      const long long got = warp_ticket(a.work, need);
+      if (need) {
+        if (got < n) {
+          k = got;
+          const long long hd = a.head[k];
+          if (a.status[k] != TRAJ_OK || hd < 0) {
+            write_nan<NP, D>(a, k);
+            k = -1;
+          } else {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) p[q] = (R)a.params[q * n + k];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              lam[c] = R(0);
+              yx[c] = (R)a.y_final[c * n + k];
+            }
+            pacc.zero();
+            loss = 0.0;
+            tx = a.t1;
+            seg = hd;
+            segs_left = a.S[k];
+            js = ns - 1;
+          }
+        } else {
+          drained = true;
+        }
+      }
+    }
+    if (!__any_sync(FULL_MASK, k >= 0 || !drained)) break;
+
+    int mode = U_NONE, us = 0;
+    double uh = 0.0;
+    if (k >= 0) {
+      if (next_save<D, R, USER_COT>(a, s_save, k, js, tx, yx, lam, loss, us)) {
+        mode = U_SIDE;
+        uh = s_save[us] - tx;
+      } else if (seg < 0) {
+        mode = (segs_left == 0) ? U_DONE : U_FAIL;
+      } else if (seg >= a.arena_cap || segs_left <= 0) {
+        mode = U_FAIL;  // inconsistent record
+      } else {
+        // segment i: [prev, t_{i-1}, y_{i-1}[D], h_i]
+        const double* sp = a.arena + seg * a.segw;
+        const double2 w0 = *reinterpret_cast<const double2*>(sp);
+        seg = __double_as_longlong(w0.x);
+        tx = w0.y;
+#pragma unroll
+        for (int c = 0; c < D; ++c) yx[c] = (R)sp[2 + c];
+        uh = sp[2 + D];
+        --segs_left;
+        mode = U_STEP;
+      }
+    }
+
+    __syncwarp();
+    if (mode == U_STEP || mode == U_SIDE) {
+      R yn[D];
+      if (!M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, us, yx, uh, p, lam, pacc, loss, yn)) mode = U_FAIL;
+    }
+    if (mode == U_FAIL) {
+      write_nan<NP, D>(a, k);
+      k = -1;
+    }
+    if (mode == U_DONE) {
+      write_grad<NP, D, R>(a, k, pacc, lam, loss);
+      k = -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+inline int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// Persistent grid: as many CTAs as fit on the SMs at once (no more than the
+// ensemble needs).
+template <class Kern>
+inline cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long n, cudaStream_t s,
+                                     const void* args_ptr) {
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int bps = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, tpb, smem);
+  if (err != cudaSuccess) return err;
+  long long blocks = (long long)sm_count() * (bps > 0 ? bps : 1);
+  const long long need = (n + tpb - 1) / tpb;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {const_cast<void*>(args_ptr)};
+  return cudaLaunchKernel((const void*)kern, dim3((unsigned)blocks), dim3(tpb), args, smem, s);
+}
+
+template <class M, class Pb, class R>
+inline cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)(((a.n_save + 1) & ~1) + a.segw * TPB_FWD) * sizeof(double);
+  if (a.y_save) return persistent_launch(record_kernel<M, Pb, R, true>, TPB_FWD, smem, a.n, s, &a);
+  return persistent_launch(record_kernel<M, Pb, R, false>, TPB_FWD, smem, a.n, s, &a);
+}
+
+template <class M, class Pb, class R>
+inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)((a.n_save + 1) & ~1) * sizeof(double);
+  if (a.k == 1) {
+    if (a.y_save_bar) return persistent_launch(reverse_k1_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a);
+    return persistent_launch(reverse_k1_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);
+  }
+  if (a.y_save_bar) return persistent_launch(reverse_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a);
+  return persistent_launch(reverse_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);
+}
+
+}  // namespace gs

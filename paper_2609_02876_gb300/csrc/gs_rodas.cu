@@ -1,0 +1,32 @@
+// Rodas5P (stiff) instantiations of the record and reverse-sweep kernels:
+// Robertson, HIRES and the linear test problem, FP64 (the W-matrix LU and its
+// solves are FP64 in every precision mode).
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+bool rodas_supports(int problem, int precision) {
+  return (problem == 2 || problem == 3 || problem == 4) && precision == 0;
+}
+
+cudaError_t launch_rodas_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s) {
+  if (precision != 0) return cudaErrorInvalidValue;
+  switch (problem) {
+    case 2: return fwd_dispatch<Rodas5PMethod, Robertson, double>(a, s);
+    case 3: return fwd_dispatch<Rodas5PMethod, Hires, double>(a, s);
+    case 4: return fwd_dispatch<Rodas5PMethod, Linear2, double>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rodas_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s) {
+  if (precision != 0) return cudaErrorInvalidValue;
+  switch (problem) {
+    case 2: return rev_dispatch<Rodas5PMethod, Robertson, double>(a, s);
+    case 3: return rev_dispatch<Rodas5PMethod, Hires, double>(a, s);
+    case 4: return rev_dispatch<Rodas5PMethod, Linear2, double>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gs

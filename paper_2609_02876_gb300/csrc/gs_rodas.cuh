@@ -1,0 +1,272 @@
+// Rodas5P (Steinebach 2023): the stiff one-step map of the paper's Sec. 3.2,
+// its per-lane dense LU, and the discrete adjoint of one step.
+//
+// Transformed Rosenbrock form, with W = I/(h gamma) - J(y):
+//   W U_i = f(y + sum_{j<i} a_ij U_j) + (1/h) sum_{j<i} C_ij U_j,  i = 1..8,
+//   y_new = y + sum_j m_j U_j,
+// stiffly accurate: rows 7 and 8 of a extend row 6 by ones and m = (a_8., 1),
+// so y_new = Y_8 + U_8 and the embedded solution is Y_8 = y_new - U_8 (error
+// estimate U_8). All problems here are autonomous (no df/dt term).
+#pragma once
+
+#include "gs_device.cuh"
+
+namespace gs {
+namespace rodas {
+
+constexpr double GAMMA = 0.21193756319429014;
+
+__host__ __device__ constexpr double A6(int j) {  // row 6 (1-based), extended into rows 7 and 8
+  return j == 0   ? -7.502846399306121
+         : j == 1 ? 2.561846144803919
+         : j == 2 ? -11.627539656261098
+         : j == 3 ? -0.18268767659942256
+         : j == 4 ? 0.030198172008377946
+                  : 0.0;
+}
+// a_ij, 0-based stage i (1..7), j < i.
+__host__ __device__ constexpr double a(int i, int j) {
+  return (i == 1 && j == 0)   ? 3.0
+         : (i == 2 && j == 0) ? 2.849394379747939
+         : (i == 2 && j == 1) ? 0.45842242204463923
+         : (i == 3 && j == 0) ? -6.954028509809101
+         : (i == 3 && j == 1) ? 2.489845061869568
+         : (i == 3 && j == 2) ? -10.358996098473584
+         : (i == 4 && j == 0) ? 2.8029986275628964
+         : (i == 4 && j == 1) ? 0.5072464736228206
+         : (i == 4 && j == 2) ? -0.3988312541770524
+         : (i == 4 && j == 3) ? -0.04721187230404641
+         : (i == 5 && j < 5)  ? A6(j)
+         : (i == 6 && j < 5)  ? A6(j)
+         : (i == 6 && j == 5) ? 1.0
+         : (i == 7 && j < 5)  ? A6(j)
+         : (i == 7 && j == 5) ? 1.0
+         : (i == 7 && j == 6) ? 1.0
+                              : 0.0;
+}
+__host__ __device__ constexpr double C(int i, int j) {
+  return (i == 1 && j == 0)   ? -14.155112264123755
+         : (i == 2 && j == 0) ? -17.97296035885952
+         : (i == 2 && j == 1) ? -2.859693295451294
+         : (i == 3 && j == 0) ? 147.12150275711716
+         : (i == 3 && j == 1) ? -1.41221402718213
+         : (i == 3 && j == 2) ? 71.68940251302358
+         : (i == 4 && j == 0) ? 165.43517024871676
+         : (i == 4 && j == 1) ? -0.4592823456491126
+         : (i == 4 && j == 2) ? 42.90938336958603
+         : (i == 4 && j == 3) ? -5.961986721573306
+         : (i == 5 && j == 0) ? 24.854864614690072
+         : (i == 5 && j == 1) ? -3.0009227002832186
+         : (i == 5 && j == 2) ? 47.4931110020768
+         : (i == 5 && j == 3) ? 5.5814197821558125
+         : (i == 5 && j == 4) ? -0.6610691825249471
+         : (i == 6 && j == 0) ? 30.91273214028599
+         : (i == 6 && j == 1) ? -3.1208243349937974
+         : (i == 6 && j == 2) ? 77.79954646070892
+         : (i == 6 && j == 3) ? 34.28646028294783
+         : (i == 6 && j == 4) ? -19.097331116725623
+         : (i == 6 && j == 5) ? -28.087943162872662
+         : (i == 7 && j == 0) ? 37.80277123390563
+         : (i == 7 && j == 1) ? -3.2571969029072276
+         : (i == 7 && j == 2) ? 112.26918849496327
+         : (i == 7 && j == 3) ? 66.9347231244047
+         : (i == 7 && j == 4) ? -40.06618937091002
+         : (i == 7 && j == 5) ? -54.66780262877968
+         : (i == 7 && j == 6) ? -9.48861652309627
+                              : 0.0;
+}
+__host__ __device__ constexpr double m(int j) { return j < 7 ? a(7, j) : 1.0; }
+
+}  // namespace rodas
+
+// ---------------------------------------------------------------------------
+// Dense LU with partial pivoting (Doolittle; ties pick the lowest row index),
+// fully unrolled and branch-free: row swaps are selects, so the matrix stays
+// in registers. piv[k] is the row swapped with row k at column k; rinv[k] is
+// 1 / U_kk. Returns false on an exactly zero pivot.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ bool lu_factor(double (&A)[D][D], int (&piv)[D], double (&rinv)[D]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    int pr = k;
+    double best = fabs(A[k][k]);
+#pragma unroll
+    for (int i = k + 1; i < D; ++i) {
+      const double v = fabs(A[i][k]);
+      const bool gt = v > best;
+      best = gt ? v : best;
+      pr = gt ? i : pr;
+    }
+    piv[k] = pr;
+    ok = ok && (best != 0.0);
+#pragma unroll
+    for (int i = k + 1; i < D; ++i) {
+      const bool sw = (i == pr);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const double t = A[k][j];
+        A[k][j] = sw ? A[i][j] : t;
+        A[i][j] = sw ? t : A[i][j];
+      }
+    }
+    rinv[k] = 1.0 / A[k][k];
+#pragma unroll
+    for (int i = k + 1; i < D; ++i) {
+      const double l = mul_(A[i][k], rinv[k]);
+      A[i][k] = l;
+#pragma unroll
+      for (int j = k + 1; j < D; ++j) A[i][j] = fma_(-l, A[k][j], A[i][j]);
+    }
+  }
+  return ok;
+}
+
+// Solve W x = b with the factors (apply the row swaps, then L and U).
+template <int D>
+__device__ __forceinline__ void lu_solve(const double (&LU)[D][D], const int (&piv)[D], const double (&rinv)[D],
+                                         const double (&b)[D], double (&x)[D]) {
+  double z[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) z[i] = b[i];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int i = k + 1; i < D; ++i) {
+      const bool sw = (i == piv[k]);
+      const double t = z[k];
+      z[k] = sw ? z[i] : t;
+      z[i] = sw ? t : z[i];
+    }
+  }
+#pragma unroll
+  for (int i = 1; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) z[i] = fma_(-LU[i][j], z[j], z[i]);
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i) {
+    double s = z[i];
+#pragma unroll
+    for (int j = i + 1; j < D; ++j) s = fma_(-LU[i][j], x[j], s);
+    x[i] = mul_(s, rinv[i]);
+  }
+}
+
+// Solve W^T x = b: U^T w = b, L^T v = w, then undo the row swaps in reverse.
+template <int D>
+__device__ __forceinline__ void lu_solve_t(const double (&LU)[D][D], const int (&piv)[D], const double (&rinv)[D],
+                                           const double (&b)[D], double (&x)[D]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = b[i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) s = fma_(-LU[j][i], x[j], s);
+    x[i] = mul_(s, rinv[i]);
+  }
+#pragma unroll
+  for (int i = D - 2; i >= 0; --i)
+#pragma unroll
+    for (int j = i + 1; j < D; ++j) x[i] = fma_(-LU[j][i], x[j], x[i]);
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) {
+#pragma unroll
+    for (int i = k + 1; i < D; ++i) {
+      const bool sw = (i == piv[k]);
+      const double t = x[k];
+      x[k] = sw ? x[i] : t;
+      x[i] = sw ? t : x[i];
+    }
+  }
+}
+
+// One Rodas5P step from y with size h: stage inputs Y[0..7], stage solutions
+// U[0..7], the LU of W, y_new and the error estimate U[7]. false if W is singular.
+template <class Pb>
+__device__ __forceinline__ bool rodas_step(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
+                                           double (&Y)[8][Pb::D], double (&U)[8][Pb::D], double (&LU)[Pb::D][Pb::D],
+                                           int (&piv)[Pb::D], double (&rinv)[Pb::D], double (&ynew)[Pb::D]) {
+  constexpr int D = Pb::D;
+  Pb::jac(y, p, LU);
+  const double inv_hg = 1.0 / mul_(h, rodas::GAMMA);
+  const double inv_h = 1.0 / h;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) LU[i][j] = -LU[i][j];
+    LU[i][i] = add_(LU[i][i], inv_hg);
+  }
+  const bool ok = lu_factor<D>(LU, piv, rinv);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    double F[D], Rhs[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double s = y[c];
+#pragma unroll
+      for (int j = 0; j < i; ++j) s = fma_(rodas::a(i, j), U[j][c], s);
+      Y[i][c] = s;
+    }
+    Pb::f(Y[i], p, F);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      if (i == 0) {
+        Rhs[c] = F[c];
+      } else {
+        double s = mul_(rodas::C(i, 0), U[0][c]);
+#pragma unroll
+        for (int j = 1; j < i; ++j) s = fma_(rodas::C(i, j), U[j][c], s);
+        Rhs[c] = fma_(inv_h, s, F[c]);
+      }
+    }
+    lu_solve<D>(LU, piv, rinv, Rhs, U[i]);
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) ynew[c] = add_(Y[7][c], U[7][c]);
+  return ok;
+}
+
+// Reverse of one Rodas5P step (h held as data) over its recomputed stages:
+// given the cotangent lam of y_new, returns v = dL/dy and accumulates dL/dtheta.
+//   Ubar_j = m_j lam;  for i = 8..1: Rbar_i = W^{-T} Ubar_i,
+//   Ubar_j += (C_ij / h) Rbar_i, Ybar_i = J(Y_i)^T Rbar_i, theta_bar += f_theta(Y_i)^T Rbar_i,
+//   v += Ybar_i, Ubar_j += a_ij Ybar_i;
+// and W = I/(h gamma) - J(y) gives dL/dJ = sum_i Rbar_i U_i^T, contracted through
+// J(y, theta): v += d/dy (Rbar_i^T J U_i), theta_bar += d/dtheta (Rbar_i^T J U_i).
+template <class Pb, class Acc>
+__device__ __forceinline__ void rodas_reverse(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
+                                              const double (&Y)[8][Pb::D], const double (&U)[8][Pb::D],
+                                              const double (&LU)[Pb::D][Pb::D], const int (&piv)[Pb::D],
+                                              const double (&rinv)[Pb::D], const double (&lam)[Pb::D],
+                                              double (&v)[Pb::D], Acc& pacc) {
+  constexpr int D = Pb::D;
+  const double inv_h = 1.0 / h;
+  double Ub[8][D];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < D; ++c) Ub[j][c] = (j == 7) ? lam[c] : mul_(rodas::m(j), lam[c]);
+#pragma unroll
+  for (int c = 0; c < D; ++c) v[c] = lam[c];
+#pragma unroll
+  for (int i = 7; i >= 0; --i) {
+    double Rb[D], Yb[D], Rh[D];
+    lu_solve_t<D>(LU, piv, rinv, Ub[i], Rb);
+#pragma unroll
+    for (int c = 0; c < D; ++c) Rh[c] = mul_(inv_h, Rb[c]);
+#pragma unroll
+    for (int j = 0; j < i; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c) Ub[j][c] = fma_(rodas::C(i, j), Rh[c], Ub[j][c]);
+    pacc.template vjp<Pb>(Y[i], p, Rb, Yb);
+#pragma unroll
+    for (int c = 0; c < D; ++c) v[c] = add_(v[c], Yb[c]);
+#pragma unroll
+    for (int j = 0; j < i; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c) Ub[j][c] = fma_(rodas::a(i, j), Yb[c], Ub[j][c]);
+    pacc.template jac_contract<Pb>(y, p, Rb, U[i], v);
+  }
+}
+
+}  // namespace gs

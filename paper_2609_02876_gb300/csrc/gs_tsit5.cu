@@ -1,613 +1,8 @@
-// Tsit5 record and reverse-sweep kernels (non-stiff problems).
-//
-// Both kernels are persistent: a grid of resident CTAs whose lanes each own one
-// trajectory at a time and take the next one from a global ticket counter
-// (one atomic per warp per refill) as soon as theirs finishes, so a lane never
-// waits for a slower neighbour's trajectory to end. Each loop iteration first
-// does the lane's bookkeeping (refill, record write-out, the walk through its
-// record), then meets the warp at a __syncwarp and runs one unit of solver
-// arithmetic written as a single branch-free block, so the FP64 / FP32 work of
-// all busy lanes issues together whatever phase their trajectories are in.
-//
-// Record (paper Sec. 3.1, map R): the adaptive loop of Sec. 2.1 with FSAL, the
-// weighted RMS error test and an integral controller. Accepted step sizes are
-// staged per lane in shared memory and written out as fixed-size record
-// segments [prev, t_start, y_start[d], h[k]] (one vector-stored segment per k
-// accepted steps) allocated from a device arena.
-//
-// Reverse (paper Sec. 3.1, discrete adjoint of Eq. (replay)): each lane walks
-// its trajectory's segments last to first and runs one unit per iteration: a
-// state recompute inside a segment (k > 1 only), a step VJP
-// (lambda_{i-1} = dPhi/dy^T lambda_i), or a save-time side-step VJP
-// (lambda_i += dPhi/dy^T ybar_s).
-#include <type_traits>
-
-#include "gs_device.cuh"
-#include "gs_internal.h"
+// Tsit5 (non-stiff) instantiations of the record and reverse-sweep kernels:
+// Lorenz, Van der Pol and the linear test problem, FP64 and FP32-mixed.
+#include "gs_kernels.cuh"
 
 namespace gs {
-
-constexpr int TPB_FWD = 128;
-constexpr int TPB_REV = 128;
-
-__device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
-
-// ---------------------------------------------------------------------------
-// Record kernel
-// ---------------------------------------------------------------------------
-template <class Pb, class R, bool SAVES>
-__global__ void __launch_bounds__(TPB_FWD) tsit5_record_kernel(const FwdArgs a) {
-  constexpr int D = Pb::D, NP = Pb::NP;
-  extern __shared__ double smem[];
-  const int ns = a.n_save;
-  double* s_save = smem;
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
-  const int TB = blockDim.x;
-  double* stg = smem + ((ns + 1) & ~1) + threadIdx.x;  // this lane's segment staging, stride TB
-  __syncthreads();
-
-  const long long n = a.n;
-  const double t1 = a.t1;
-  const double sliver = 1e-12 * fmax(1.0, fabs(t1));
-  long long k = -1;
-  bool drained = false;
-  double t = 0.0, h = 0.0;
-  R y[D], k1[D], p[NP];
-  int S = 0, natt = 0, slot = 0, js = 0, status = TRAJ_OK;
-  bool rej = false, lastnf = false, pending_fail = false;
-  long long prev = -1;
-
-  for (;;) {
-    // ---- refill: lanes without a trajectory take the next ticket
-    const bool need = (k < 0) && !drained;
-    if (__any_sync(FULL_MASK, need)) {
-      const long long got = warp_ticket(a.work, need);
-      if (need) {
-        if (got < n) {
-          k = got;
-          bool fin = true;
-          float yf[D], pf[NP], ff[D];
-#pragma unroll
-          for (int q = 0; q < NP; ++q) {
-            const double v = a.params[q * n + k];
-            p[q] = (R)v;
-            pf[q] = (float)v;
-            fin = fin && isfinite(v);
-          }
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            const double v = a.y0[c * n + k];
-            y[c] = (R)v;
-            yf[c] = (float)v;
-            fin = fin && isfinite(v);
-          }
-          t = a.t0;
-          S = natt = slot = js = 0;
-          status = TRAJ_OK;
-          rej = lastnf = false;
-          prev = -1;
-          Pb::f(y, p, k1);
-#pragma unroll
-          for (int c = 0; c < D; ++c) ff[c] = (float)k1[c];
-          h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
-          fin = fin && isfinite(h) && h > 0.0;
-          pending_fail = !fin;
-          if (!fin) status = TRAJ_NONFINITE;
-          stg[1 * TB] = t;
-#pragma unroll
-          for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = (double)y[c];
-        } else {
-          drained = true;
-        }
-      }
-    }
-    if (!__any_sync(FULL_MASK, k >= 0)) break;
-
-    bool done = false;
-    if (k >= 0 && pending_fail) done = true;
-    if (k >= 0 && !pending_fail && natt >= a.max_steps) {
-      status = TRAJ_MAXSTEPS;
-      done = true;
-    }
-    const bool trial = (k >= 0) && !done;
-    bool last = false;
-    if (trial && t + h >= t1 - sliver) {
-      h = t1 - t;
-      last = true;
-    }
-
-    // ---- one trial step (all lanes with a live trajectory, one code path)
-    __syncwarp();
-    R Y[7][D], K[7][D];
-    double q = 2.0;
-    if (trial) {
-      ++natt;
-      const R hr = (R)h;
-#pragma unroll
-      for (int c = 0; c < D; ++c) K[0][c] = k1[c];
-      tsit5_stages<Pb, R, 7>(y, p, hr, Y, K);
-      R e[D];
-      tsit5_error<Pb, R>(K, hr, e);
-      q = err_meansq<D>(e, y, Y[6], a.rtol, a.atol);
-    }
-    const bool accept = trial && (q <= 1.0);  // NaN rejects
-    double tn = 0.0;
-    if (accept) {
-      tn = last ? t1 : add_(t, h);
-      if (SAVES) {
-        // save times in [t, tn): one extra step from y; exactly tn: y_new
-        while (js < ns && s_save[js] < tn) {
-          const double hs = s_save[js] - t;
-          R Ys[7][D], Ks[7][D];
-#pragma unroll
-          for (int c = 0; c < D; ++c) Ks[0][c] = k1[c];
-          if (hs == 0.0) {
-#pragma unroll
-            for (int c = 0; c < D; ++c) Ys[6][c] = y[c];
-          } else {
-            tsit5_stages<Pb, R, 6>(y, p, (R)hs, Ys, Ks);
-          }
-#pragma unroll
-          for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = (double)Ys[6][c];
-          ++js;
-        }
-        while (js < ns && s_save[js] == tn) {
-#pragma unroll
-          for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = (double)Y[6][c];
-          ++js;
-        }
-      }
-      stg[(2 + D + slot) * TB] = h;
-      ++slot;
-      t = tn;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        y[c] = Y[6][c];
-        k1[c] = K[6][c];
-      }
-      ++S;
-      if (last) done = true;
-    }
-    if (trial && !done) {
-      // integral controller: accepted steps grow at most x10 (x1 right after a
-      // rejection); rejected ones shrink by the same rule, x0.2 on a non-finite error
-      const bool nf = !isfinite(q);
-      double fac = nf ? 0.2 : ctrl_factor(q);
-      if (accept && rej) fac = fmin(fac, 1.0);
-      h = mul_(h, fac);
-      rej = !accept;
-      lastnf = !accept && nf;
-      if (fabs(h) < 1e-14 * fmax(1.0, fabs(t))) {
-        status = lastnf ? TRAJ_NONFINITE : TRAJ_DT_UNDERFLOW;
-        done = true;
-      }
-    }
-    const bool flush = (k >= 0) && ((slot == a.k) || (done && slot > 0));
-
-    // ---- segment write-out: one arena slot per flushing lane, one atomic per warp
-    if (__any_sync(FULL_MASK, flush)) {
-      const long long idx = warp_ticket(a.arena_top, flush);
-      if (flush) {
-        stg[0] = __longlong_as_double(prev);
-        if (idx < a.arena_cap) {
-          double2* dst = reinterpret_cast<double2*>(a.arena + idx * a.segw);
-          for (int w = 0; w < (a.segw >> 1); ++w) dst[w] = make_double2(stg[(2 * w) * TB], stg[(2 * w + 1) * TB]);
-        } else {
-          *a.overflow = 1;
-        }
-        prev = idx;
-        slot = 0;
-        stg[1 * TB] = t;
-#pragma unroll
-        for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = (double)y[c];
-      }
-    }
-
-    if (done) {
-      a.head[k] = prev;
-      a.S[k] = S;
-      a.natt[k] = natt;
-      a.status[k] = status;
-#pragma unroll
-      for (int c = 0; c < D; ++c) a.y_final[c * n + k] = (double)y[c];
-      if (a.step_counts) {
-        a.step_counts[k] = S;
-        a.step_counts[n + k] = natt;
-      }
-      if (status != TRAJ_OK) *a.any_failed = 1;
-      k = -1;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// The reverse unit: stages of one Tsit5 step from x with size h, then (unless
-// the unit only recomputes a state) the step's VJP with cotangent `side ? the
-// save-time cotangent : lambda`. A step unit replaces lambda, a side unit adds
-// to it. Returns y_new (the recomputed state, or the side step's y(t_s)).
-// ---------------------------------------------------------------------------
-enum : int { U_NONE = 0, U_RECOMP = 1, U_STEP = 2, U_SIDE = 3, U_DONE = 4, U_FAIL = 5 };
-
-template <class Pb, class R, bool USER_COT, class Acc>
-__device__ __forceinline__ void reverse_unit(const RevArgs& a, long long k, int mode, int us, const R (&x)[Pb::D],
-                                             double h, const R (&p)[Pb::NP], R (&lam)[Pb::D], Acc& pacc,
-                                             double& loss, R (&ynew)[Pb::D]) {
-  constexpr int D = Pb::D;
-  R Y[7][D], K[7][D];
-  Pb::f(x, p, K[0]);
-  tsit5_stages<Pb, R, 6>(x, p, (R)h, Y, K);
-#pragma unroll
-  for (int c = 0; c < D; ++c) ynew[c] = Y[6][c];
-  if (mode == U_RECOMP) return;
-  const bool side = (mode == U_SIDE);
-  R cv[D], v[D];
-  double l2 = 0.0;
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    R cs;
-    if (USER_COT) {
-      cs = (R)a.y_save_bar[((long long)us * D + c) * a.n + k];
-    } else {
-      cs = add_(Y[6][c], Y[6][c]);  // d/dy of ||y||^2
-      l2 = fma_((double)Y[6][c], (double)Y[6][c], l2);
-    }
-    cv[c] = side ? cs : lam[c];
-  }
-  if (!USER_COT && side) loss = add_(loss, l2);
-  tsit5_reverse<Pb, R>(Y, p, (R)h, cv, v, pacc);
-#pragma unroll
-  for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
-}
-
-template <int NP, int D>
-__device__ __forceinline__ void write_nan(const RevArgs& a, long long k) {
-  const long long n = a.n;
-  if (a.params_bar)
-    for (int q = 0; q < NP; ++q) a.params_bar[q * n + k] = nan_d();
-  if (a.y0_bar)
-    for (int c = 0; c < D; ++c) a.y0_bar[c * n + k] = nan_d();
-  if (a.loss) a.loss[k] = nan_d();
-}
-
-// Save times attached to the state (tx, yx), visited in decreasing order:
-// equal times add their cotangent to lambda directly; a later time is a side
-// step from the state (returns true with its save index in us).
-template <int D, class R, bool USER_COT>
-__device__ __forceinline__ bool next_save(const RevArgs& a, const double* s_save, long long k, int& js, double tx,
-                                          const R (&yx)[D], R (&lam)[D], double& loss, int& us) {
-  while (js >= 0 && s_save[js] >= tx) {
-    if (s_save[js] == tx) {
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        if (USER_COT) {
-          lam[c] = add_(lam[c], (R)a.y_save_bar[((long long)js * D + c) * a.n + k]);
-        } else {
-          lam[c] = add_(lam[c], add_(yx[c], yx[c]));
-          loss = fma_((double)yx[c], (double)yx[c], loss);
-        }
-      }
-      --js;
-    } else {
-      us = js;
-      --js;
-      return true;
-    }
-  }
-  return false;
-}
-
-// ---------------------------------------------------------------------------
-// Reverse kernel, checkpoint interval k > 1: states inside a segment are
-// recomputed from its checkpoint into a per-lane buffer (local memory).
-// ---------------------------------------------------------------------------
-enum : int { PH_LOAD = 0, PH_RECOMP = 1, PH_INJECT = 2 };
-
-template <class Pb, class R, bool USER_COT>
-__global__ void __launch_bounds__(TPB_REV) tsit5_reverse_kernel(const RevArgs a) {
-  constexpr int D = Pb::D, NP = Pb::NP;
-  using Acc = typename std::conditional<std::is_same<R, float>::value, CompensatedAcc<NP>, PlainAcc<NP>>::type;
-  extern __shared__ double smem[];
-  const int ns = a.n_save;
-  double* s_save = smem;
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
-  __syncthreads();
-
-  const long long n = a.n;
-  long long k = -1;
-  bool drained = false;
-  R p[NP], lam[D], yfin[D];
-  Acc pacc;
-  double loss = 0.0;
-  long long seg = -1, prevseg = -1;
-  int m = 0, j = 0, rj = 0, js = -1, phase = PH_LOAD, segs_left = 0;
-  bool final_seg = true;
-  double ts[KMAX], hs[KMAX];
-  R ys[KMAX][D];
-
-  for (;;) {
-    const bool need = (k < 0) && !drained;
-    if (__any_sync(FULL_MASK, need)) {
-      const long long got = warp_ticket(a.work, need);
-      if (need) {
-        if (got < n) {
-          k = got;
-          const long long hd = a.head[k];
-          if (a.status[k] != TRAJ_OK || hd < 0) {
-            write_nan<NP, D>(a, k);
-            k = -1;  // take another ticket next iteration
-          } else {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) p[q] = (R)a.params[q * n + k];
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-              lam[c] = R(0);
-              yfin[c] = (R)a.y_final[c * n + k];
-            }
-            pacc.zero();
-            loss = 0.0;
-            seg = hd;
-            const int Sk = a.S[k];
-            m = Sk - ((Sk - 1) / a.k) * a.k;  // steps in the last segment
-            segs_left = (Sk + a.k - 1) / a.k;
-            final_seg = true;
-            phase = PH_LOAD;
-            js = ns - 1;
-          }
-        } else {
-          drained = true;
-        }
-      }
-    }
-    if (!__any_sync(FULL_MASK, k >= 0 || !drained)) break;
-
-    // Advance this lane to its next unit of work.
-    int mode = U_NONE, us = 0;
-    R ux[D];
-    double uh = 0.0;
-    if (k >= 0) {
-      for (;;) {
-        if (phase == PH_LOAD) {
-          if (seg < 0 || seg >= a.arena_cap || segs_left <= 0) {  // inconsistent record: stop this lane
-            mode = U_FAIL;
-            break;
-          }
-          --segs_left;
-          const double2* src = reinterpret_cast<const double2*>(a.arena + seg * a.segw);
-          const double2 w0 = src[0];
-          prevseg = __double_as_longlong(w0.x);
-          ts[0] = w0.y;
-          // y_start at [2, 2+D), h at [2+D, 2+D+m)
-          for (int w = 1; w < (a.segw >> 1); ++w) {
-            const double2 v = src[w];
-            const int i0 = 2 * w, i1 = 2 * w + 1;
-            if (i0 < 2 + D) ys[0][i0 - 2] = (R)v.x; else if (i0 - 2 - D < m) hs[i0 - 2 - D] = v.x;
-            if (i1 < 2 + D) ys[0][i1 - 2] = (R)v.y; else if (i1 - 2 - D < m) hs[i1 - 2 - D] = v.y;
-          }
-          rj = 1;
-          phase = PH_RECOMP;
-        }
-        if (phase == PH_RECOMP) {
-          if (rj < m) {
-            mode = U_RECOMP;
-#pragma unroll
-            for (int c = 0; c < D; ++c) ux[c] = ys[rj - 1][c];
-            uh = hs[rj - 1];
-            break;
-          }
-          j = m;
-          phase = PH_INJECT;
-        }
-        // saves at state j of this segment (state m only in the final segment: y(t1))
-        if (j < m || final_seg) {
-          const double tj = (j == m) ? a.t1 : ts[j];
-          R yj[D];
-#pragma unroll
-          for (int c = 0; c < D; ++c) yj[c] = (j == m) ? yfin[c] : ys[j][c];
-          if (next_save<D, R, USER_COT>(a, s_save, k, js, tj, yj, lam, loss, us)) {
-            mode = U_SIDE;
-#pragma unroll
-            for (int c = 0; c < D; ++c) ux[c] = yj[c];
-            uh = s_save[us] - tj;
-            break;
-          }
-        }
-        if (j > 0) {
-          mode = U_STEP;
-#pragma unroll
-          for (int c = 0; c < D; ++c) ux[c] = ys[j - 1][c];
-          uh = hs[j - 1];
-          --j;
-          break;
-        }
-        if (prevseg < 0) {
-          mode = (segs_left == 0) ? U_DONE : U_FAIL;
-          break;
-        }
-        seg = prevseg;
-        m = a.k;
-        final_seg = false;
-        phase = PH_LOAD;
-      }
-    }
-
-    __syncwarp();
-    if (mode == U_RECOMP || mode == U_STEP || mode == U_SIDE) {
-      R yn[D];
-      reverse_unit<Pb, R, USER_COT>(a, k, mode, us, ux, uh, p, lam, pacc, loss, yn);
-      if (mode == U_RECOMP) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) ys[rj][c] = yn[c];
-        ts[rj] = add_(ts[rj - 1], hs[rj - 1]);
-        ++rj;
-      }
-    }
-    if (mode == U_FAIL) {
-      write_nan<NP, D>(a, k);
-      k = -1;
-    }
-    if (mode == U_DONE) {
-      if (a.params_bar)
-#pragma unroll
-        for (int q = 0; q < NP; ++q) a.params_bar[q * n + k] = pacc.get(q);
-      if (a.y0_bar)
-#pragma unroll
-        for (int c = 0; c < D; ++c) a.y0_bar[c * n + k] = (double)lam[c];
-      if (a.loss) a.loss[k] = loss;
-      k = -1;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Reverse kernel, every accepted state stored (checkpoint interval k = 1).
-//
-// Segment i holds (t_{i-1}, y_{i-1}, h_i): nothing is recomputed, and every
-// unit is a VJP with the same code, either the step-i VJP from y_{i-1} or a
-// save-time side-step VJP from a mesh state. Per trajectory: the saves at
-// state S (y(t1)); then for i = S..1: load segment i, step VJP, the saves
-// attached to state i-1.
-// ---------------------------------------------------------------------------
-template <class Pb, class R, bool USER_COT>
-__global__ void __launch_bounds__(TPB_REV) tsit5_reverse_k1_kernel(const RevArgs a) {
-  constexpr int D = Pb::D, NP = Pb::NP;
-  using Acc = typename std::conditional<std::is_same<R, float>::value, CompensatedAcc<NP>, PlainAcc<NP>>::type;
-  extern __shared__ double smem[];
-  const int ns = a.n_save;
-  double* s_save = smem;
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
-  __syncthreads();
-
-  const long long n = a.n;
-  long long k = -1;
-  bool drained = false;
-  R p[NP], lam[D], yx[D];  // yx: the mesh state the next unit starts from
-  Acc pacc;
-  double loss = 0.0, tx = 0.0;
-  long long seg = -1;
-  int js = -1, segs_left = 0;
-
-  for (;;) {
-    const bool need = (k < 0) && !drained;
-    if (__any_sync(FULL_MASK, need)) {
-      const long long got = warp_ticket(a.work, need);
-      if (need) {
-        if (got < n) {
-          k = got;
-          const long long hd = a.head[k];
-          if (a.status[k] != TRAJ_OK || hd < 0) {
-            write_nan<NP, D>(a, k);
-            k = -1;
-          } else {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) p[q] = (R)a.params[q * n + k];
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-              lam[c] = R(0);
-              yx[c] = (R)a.y_final[c * n + k];
-            }
-            pacc.zero();
-            loss = 0.0;
-            tx = a.t1;
-            seg = hd;
-            segs_left = a.S[k];
-            js = ns - 1;
-          }
-        } else {
-          drained = true;
-        }
-      }
-    }
-    if (!__any_sync(FULL_MASK, k >= 0 || !drained)) break;
-
-    int mode = U_NONE, us = 0;
-    double uh = 0.0;
-    if (k >= 0) {
-      if (next_save<D, R, USER_COT>(a, s_save, k, js, tx, yx, lam, loss, us)) {
-        mode = U_SIDE;
-        uh = s_save[us] - tx;
-      } else if (seg < 0) {
-        mode = (segs_left == 0) ? U_DONE : U_FAIL;
-      } else if (seg >= a.arena_cap || segs_left <= 0) {
-        mode = U_FAIL;  // inconsistent record
-      } else {
-        // segment i: [prev, t_{i-1}, y_{i-1}[D], h_i]
-        const double* sp = a.arena + seg * a.segw;
-        const double2 w0 = *reinterpret_cast<const double2*>(sp);
-        seg = __double_as_longlong(w0.x);
-        tx = w0.y;
-#pragma unroll
-        for (int c = 0; c < D; ++c) yx[c] = (R)sp[2 + c];
-        uh = sp[2 + D];
-        --segs_left;
-        mode = U_STEP;
-      }
-    }
-
-    __syncwarp();
-    if (mode == U_STEP || mode == U_SIDE) {
-      R yn[D];
-      reverse_unit<Pb, R, USER_COT>(a, k, mode, us, yx, uh, p, lam, pacc, loss, yn);
-    }
-    if (mode == U_FAIL) {
-      write_nan<NP, D>(a, k);
-      k = -1;
-    }
-    if (mode == U_DONE) {
-      if (a.params_bar)
-#pragma unroll
-        for (int q = 0; q < NP; ++q) a.params_bar[q * n + k] = pacc.get(q);
-      if (a.y0_bar)
-#pragma unroll
-        for (int c = 0; c < D; ++c) a.y0_bar[c * n + k] = (double)lam[c];
-      if (a.loss) a.loss[k] = loss;
-      k = -1;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Launchers
-// ---------------------------------------------------------------------------
-static int sm_count() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms > 0 ? sms : 1;
-}
-
-template <class Kern>
-static cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long n, cudaStream_t s,
-                                     const void* args_ptr) {
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  int bps = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, tpb, smem);
-  if (err != cudaSuccess) return err;
-  long long blocks = (long long)sm_count() * (bps > 0 ? bps : 1);
-  const long long need = (n + tpb - 1) / tpb;
-  if (blocks > need) blocks = need;
-  if (blocks < 1) blocks = 1;
-  void* args[] = {const_cast<void*>(args_ptr)};
-  return cudaLaunchKernel((const void*)kern, dim3((unsigned)blocks), dim3(tpb), args, smem, s);
-}
-
-template <class Pb, class R>
-static cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)(((a.n_save + 1) & ~1) + a.segw * TPB_FWD) * sizeof(double);
-  if (a.y_save) return persistent_launch(tsit5_record_kernel<Pb, R, true>, TPB_FWD, smem, a.n, s, &a);
-  return persistent_launch(tsit5_record_kernel<Pb, R, false>, TPB_FWD, smem, a.n, s, &a);
-}
-
-template <class Pb, class R>
-static cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)((a.n_save + 1) & ~1) * sizeof(double);
-  if (a.k == 1) {
-    if (a.y_save_bar) return persistent_launch(tsit5_reverse_k1_kernel<Pb, R, true>, TPB_REV, smem, a.n, s, &a);
-    return persistent_launch(tsit5_reverse_k1_kernel<Pb, R, false>, TPB_REV, smem, a.n, s, &a);
-  }
-  if (a.y_save_bar) return persistent_launch(tsit5_reverse_kernel<Pb, R, true>, TPB_REV, smem, a.n, s, &a);
-  return persistent_launch(tsit5_reverse_kernel<Pb, R, false>, TPB_REV, smem, a.n, s, &a);
-}
 
 bool tsit5_supports(int problem, int precision) {
   return (problem == 0 || problem == 1 || problem == 4) && (precision == 0 || precision == 1);
@@ -615,24 +10,24 @@ bool tsit5_supports(int problem, int precision) {
 
 cudaError_t launch_tsit5_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s) {
   switch (problem * 2 + precision) {
-    case 0: return fwd_dispatch<Lorenz, double>(a, s);
-    case 1: return fwd_dispatch<Lorenz, float>(a, s);
-    case 2: return fwd_dispatch<VanDerPol, double>(a, s);
-    case 3: return fwd_dispatch<VanDerPol, float>(a, s);
-    case 8: return fwd_dispatch<Linear2, double>(a, s);
-    case 9: return fwd_dispatch<Linear2, float>(a, s);
+    case 0: return fwd_dispatch<Tsit5Method, Lorenz, double>(a, s);
+    case 1: return fwd_dispatch<Tsit5Method, Lorenz, float>(a, s);
+    case 2: return fwd_dispatch<Tsit5Method, VanDerPol, double>(a, s);
+    case 3: return fwd_dispatch<Tsit5Method, VanDerPol, float>(a, s);
+    case 8: return fwd_dispatch<Tsit5Method, Linear2, double>(a, s);
+    case 9: return fwd_dispatch<Tsit5Method, Linear2, float>(a, s);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tsit5_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s) {
   switch (problem * 2 + precision) {
-    case 0: return rev_dispatch<Lorenz, double>(a, s);
-    case 1: return rev_dispatch<Lorenz, float>(a, s);
-    case 2: return rev_dispatch<VanDerPol, double>(a, s);
-    case 3: return rev_dispatch<VanDerPol, float>(a, s);
-    case 8: return rev_dispatch<Linear2, double>(a, s);
-    case 9: return rev_dispatch<Linear2, float>(a, s);
+    case 0: return rev_dispatch<Tsit5Method, Lorenz, double>(a, s);
+    case 1: return rev_dispatch<Tsit5Method, Lorenz, float>(a, s);
+    case 2: return rev_dispatch<Tsit5Method, VanDerPol, double>(a, s);
+    case 3: return rev_dispatch<Tsit5Method, VanDerPol, float>(a, s);
+    case 8: return rev_dispatch<Tsit5Method, Linear2, double>(a, s);
+    case 9: return rev_dispatch<Tsit5Method, Linear2, float>(a, s);
   }
   return cudaErrorInvalidValue;
 }
