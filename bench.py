@@ -37,20 +37,33 @@ from paper_2609_02876_gb300 import workloads as W  # noqa: E402
 METRIC = "gradient trajectories/s on 1 GB300 at matched error vs FP64 oracle; p50/p99 latency"
 UNIT = "trajectories/s"
 
-# Hand-counted algorithmic flops (FMA = 2) of one Tsit5 unit; derivation in the design doc.
-#   f: one right-hand-side evaluation; vjp: one J^T v + f_theta^T v.
-#   stage forward (6 slopes + 6 stage inputs): 6 f + 48 D
-#   stage reverse (6 stage VJPs):              6 vjp + 54 D
-#   trial step of the record:                  7 f + 48 D (stages) + 14 D (error) + 6 D + 4 (norm, control)
-RHS_FLOPS = {"lorenz": (8, 20, 3), "vdp": (5, 15, 2), "linear": (6, 12, 2)}
+# Hand-counted algorithmic flops (FMA = 2) per unit; derivation in the design doc.
+# Per problem: f = one right-hand side, vjp = one J^T v + f_theta^T v,
+# jac = the dense Jacobian, con = one gradient of r^T J u (stiff problems), D.
+RHS_FLOPS = {"lorenz": dict(f=8, vjp=20, D=3), "vdp": dict(f=5, vjp=15, D=2),
+             "robertson": dict(f=8, vjp=19, jac=5, con=23, D=3),
+             "hires": dict(f=36, vjp=80, jac=4, con=49, D=8)}
+STIFF = {"robertson", "hires"}
 
 
 def unit_flops(problem):
-    f, v, D = RHS_FLOPS[problem]
-    fwd = 6 * f + 48 * D
-    rev = 6 * v + 54 * D
-    trial = 7 * f + 48 * D + 14 * D + 6 * D + 4
-    return {"stage_fwd": fwd, "vjp_unit": fwd + rev, "trial": trial}
+    c = RHS_FLOPS[problem]
+    f, v, D = c["f"], c["vjp"], c["D"]
+    norm = 6 * D + 4  # weighted RMS error test and step control
+    if problem not in STIFF:
+        # Tsit5: stage forward (6 slopes + 6 stage inputs) 6 f + 48 D;
+        # stage reverse (6 stage VJPs + cotangent recursion) 6 vjp + 54 D
+        fwd = 6 * f + 48 * D
+        rev = 6 * v + 54 * D
+        trial = 7 * f + 48 * D + 14 * D + norm
+        return {"stage_fwd": fwd, "vjp_unit": fwd + rev, "trial": trial}
+    # Rodas5P (8 stages): J, W = I/(h gamma) - J, LU (2/3 D^3), per stage the
+    # stage input (2 i D), f, the right-hand side (2 i D + 2 D) and one solve
+    # (2 D^2); y_new (D). Reverse: per stage one transposed solve (2 D^2), the
+    # C and a recursions (4 i D + D), one VJP, one Jacobian contraction.
+    step = c["jac"] + D + (2 * D ** 3) // 3 + 56 * D + 8 * f + 70 * D + 16 * D * D + D
+    rev = 7 * D + 16 * D * D + 8 * D + 112 * D + 8 * v + 8 * D + 8 * c["con"]
+    return {"stage_fwd": step, "vjp_unit": step + rev, "trial": step + D + norm}
 
 
 def fp_peak_tflops(precision):
@@ -180,8 +193,13 @@ def run_reference(args):
 def config_of(args, n):
     wl = {"lorenz": "Lorenz-63 (sigma~U[8,12], rho~U[20,30], beta~U[2,3], y0~N((1,1,1),0.1^2 I), t in [0,1], "
                     "10 uniform saves)",
-          "vdp": "Van der Pol (mu~U[0.5,2], y0~U[-2,2]^2, t in [0,10], 50 uniform saves)"}[args.problem]
-    return {"workload": f"{wl}, Tsit5 rtol={args.rtol:g} atol={args.rtol * 1e-2:g}, {args.precision}, "
+          "vdp": "Van der Pol (mu~U[0.5,2], y0~U[-2,2]^2, t in [0,10], 50 uniform saves)",
+          "robertson": "Robertson (k=(0.04,3e7,1e4) x logU[0.9,1.1], y0=(1,0,0), t in [1e-5,1e5], 20 log saves)",
+          "hires": "HIRES (12 rates x logU[0.9,1.1], standard y0, t in [0,321.8122], 10 uniform saves)",
+          }[args.problem]
+    method = "Rodas5P" if args.problem in STIFF else "Tsit5"
+    atol = 1e-10 if args.problem in STIFF else args.rtol * 1e-2
+    return {"workload": f"{wl}, {method} rtol={args.rtol:g} atol={atol:g}, {args.precision}, "
                         f"n={n} per GPU, loss=sum_s ||y(t_s)||^2, grads wrt theta and y0",
             "n_per_gpu": n, "problem": args.problem, "precision": args.precision, "rtol": args.rtol,
             "l2": "inputs and record larger than L2 (no flush)"}
@@ -193,7 +211,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gradsolve", choices=["gradsolve", "reference"])
-    ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp"])
+    ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp", "robertson", "hires"])
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
@@ -300,7 +318,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": config_of(args, n),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "kernel": f"tsit5_{dominant}_kernel",
+                         "traffic": None, "kernel": f"{dominant}_kernel<{'Rodas5P' if args.problem in STIFF else 'Tsit5'}>",
                          "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz (DESIGN.md)"},
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
