@@ -72,6 +72,7 @@ struct gs_record {
   int32_t* natt = nullptr;
   int32_t* status = nullptr;
   double* y_final = nullptr;
+  float* wpart = nullptr;  // per-warp shared-weight gradient partials (LV UDE)
   Counters* ctr = nullptr;
   Counters* ctr_host = nullptr;  // pinned
   int64_t n_cap = 0;             // capacity of the per-trajectory arrays
@@ -151,6 +152,7 @@ void destroy(gs_record* r) {
   free_arrays(r);
   cudaFree(r->arena);
   cudaFree(r->ctr);
+  cudaFree(r->wpart);
   cudaFreeHost(r->ctr_host);
   delete r;
 }
@@ -188,6 +190,7 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   int method = o.method == GS_METHOD_AUTO ? (c->pi.stiff ? GS_METHOD_RODAS5P : GS_METHOD_TSIT5) : o.method;
   if (method != GS_METHOD_TSIT5 && method != GS_METHOD_RODAS5P) return GS_ERR_INVALID_ARG;
   if (o.ckpt_k < 0 || o.ckpt_k > KMAX_HOST) return GS_ERR_INVALID_ARG;
+  if (c->pi.n_shared > 0 && o.ckpt_k > 1) return GS_ERR_INVALID_ARG;  // shared weights: every state stored
   if (o.max_steps < 0 || !std::isfinite(o.h0) || o.h0 < 0) return GS_ERR_INVALID_ARG;
   c->method = method;
   c->precision = o.precision;
@@ -278,7 +281,11 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
   r->precision = c.precision;
   r->d = c.pi.d;
   r->P = c.pi.P;
-  r->k = c.k > 0 ? c.k : auto_ckpt_k(r, c.problem, c.pi.d, n);
+  r->k = c.k > 0 ? c.k : (c.pi.n_shared > 0 ? 1 : auto_ckpt_k(r, c.problem, c.pi.d, n));
+  if (c.pi.n_shared > 0 && !r->wpart) {
+    const cudaError_t e = cudaMalloc(&r->wpart, (size_t)ude_max_warps() * UDE_NW_HOST * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   r->n = n;
   r->t0 = t0;
   r->t1 = t1;
@@ -334,6 +341,7 @@ gs_status launch_reverse(const gs_record* r, const double* params, const float* 
   a.head = r->head;
   a.S = r->S;
   a.y_final = r->y_final;
+  a.wpart = r->wpart;
   a.work = &r->ctr->work_rev;
   a.k = r->k;
   a.segw = r->segw;

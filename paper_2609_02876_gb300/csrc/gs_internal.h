@@ -50,6 +50,7 @@ struct RevArgs {
   double* loss;              // [n] or nullptr
   double* params_bar;        // [P][n] or nullptr
   double* y0_bar;            // [d][n] or nullptr
+  float* wpart;              // [warps][354] per-warp weight-gradient partials (shared-weight problems)
   const int32_t* status;     // [n] recorded status
   const double* arena;
   long long arena_cap;       // segments (bounds every segment index read)
@@ -75,5 +76,9 @@ bool tsit5_supports(int problem, int precision);
 cudaError_t launch_rodas_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_rodas_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
 bool rodas_supports(int problem, int precision);
+// Upper bound on the warps of a persistent reverse grid (the number of
+// per-warp weight-gradient partials a shared-weight problem can produce).
+int ude_max_warps();
+constexpr int UDE_NW_HOST = 354;
 
 }  // namespace gs

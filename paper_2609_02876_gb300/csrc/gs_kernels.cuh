@@ -33,8 +33,17 @@
 #include "gs_device.cuh"
 #include "gs_internal.h"
 #include "gs_rodas.cuh"
+#include "gs_ude.cuh"
 
 namespace gs {
+
+// Problems with shared network weights (the LV UDE): weights staged per CTA,
+// trajectories assigned to lanes statically (so the per-warp weight-gradient
+// sums are reproducible), and warp-collective reverse units.
+template <class Pb, class = void>
+struct HasWeights : std::false_type {};
+template <class Pb>
+struct HasWeights<Pb, std::void_t<decltype(Pb::kWeights)>> : std::integral_constant<bool, Pb::kWeights> {};
 
 constexpr int TPB_FWD = 128;
 constexpr int TPB_REV = 128;
@@ -47,23 +56,23 @@ __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff800
 // a side unit (the user's, or 2 y(t_s) for the built-in loss, whose value the
 // unit adds to the loss).
 template <class Pb, class R, bool USER_COT>
-__device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bool side, int us,
+__device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bool active, bool side, int us,
                                                const R (&ynew)[Pb::D], const R (&lam)[Pb::D], R (&cv)[Pb::D],
                                                double& loss) {
   constexpr int D = Pb::D;
   double l2 = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    R cs;
+    R cs = R(0);
     if (USER_COT) {
-      cs = (R)a.y_save_bar[((long long)us * D + c) * a.n + k];
+      if (active && side) cs = (R)a.y_save_bar[((long long)us * D + c) * a.n + k];
     } else {
       cs = add_(ynew[c], ynew[c]);  // d/dy of ||y||^2
       l2 = fma_((double)ynew[c], (double)ynew[c], l2);
     }
-    cv[c] = side ? cs : lam[c];
+    cv[c] = active ? (side ? cs : lam[c]) : R(0);
   }
-  if (!USER_COT && side) loss = add_(loss, l2);
+  if (!USER_COT && active && side) loss = add_(loss, l2);
 }
 
 // ---------------------------------------------------------------------------
@@ -112,10 +121,13 @@ struct Tsit5Method {
   }
   // Reverse unit: stages from x with step h; a step unit replaces lambda with
   // dPhi/dy^T lambda, a side unit adds dPhi/dy^T ybar_s. Returns y_new in ynew.
+  // `active` is false only for the lanes without work that join a
+  // warp-collective unit (shared-weight problems); they run with h = 0 and a
+  // zero cotangent and change nothing.
   template <class Pb, class R, bool USER_COT, class Acc>
-  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, int us, const R (&x)[Pb::D],
-                                              double h, const R (&p)[Pb::NP], R (&lam)[Pb::D], Acc& pacc,
-                                              double& loss, R (&ynew)[Pb::D]) {
+  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, bool active, int us,
+                                              const R (&x)[Pb::D], double h, const R (&p)[Pb::NP], R (&lam)[Pb::D],
+                                              Acc& pacc, double& loss, R (&ynew)[Pb::D]) {
     constexpr int D = Pb::D;
     R Y[7][D], K[7][D];
     Pb::f(x, p, K[0]);
@@ -125,10 +137,10 @@ struct Tsit5Method {
     if (mode == U_RECOMP) return true;
     const bool side = (mode == U_SIDE);
     R cv[D], v[D];
-    unit_cotangent<Pb, R, USER_COT>(a, k, side, us, ynew, lam, cv, loss);
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
     tsit5_reverse<Pb, R>(Y, p, (R)h, cv, v, pacc);
 #pragma unroll
-    for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
     return true;
   }
 };
@@ -166,9 +178,9 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
     return rodas_step<Pb>(y, p, h, Y, U, LU, piv, rinv, ys);
   }
   template <class Pb, class R, bool USER_COT, class Acc>
-  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, int us, const R (&x)[Pb::D],
-                                              double h, const R (&p)[Pb::NP], R (&lam)[Pb::D], Acc& pacc,
-                                              double& loss, R (&ynew)[Pb::D]) {
+  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, bool active, int us,
+                                              const R (&x)[Pb::D], double h, const R (&p)[Pb::NP], R (&lam)[Pb::D],
+                                              Acc& pacc, double& loss, R (&ynew)[Pb::D]) {
     static_assert(std::is_same<R, double>::value, "Rodas5P runs in FP64");
     constexpr int D = Pb::D;
     double Y[8][D], U[8][D], LU[D][D], rinv[D];
@@ -177,7 +189,7 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
     if (mode == U_RECOMP) return ok;
     const bool side = (mode == U_SIDE);
     double cv[D], v[D];
-    unit_cotangent<Pb, R, USER_COT>(a, k, side, us, ynew, lam, cv, loss);
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
     rodas_reverse<Pb>(x, p, h, Y, U, LU, piv, rinv, cv, v, pacc);
 #pragma unroll
     for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
@@ -198,6 +210,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
   for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
   const int TB = blockDim.x;
   double* stg = smem + ((ns + 1) & ~1) + threadIdx.x;  // this lane's segment staging, stride TB
+  if constexpr (HasWeights<Pb>::value) Pb::block_setup(a.shared_w);
   __syncthreads();
 
   const long long n = a.n;
@@ -423,6 +436,8 @@ __device__ __forceinline__ bool next_save(const RevArgs& a, const double* s_save
 
 template <class R, int NP>
 using AccOf = typename std::conditional<std::is_same<R, float>::value, CompensatedAcc<NP>, PlainAcc<NP>>::type;
+template <class Pb, class R>
+using AccFor = typename std::conditional<HasWeights<Pb>::value, UdeAcc, AccOf<R, Pb::NP>>::type;
 
 // ---------------------------------------------------------------------------
 // Reverse kernel, checkpoint interval k > 1: states inside a segment are
@@ -433,6 +448,7 @@ enum : int { PH_LOAD = 0, PH_RECOMP = 1, PH_INJECT = 2 };
 template <class M, class Pb, class R, bool USER_COT>
 __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
   constexpr int D = Pb::D, NP = Pb::NP;
+  static_assert(!HasWeights<Pb>::value, "shared-weight problems use the k = 1 reverse kernel");
   using Acc = AccOf<R, NP>;
   extern __shared__ double smem[];
   const int ns = a.n_save;
@@ -561,7 +577,7 @@ __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
     __syncwarp();
     if (mode == U_RECOMP || mode == U_STEP || mode == U_SIDE) {
       R yn[D];
-      const bool ok = M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, us, ux, uh, p, lam, pacc, loss, yn);
+      const bool ok = M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, true, us, ux, uh, p, lam, pacc, loss, yn);
       if (!ok) {
         mode = U_FAIL;
       } else if (mode == U_RECOMP) {
@@ -594,18 +610,28 @@ __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
 template <class M, class Pb, class R, bool USER_COT>
 __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
   constexpr int D = Pb::D, NP = Pb::NP;
-  using Acc = AccOf<R, NP>;
+  constexpr bool COLL = HasWeights<Pb>::value;
+  using Acc = AccFor<Pb, R>;
   extern __shared__ double smem[];
   const int ns = a.n_save;
   double* s_save = smem;
   for (int i = threadIdx.x; i < ns; i += blockDim.x) s_save[i] = a.save_t[i];
+  if constexpr (COLL) Pb::block_setup(a.shared_w);
   __syncthreads();
 
   const long long n = a.n;
   long long k = -1;
   bool drained = false;
   R p[NP], lam[D], yx[D];  // yx: the mesh state the next unit starts from
+  // static schedule (shared-weight problems): lane i takes trajectories i, i + L, i + 2L, ...
+  long long stat_next = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stat_stride = (long long)gridDim.x * blockDim.x;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) p[q] = R(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) lam[c] = yx[c] = R(0);
   Acc pacc;
+  if constexpr (COLL) pacc.init();
   double loss = 0.0, tx = 0.0;
   long long seg = -1;
   int js = -1, segs_left = 0;
@@ -613,7 +639,13 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
   for (;;) {
     const bool need = (k < 0) && !drained;
     if (__any_sync(FULL_MASK, need)) {
-      const long long got = warp_ticket(a.work, need);
+      long long got;
+      if constexpr (COLL) {
+        got = need ? stat_next : -1;
+        if (need) stat_next += stat_stride;
+      } else {
+        got = warp_ticket(a.work, need);
+      }
       if (need) {
         if (got < n) {
           k = got;
@@ -668,9 +700,15 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
     }
 
     __syncwarp();
-    if (mode == U_STEP || mode == U_SIDE) {
-      R yn[D];
-      if (!M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, us, yx, uh, p, lam, pacc, loss, yn)) mode = U_FAIL;
+    const bool busy = (mode == U_STEP || mode == U_SIDE);
+    if (COLL || busy) {
+      R yn[D], xin[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) xin[c] = busy ? yx[c] : R(0);
+      if (!M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, busy, us, xin, busy ? uh : 0.0, p, lam, pacc, loss,
+                                                   yn) &&
+          busy)
+        mode = U_FAIL;
     }
     if (mode == U_FAIL) {
       write_nan<NP, D>(a, k);
@@ -680,6 +718,9 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
       write_grad<NP, D, R>(a, k, pacc, lam, loss);
       k = -1;
     }
+  }
+  if constexpr (COLL) {
+    if (a.wpart) pacc.finish(a.wpart + ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * UDE_NW);
   }
 }
 
@@ -721,12 +762,27 @@ inline cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
 template <class M, class Pb, class R>
 inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)((a.n_save + 1) & ~1) * sizeof(double);
+  if constexpr (HasWeights<Pb>::value) {
+    if (a.k != 1) return cudaErrorInvalidValue;
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, reverse_k1_kernel<M, Pb, R, false>, TPB_REV, smem);
+    cudaError_t e = a.y_save_bar ? persistent_launch(reverse_k1_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a)
+                                 : persistent_launch(reverse_k1_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);
+    if (e != cudaSuccess || !a.wpart || !a.shared_w_bar) return e;
+    long long blocks = (long long)sm_count() * (bps > 0 ? bps : 1);
+    const long long need = (a.n + TPB_REV - 1) / TPB_REV;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    ude_reduce_kernel<<<(UDE_NW + 127) / 128, 128, 0, s>>>(a.wpart, (int)(blocks * (TPB_REV / 32)), a.shared_w_bar);
+    return cudaGetLastError();
+  } else {
   if (a.k == 1) {
     if (a.y_save_bar) return persistent_launch(reverse_k1_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a);
     return persistent_launch(reverse_k1_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);
   }
   if (a.y_save_bar) return persistent_launch(reverse_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a);
   return persistent_launch(reverse_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);
+  }
 }
 
 }  // namespace gs

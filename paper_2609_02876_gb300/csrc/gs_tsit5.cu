@@ -5,6 +5,7 @@
 namespace gs {
 
 bool tsit5_supports(int problem, int precision) {
+  if (problem == 5) return precision == 1;  // LV UDE: FP32 network and state, FP64 control
   return (problem == 0 || problem == 1 || problem == 4) && (precision == 0 || precision == 1);
 }
 
@@ -16,6 +17,7 @@ cudaError_t launch_tsit5_forward(int problem, int precision, const FwdArgs& a, c
     case 3: return fwd_dispatch<Tsit5Method, VanDerPol, float>(a, s);
     case 8: return fwd_dispatch<Tsit5Method, Linear2, double>(a, s);
     case 9: return fwd_dispatch<Tsit5Method, Linear2, float>(a, s);
+    case 11: return fwd_dispatch<Tsit5Method, LvUde, float>(a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -28,8 +30,17 @@ cudaError_t launch_tsit5_reverse(int problem, int precision, const RevArgs& a, c
     case 3: return rev_dispatch<Tsit5Method, VanDerPol, float>(a, s);
     case 8: return rev_dispatch<Tsit5Method, Linear2, double>(a, s);
     case 9: return rev_dispatch<Tsit5Method, Linear2, float>(a, s);
+    case 11: return rev_dispatch<Tsit5Method, LvUde, float>(a, s);
   }
   return cudaErrorInvalidValue;
+}
+
+int ude_max_warps() {
+  int dev = 0, sms = 0, threads = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  return (sms > 0 ? sms : 1) * (threads > 0 ? threads : 2048) / 32;
 }
 
 }  // namespace gs

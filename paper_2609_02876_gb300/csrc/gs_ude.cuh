@@ -1,0 +1,288 @@
+// The LV UDE problem: dx/dt = a x - NN(x, y)_1, dy/dt = -d y + NN(x, y)_2 with a
+// shared-weight MLP 2-16-16-2 (tanh hidden layers, linear output), FP32.
+//
+// Per lane the network is evaluated and differentiated on the FP32 CUDA cores
+// (weights in shared memory, broadcast reads). The gradient with respect to the
+// 354 shared weights is a sum over every lane, stage and step of rank-1
+// products, i.e. a dense contraction over the lanes; each warp accumulates it
+// with tensor-core MMAs (mma.sync m16n8k8, TF32 inputs split hi + lo so that
+// the three products hi*hi + hi*lo + lo*hi carry FP32 accuracy), with the
+// lanes as the contraction dimension and the accumulators held in registers
+// for the kernel's whole life. Each warp writes its partial sums once; a
+// separate kernel adds the partials in warp order (deterministic).
+#pragma once
+
+#include "gs_device.cuh"
+
+namespace gs {
+
+constexpr int UDE_H = 16;
+constexpr int UDE_NW = UDE_H * 2 + UDE_H + UDE_H * UDE_H + UDE_H + 2 * UDE_H + 2;  // 354
+// Flat weight layout: W1[16][2], b1[16], W2[16][16], b2[16], W3[2][16], b3[2].
+constexpr int UDE_W1 = 0, UDE_B1 = 32, UDE_W2 = 48, UDE_B2 = 304, UDE_W3 = 320, UDE_B3 = 352;
+
+// tanh(z) = 1 - 2 / (exp(2 z) + 1) with the hardware exp2 and an IEEE
+// reciprocal: absolute error ~1e-7 (FP32 level), exact limits +-1.
+__device__ __forceinline__ float tanh_f32(float z) {
+  const float e = ex2_approx(z * 2.8853900817779268f);  // 2 / ln 2
+  return 1.0f - 2.0f * __frcp_rn(e + 1.0f);
+}
+
+struct LvUde {
+  static constexpr int D = 2, NP = 2;
+  static constexpr bool kWeights = true;
+
+  // Shared-memory copy of the 354 weights, one per CTA.
+  __device__ __forceinline__ static float* weights() {
+    __shared__ float w[UDE_NW];
+    return w;
+  }
+  __device__ static void block_setup(const float* shared_w) {
+    float* w = weights();
+    for (int i = threadIdx.x; i < UDE_NW; i += blockDim.x) w[i] = shared_w[i];
+  }
+  __device__ __forceinline__ static void forward(float x, float y, float (&h1)[UDE_H], float (&h2)[UDE_H],
+                                                 float (&nn)[2]) {
+    const float* w = weights();
+#pragma unroll
+    for (int i = 0; i < UDE_H; ++i)
+      h1[i] = tanh_f32(fmaf(w[UDE_W1 + 2 * i + 1], y, fmaf(w[UDE_W1 + 2 * i], x, w[UDE_B1 + i])));
+#pragma unroll
+    for (int i = 0; i < UDE_H; ++i) {
+      float s = w[UDE_B2 + i];
+#pragma unroll
+      for (int j = 0; j < UDE_H; ++j) s = fmaf(w[UDE_W2 + UDE_H * i + j], h1[j], s);
+      h2[i] = tanh_f32(s);
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      float s = w[UDE_B3 + o];
+#pragma unroll
+      for (int j = 0; j < UDE_H; ++j) s = fmaf(w[UDE_W3 + UDE_H * o + j], h2[j], s);
+      nn[o] = s;
+    }
+  }
+  __device__ __forceinline__ static void f(const float (&y)[D], const float (&p)[NP], float (&o)[D]) {
+    float h1[UDE_H], h2[UDE_H], nn[2];
+    forward(y[0], y[1], h1, h2, nn);
+    o[0] = fmaf(p[0], y[0], -nn[0]);
+    o[1] = fmaf(-p[1], y[1], nn[1]);
+  }
+  // Per-lane backpropagation of the output cotangent v through f at y:
+  // yb = J^T v, pb += f_theta^T v, and the per-layer factors whose outer
+  // products over the lanes form the weight gradient.
+  struct Factors {
+    float x, y, h1[UDE_H], h2[UDE_H], gz1[UDE_H], gz2[UDE_H], go[2];
+  };
+  __device__ __forceinline__ static void backprop(const float (&y)[D], const float (&p)[NP], const float (&v)[D],
+                                                  float (&yb)[D], float (&pb)[NP], Factors& fa) {
+    const float* w = weights();
+    float nn[2], gh2[UDE_H];
+    forward(y[0], y[1], fa.h1, fa.h2, nn);
+    fa.x = y[0];
+    fa.y = y[1];
+    fa.go[0] = -v[0];  // f0 = a x - nn0
+    fa.go[1] = v[1];   // f1 = -d y + nn1
+#pragma unroll
+    for (int j = 0; j < UDE_H; ++j) {
+      gh2[j] = fmaf(w[UDE_W3 + j], fa.go[0], w[UDE_W3 + UDE_H + j] * fa.go[1]);
+      fa.gz2[j] = gh2[j] * fmaf(-fa.h2[j], fa.h2[j], 1.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < UDE_H; ++j) {
+      float s = 0.0f;
+#pragma unroll
+      for (int i = 0; i < UDE_H; ++i) s = fmaf(w[UDE_W2 + UDE_H * i + j], fa.gz2[i], s);
+      fa.gz1[j] = s * fmaf(-fa.h1[j], fa.h1[j], 1.0f);
+    }
+    float gx = 0.0f, gy = 0.0f;
+#pragma unroll
+    for (int j = 0; j < UDE_H; ++j) {
+      gx = fmaf(w[UDE_W1 + 2 * j], fa.gz1[j], gx);
+      gy = fmaf(w[UDE_W1 + 2 * j + 1], fa.gz1[j], gy);
+    }
+    yb[0] = fmaf(p[0], v[0], gx);
+    yb[1] = fmaf(-p[1], v[1], gy);
+    pb[0] = fmaf(y[0], v[0], pb[0]);
+    pb[1] = fmaf(-y[1], v[1], pb[1]);
+  }
+  // Plain per-lane VJP (no weight gradient): used where only J^T v and f_theta^T v are needed.
+  __device__ __forceinline__ static void vjp(const float (&y)[D], const float (&p)[NP], const float (&v)[D],
+                                             float (&yb)[D], float (&pb)[NP]) {
+    Factors fa;
+    backprop(y, p, v, yb, pb, fa);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Warp-level TF32 MMA (m16n8k8, row.col, FP32 accumulate).
+// Fragment ownership (g = lane / 4, t = lane % 4):
+//   A (16x8): a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
+//   B (8x8):  b0 (t, g), b1 (t+4, g)
+//   C (16x8): c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+struct Tf32x2 {  // x = hi + lo, both TF32
+  uint32_t hi, lo;
+};
+__device__ __forceinline__ Tf32x2 split_tf32(float x) {
+  Tf32x2 s;
+  s.hi = to_tf32(x);
+  s.lo = to_tf32(x - __uint_as_float(s.hi));
+  return s;
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// c += A B with A, B given as hi/lo splits: hi*hi + hi*lo + lo*hi.
+__device__ __forceinline__ void mma_3xtf32(float (&c)[4], const Tf32x2 (&a)[4], const Tf32x2 (&b)[2]) {
+  const uint32_t ah[4] = {a[0].hi, a[1].hi, a[2].hi, a[3].hi}, al[4] = {a[0].lo, a[1].lo, a[2].lo, a[3].lo};
+  const uint32_t bh[2] = {b[0].hi, b[1].hi}, bl[2] = {b[0].lo, b[1].lo};
+  mma_tf32(c, al, bh);
+  mma_tf32(c, ah, bl);
+  mma_tf32(c, ah, bh);
+}
+
+// Per-warp staging of the lanes' factor vectors for the weight-gradient MMAs.
+// Row per lane, 72 floats (stride 72: the fragment reads of rows t, t+4 and
+// columns g hit 32 distinct banks): [gz2 0..15 | h1 16..31 | gz1 32..47 |
+// h2 48..63 | x 64, y 65, go0 66, go1 67].
+constexpr int UDE_ROW = 72;
+constexpr int UDE_WARPS_PER_CTA = 4;
+
+__device__ __forceinline__ float* ude_stage() {
+  __shared__ __align__(16) float s[UDE_WARPS_PER_CTA][32 * UDE_ROW];
+  return s[threadIdx.x >> 5];
+}
+
+// Accumulator of the UDE reverse sweep: the per-trajectory (a, d) gradient
+// (compensated FP32, per lane) and the warp's shared-weight gradient in MMA
+// accumulator fragments:
+//   GA (16 x 24): sum over lanes of gz2 (x) [h1, 1]   -> dW2, db2
+//   GB (16 x 8):  sum over lanes of gz1 (x) [x, y, 1]  -> dW1, db1
+//   GC (32 x 8):  sum over lanes of [h2, 1] (x) go     -> dW3, db3
+struct UdeAcc {
+  CompensatedAcc<2> th;
+  float ga[3][4], gb[4], gc[2][4];
+  __device__ void init() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      ga[0][i] = ga[1][i] = ga[2][i] = 0.0f;
+      gb[i] = 0.0f;
+      gc[0][i] = gc[1][i] = 0.0f;
+    }
+  }
+  __device__ void zero() { th.zero(); }
+  __device__ double get(int q) const { return th.get(q); }
+
+  // Warp-collective: every lane of the warp calls it (lanes without work pass
+  // v = 0, so their factors contribute exactly zero).
+  template <class Pb>
+  __device__ __forceinline__ void vjp(const float (&y)[2], const float (&p)[2], const float (&v)[2],
+                                      float (&yb)[2]) {
+    LvUde::Factors fa;
+    float x[2] = {0.0f, 0.0f};
+    LvUde::backprop(y, p, v, yb, x, fa);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float t = add_(th.s[q], x[q]);
+      th.comp[q] = add_(th.comp[q], (fabsf(th.s[q]) >= fabsf(x[q])) ? add_(sub_(th.s[q], t), x[q])
+                                                                    : add_(sub_(x[q], t), th.s[q]));
+      th.s[q] = t;
+    }
+    accumulate(fa);
+  }
+
+  __device__ __forceinline__ void accumulate(const LvUde::Factors& fa) {
+    float* st = ude_stage();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float* row = st + lane * UDE_ROW;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4) {
+      *reinterpret_cast<float4*>(row + j) = make_float4(fa.gz2[j], fa.gz2[j + 1], fa.gz2[j + 2], fa.gz2[j + 3]);
+      *reinterpret_cast<float4*>(row + 16 + j) = make_float4(fa.h1[j], fa.h1[j + 1], fa.h1[j + 2], fa.h1[j + 3]);
+      *reinterpret_cast<float4*>(row + 32 + j) = make_float4(fa.gz1[j], fa.gz1[j + 1], fa.gz1[j + 2], fa.gz1[j + 3]);
+      *reinterpret_cast<float4*>(row + 48 + j) = make_float4(fa.h2[j], fa.h2[j + 1], fa.h2[j + 2], fa.h2[j + 3]);
+    }
+    *reinterpret_cast<float4*>(row + 64) = make_float4(fa.x, fa.y, fa.go[0], fa.go[1]);
+    __syncwarp();
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {  // contraction over lanes, 8 at a time
+      const float* r0 = st + (ks * 8 + t) * UDE_ROW;
+      const float* r1 = st + (ks * 8 + t + 4) * UDE_ROW;
+      // GA: A[i][k] = gz2_k[i], B[k][j] = (h1_k, 1, 0...)[j]
+      {
+        const Tf32x2 a[4] = {split_tf32(r0[g]), split_tf32(r0[g + 8]), split_tf32(r1[g]), split_tf32(r1[g + 8])};
+#pragma unroll
+        for (int nt = 0; nt < 3; ++nt) {
+          const int j = nt * 8 + g;
+          const float b0 = j < 16 ? r0[16 + j] : (j == 16 ? 1.0f : 0.0f);
+          const float b1 = j < 16 ? r1[16 + j] : (j == 16 ? 1.0f : 0.0f);
+          const Tf32x2 b[2] = {split_tf32(b0), split_tf32(b1)};
+          mma_3xtf32(ga[nt], a, b);
+        }
+      }
+      // GB: A[i][k] = gz1_k[i], B[k][j] = (x_k, y_k, 1, 0...)[j]
+      {
+        const Tf32x2 a[4] = {split_tf32(r0[32 + g]), split_tf32(r0[40 + g]), split_tf32(r1[32 + g]),
+                             split_tf32(r1[40 + g])};
+        const float b0 = g < 2 ? r0[64 + g] : (g == 2 ? 1.0f : 0.0f);
+        const float b1 = g < 2 ? r1[64 + g] : (g == 2 ? 1.0f : 0.0f);
+        const Tf32x2 b[2] = {split_tf32(b0), split_tf32(b1)};
+        mma_3xtf32(gb, a, b);
+      }
+      // GC: A[i][k] = (h2_k, 1, 0...)[i] over two row tiles, B[k][o] = go_k[o]
+      {
+        const float b0 = g < 2 ? r0[66 + g] : 0.0f;
+        const float b1 = g < 2 ? r1[66 + g] : 0.0f;
+        const Tf32x2 b[2] = {split_tf32(b0), split_tf32(b1)};
+        const Tf32x2 a0[4] = {split_tf32(r0[48 + g]), split_tf32(r0[56 + g]), split_tf32(r1[48 + g]),
+                              split_tf32(r1[56 + g])};
+        mma_3xtf32(gc[0], a0, b);
+        const float one = (g == 0) ? 1.0f : 0.0f;  // row 16 of GC: the bias db3
+        const Tf32x2 a1[4] = {split_tf32(one), split_tf32(0.0f), split_tf32(one), split_tf32(0.0f)};
+        mma_3xtf32(gc[1], a1, b);
+      }
+    }
+  }
+
+  // Writes this warp's partial weight gradient (354 floats, the flat layout).
+  __device__ void finish(float* part) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // C fragment element (row, col): c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = g + ((e & 2) ? 8 : 0), cc = 2 * t + (e & 1);
+#pragma unroll
+      for (int nt = 0; nt < 3; ++nt) {  // GA: row r = hidden-2 unit, col j = hidden-1 unit / bias
+        const int j = nt * 8 + cc;
+        if (j < 16) part[UDE_W2 + UDE_H * r + j] = ga[nt][e];
+        else if (j == 16) part[UDE_B2 + r] = ga[nt][e];
+      }
+      if (cc < 2) part[UDE_W1 + 2 * r + cc] = gb[e];  // GB: dW1[r][cc]
+      else if (cc == 2) part[UDE_B1 + r] = gb[e];
+      if (cc < 2) part[UDE_W3 + UDE_H * cc + r] = gc[0][e];  // GC tile 0: dW3[o][j] at (j = r, o = cc)
+      if (cc < 2 && r == 0) part[UDE_B3 + cc] = gc[1][e];    // GC tile 1 row 16: db3[o]
+    }
+  }
+};
+
+// Adds the per-warp partial weight gradients in warp order (FP64 sums).
+static __global__ void ude_reduce_kernel(const float* part, int nwarps, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= UDE_NW) return;
+  double s = 0.0;
+  for (int w = 0; w < nwarps; ++w) s += (double)part[(size_t)w * UDE_NW + i];
+  out[i] = (float)s;
+}
+
+}  // namespace gs
