@@ -170,6 +170,23 @@ gs_status gs_solve_grad_noalloc(int problem_id, int64_t n, const double* params,
                                 double* loss_out, double* params_bar, double* y0_bar, float* shared_w_bar,
                                 int32_t* traj_status);
 
+/*
+ * Solve contexts for concurrent callers (the request server). A context owns
+ * its own reusable record workspace on the device that was current when it was
+ * created; gs_solve_grad_ctx is gs_solve_grad on that workspace, so calls on
+ * different contexts and streams proceed concurrently (calls on one context
+ * are serialised by the context). gs_context_bytes reports the device bytes
+ * the workspace holds (it grows to the largest ensemble seen).
+ */
+typedef struct gs_context gs_context;
+gs_status gs_context_create(gs_context** ctx);
+gs_status gs_context_destroy(gs_context* ctx);
+gs_status gs_context_bytes(const gs_context* ctx, size_t* bytes);
+gs_status gs_solve_grad_ctx(gs_context* ctx, int problem_id, int64_t n, const double* params, const double* y0,
+                            const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                            double rtol, double atol, const gs_options* opt, gs_stream stream, double* loss_out,
+                            double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status);
+
 /* Device bytes held by a record. */
 gs_status gs_record_bytes(const gs_record* rec, size_t* bytes);
 

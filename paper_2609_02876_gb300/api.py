@@ -186,9 +186,45 @@ def reverse(record: Record, params, y0, y_save_bar=None, *, shared_w=None, layou
     return out
 
 
+class Context:
+    """A gs_context: its own device workspace, so solves on different contexts
+    (and streams) run concurrently."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        rc = N.lib().gs_context_create(C.byref(h))
+        if rc != N.GS_OK:
+            raise N.GsError(rc, "gs_context_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bytes(self) -> int:
+        b = C.c_size_t()
+        N.lib().gs_context_bytes(self._h, C.byref(b))
+        return b.value
+
+    def close(self):
+        if self._h and self._h.value:
+            N.lib().gs_context_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve_grad(self, problem, params, y0, t0, t1, save_t, rtol, atol, **kw):
+        return solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, context=self, **kw)
+
+
 def solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, *, shared_w=None, layout="aos", check=True,
-               out=None, **opts):
-    """gs_solve_grad (record + reverse, built-in loss). Returns dict(loss, params_bar, y0_bar, status)."""
+               out=None, context=None, **opts):
+    """gs_solve_grad (record + reverse, built-in loss); with `context`, gs_solve_grad_ctx.
+    Returns dict(loss, params_bar, y0_bar, status)."""
     pid = _pid(problem)
     d, P, _, nw = problem_info(pid)
     p = _soa_in(params, P, layout, "params")
@@ -204,10 +240,13 @@ def solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, *, shared_w=None
     wb = torch.zeros(nw, dtype=torch.float32, device=p.device) if nw else None
     counts = torch.empty((2, n), dtype=torch.int32, device=p.device) if opts.pop("step_counts", False) else None
     o = _opts(step_counts=counts, **opts)
-    rc = N.lib().gs_solve_grad(pid, n, p.data_ptr(), y.data_ptr(), _ptr(w), float(t0), float(t1), stp, st.size,
-                               float(rtol), float(atol), C.byref(o), _stream(), out["loss"].data_ptr(),
-                               out["params_bar"].data_ptr(), out["y0_bar"].data_ptr(), _ptr(wb),
-                               out["status"].data_ptr())
+    args = (pid, n, p.data_ptr(), y.data_ptr(), _ptr(w), float(t0), float(t1), stp, st.size, float(rtol),
+            float(atol), C.byref(o), _stream(), out["loss"].data_ptr(), out["params_bar"].data_ptr(),
+            out["y0_bar"].data_ptr(), _ptr(wb), out["status"].data_ptr())
+    if context is None:
+        rc = N.lib().gs_solve_grad(*args)
+    else:
+        rc = N.lib().gs_solve_grad_ctx(context.handle, *args)
     if rc not in (N.GS_OK, N.GS_ERR_TRAJ_FAILED) or (check and rc != N.GS_OK):
         raise N.GsError(rc, "gs_solve_grad")
     res = dict(out)

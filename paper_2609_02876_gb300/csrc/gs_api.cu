@@ -80,6 +80,14 @@ struct gs_record {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (optional)
 };
 
+// A solve context: its own reusable record workspace, so that calls on
+// different contexts (and streams) run concurrently.
+struct gs_context {
+  gs_record* ws = nullptr;
+  std::mutex mu;
+  int device = 0;
+};
+
 namespace {
 
 gs_status cuda_fail(cudaError_t e) {
@@ -99,16 +107,21 @@ void free_arrays(gs_record* r) {
   r->n_cap = 0;
 }
 
+constexpr int kMaxDim = 8;  // largest state dimension of the registry
+
 size_t record_bytes(const gs_record* r) {
   return (size_t)r->arena_cap * r->segw * sizeof(double) +
-         (size_t)r->n_cap * (sizeof(long long) + 3 * sizeof(int32_t) + r->d * sizeof(double)) + sizeof(Counters);
+         (size_t)r->n_cap * (sizeof(long long) + 3 * sizeof(int32_t) + kMaxDim * sizeof(double)) +
+         sizeof(Counters);
 }
 
 // Ensures per-trajectory arrays for n trajectories of dimension d.
 gs_status ensure_arrays(gs_record* r, int64_t n, int d) {
-  if (r->n_cap >= n && r->d == d && r->head) return GS_OK;
+  (void)d;
+  if (r->n_cap >= n && r->head) return GS_OK;
   free_arrays(r);
   const int64_t m = n > 0 ? n : 1;
+  d = kMaxDim;  // y(t1) sized for any problem, so a reused workspace never reallocates for d
   cudaError_t e;
   if ((e = cudaMalloc(&r->head, m * sizeof(long long))) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMalloc(&r->S, m * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e);
@@ -352,6 +365,26 @@ gs_status launch_reverse(const gs_record* r, const double* params, const float* 
   return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
+// Record then reverse into workspace r (the body of gs_solve_grad[_ctx]).
+gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* params, const double* y0,
+                        const float* shared_w, double t0, double t1, const double* save_t, int n_save, double rtol,
+                        double atol, cudaStream_t s, double* loss_out, double* params_bar, double* y0_bar,
+                        float* shared_w_bar, int32_t* traj_status) {
+  gs_status st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol);
+  if (st != GS_OK) return st;
+  st = run_record(r, c, n, params, y0, shared_w, nullptr, s);
+  if (st != GS_OK) return st;
+  if (c.kernel_ms) cudaEventRecord(r->ev[2], s);
+  st = launch_reverse(r, params, shared_w, nullptr, loss_out, params_bar, y0_bar, shared_w_bar, s);
+  if (st != GS_OK) return st;
+  if (c.kernel_ms) cudaEventRecord(r->ev[3], s);
+  cudaError_t e = cudaMemcpyAsync(traj_status, r->status, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[1], r->ev[2], r->ev[3]);
+  return r->ctr_host->any_failed ? GS_ERR_TRAJ_FAILED : GS_OK;
+}
+
 // gs_solve_grad's reusable record, one per device.
 std::mutex g_ws_mu;
 std::vector<gs_record*> g_ws;
@@ -455,20 +488,58 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
   std::lock_guard<std::mutex> lock(g_ws_mu);
   gs_record* r = workspace(dev);
   if (!r) return GS_ERR_OOM;
-  st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol);
+  return solve_grad_in(r, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
+                       loss_out, params_bar, y0_bar, shared_w_bar, traj_status);
+}
+
+gs_status gs_context_create(gs_context** ctx) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  *ctx = nullptr;
+  gs_context* c = new (std::nothrow) gs_context();
+  if (!c) return GS_ERR_OOM;
+  c->ws = new (std::nothrow) gs_record();
+  if (!c->ws) {
+    delete c;
+    return GS_ERR_OOM;
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c->ws;
+    delete c;
+    return GS_ERR_CUDA;
+  }
+  *ctx = c;
+  return GS_OK;
+}
+
+gs_status gs_context_destroy(gs_context* ctx) {
+  if (!ctx) return GS_OK;
+  destroy(ctx->ws);
+  delete ctx;
+  return GS_OK;
+}
+
+gs_status gs_context_bytes(const gs_context* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return GS_ERR_INVALID_ARG;
+  *bytes = record_bytes(ctx->ws);
+  return GS_OK;
+}
+
+gs_status gs_solve_grad_ctx(gs_context* ctx, int problem_id, int64_t n, const double* params, const double* y0,
+                            const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                            double rtol, double atol, const gs_options* opt, gs_stream stream, double* loss_out,
+                            double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  Call c;
+  gs_status st = check_common(problem_id, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, opt, &c);
   if (st != GS_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  st = run_record(r, c, n, params, y0, shared_w, nullptr, s);
-  if (st != GS_OK) return st;
-  if (c.kernel_ms) cudaEventRecord(r->ev[2], s);
-  st = launch_reverse(r, params, shared_w, nullptr, loss_out, params_bar, y0_bar, shared_w_bar, s);
-  if (st != GS_OK) return st;
-  if (c.kernel_ms) cudaEventRecord(r->ev[3], s);
-  cudaError_t e = cudaMemcpyAsync(traj_status, r->status, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
-  if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[1], r->ev[2], r->ev[3]);
-  return r->ctr_host->any_failed ? GS_ERR_TRAJ_FAILED : GS_OK;
+  if (n == 0) return GS_OK;
+  if (!traj_status) return GS_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != ctx->device) return GS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  return solve_grad_in(ctx->ws, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol,
+                       (cudaStream_t)stream, loss_out, params_bar, y0_bar, shared_w_bar, traj_status);
 }
 
 gs_status gs_record_bytes(const gs_record* rec, size_t* bytes) {
