@@ -158,6 +158,43 @@ def cpu_baseline(args, budget_s=12.0):
                       f"gradient, {dt:.1f} s on {cores} threads"}
 
 
+def serving_measure(args):
+    """The serving workload (uneven requests: problem ~ U{Lorenz, VdP, Robertson},
+    n ~ 2^U[6, max], rtol ~ U{1e-6, 1e-8}, FP64, 64 GB record budget) through the
+    continuous-batching server: capacity with all requests queued, then p50/p99
+    latency under Poisson arrivals at 0.5 / 0.8 / 1.0 of that capacity, beside
+    serial plain launches of the same stream."""
+    from paper_2609_02876_gb300 import serve
+    reqs = serve.c4_stream(args.serve_requests, seed=0, log2n=(6, args.serve_log2n_max))
+    total = sum(r.n for r in reqs)
+    serve.run_serial(reqs[:8])  # warm the kernels and allocators
+
+    def server_run(rate):
+        srv = serve.Server(slots=4, budget_bytes=64 << 30, max_pack=1 << 21)
+        t = time.perf_counter()
+        serve.run_stream(srv, reqs, rate=rate)
+        dt = time.perf_counter() - t
+        srv.close()
+        assert all((r.status == 0).all() for r in reqs)
+        lat = [r.latency for r in reqs]
+        return dt, serve.latency_stats(lat), len(srv.batch_log)
+
+    dt, stats, nb = server_run(None)
+    cap_rps = len(reqs) / dt
+    out = {"requests": len(reqs), "trajectories": total,
+           "workload": f"{len(reqs)} requests, problem~U{{lorenz,vdp,robertson}}, n~2^U[6,{args.serve_log2n_max}], "
+                       "rtol~U{1e-6,1e-8}, FP64, budget 64 GB, 4 slots",
+           "capacity": {"requests_per_s": cap_rps, "trajectories_per_s": total / dt, "launches": nb}}
+    for load in (0.5, 0.8, 1.0):
+        dt, stats, nb = server_run(load * cap_rps)
+        out[f"load_{load}"] = dict(stats, trajectories_per_s=total / dt, launches=nb)
+    lat, dt = serve.run_serial(reqs)
+    out["serial_all_queued"] = dict(serve.latency_stats(lat), trajectories_per_s=total / dt)
+    lat, dt = serve.run_serial(reqs, rate=0.8 * cap_rps)
+    out["serial_load_0.8"] = dict(serve.latency_stats(lat), trajectories_per_s=total / dt)
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -217,6 +254,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1 << 15)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-log2n-max", type=int, default=18)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -324,6 +364,8 @@ def main():
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
                      "reverse_tflops": rev_flops / rev_s / 1e12},
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_serve:
+        line["serving"] = serving_measure(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
