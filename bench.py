@@ -158,6 +158,30 @@ def cpu_baseline(args, budget_s=12.0):
                       f"gradient, {dt:.1f} s on {cores} threads"}
 
 
+def accuracy_sample(args, precision, m=512):
+    """Gradient error against the FP64 oracle on the GPU's own mesh, over the
+    first m trajectories of the same workload: normwise relative error of each
+    trajectory's (theta_bar, y0_bar) vector, median and max."""
+    import torch
+
+    import oracle
+    from paper_2609_02876_gb300 import api
+    wl = W.make(args.problem, m, rtol=args.rtol, seed=0)
+    P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
+    Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
+    rec, _, _ = api.forward_record(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                   layout="soa", want_saves=False, precision=precision)
+    g = api.reverse(rec, P, Y, layout="soa")
+    off, h = rec.export_mesh()
+    o = oracle.replay_grad(args.problem, wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h)
+    a = np.concatenate([g["params_bar"].cpu().numpy().T, g["y0_bar"].cpu().numpy().T], 1)
+    b = np.concatenate([o["params_bar"], o["y0_bar"]], 1)
+    e = np.abs(a - b).max(1) / np.abs(b).max(1)
+    rec.free()
+    return {"median": float(np.median(e)), "max": float(e.max()), "sample": m,
+            "reference": "FP64 oracle replayed on the GPU's own mesh (normwise per trajectory)"}
+
+
 def serving_measure(args):
     """The serving workload (uneven requests: problem ~ U{Lorenz, VdP, Robertson},
     n ~ 2^U[6, max], rtol ~ U{1e-6, 1e-8}, FP64, 64 GB record budget) through the
@@ -255,6 +279,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1 << 15)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-log2n-max", type=int, default=18)
     args = ap.parse_args()
@@ -364,6 +389,25 @@ def main():
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
                      "reverse_tflops": rev_flops / rev_s / 1e12},
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks}
+    if rank == 0:
+        line["accuracy"] = accuracy_sample(args, args.precision)
+    if rank == 0 and ws == 1 and args.precision == "fp64" and args.problem in ("lorenz", "vdp") \
+            and not args.no_mixed:
+        # the FP32-mixed form on the same workload and GPU: throughput and its error vs the FP64 oracle
+        for _ in range(2):
+            api.solve_grad(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                           layout="soa", out=out, precision="fp32_mixed")
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            api.solve_grad(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                           layout="soa", out=out, precision="fp32_mixed")
+        e1.record()
+        torch.cuda.synchronize()
+        tm = e0.elapsed_time(e1) / 1e3
+        line["fp32_mixed"] = {"value": n * args.steps / tm, "unit": UNIT, "ms_per_step": tm / args.steps * 1e3,
+                              "dtype": "f32 stages/adjoint + f64 control",
+                              "accuracy": accuracy_sample(args, "fp32_mixed")}
     if rank == 0 and ws == 1 and not args.no_serve:
         line["serving"] = serving_measure(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

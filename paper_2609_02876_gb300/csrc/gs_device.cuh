@@ -36,6 +36,41 @@ __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
 
 // ---------------------------------------------------------------------------
+// FP32 <-> FP64 conversions on the integer ALU. GB300 executes the hardware
+// conversion instructions on its FP64 pipe (2 lanes per clock per SM), which
+// the FP32-mixed form otherwise spends on format changes; these rebuild the
+// IEEE-754 encodings with integer operations instead. to_d is exact for every
+// float (subnormals flush to zero); to_f truncates the mantissa (round toward
+// zero), flushes values below the float normal range to zero and saturates
+// to infinity above it. Both are identities when R = double.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double to_d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t s = (uint64_t)(u & 0x80000000u) << 32;
+  const uint64_t ed = (e == 0u) ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+  const uint64_t m = (e == 0u) ? 0u : (uint64_t)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(s | (ed << 52) | m));
+}
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ float to_f(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t s = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+  const uint32_t m = (uint32_t)(b >> 29) & 0x7fffffu;
+  uint32_t r = s | ((e - 896u) << 23) | m;                   // normal range: e in [897, 1150]
+  r = (e < 897u) ? s : r;                                     // underflow: signed zero
+  r = (e > 1150u) ? (s | 0x7f800000u | (e == 0x7ffu && (b << 12) ? 0x400000u : 0u)) : r;  // inf / nan
+  return __uint_as_float(r);
+}
+template <class R>
+__device__ __forceinline__ R to_r(double x);
+template <>
+__device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_r<float>(double x) { return to_f(x); }
+
+// ---------------------------------------------------------------------------
 // Problems (paper Appendix A). Each provides
 //   f(y, p, o):           o = f(y, theta)
 //   vjp(y, p, v, yb, pb): yb = J(y)^T v,  pb += (df/dtheta)^T v
@@ -426,14 +461,30 @@ __device__ __forceinline__ double recip_scale(double sc) {
 // The scale and the sum are FP64; each ratio uses an FP32-accurate reciprocal
 // of the scale, so q carries a relative error below 1e-6: it decides accept /
 // reject and scales the next step, and never enters the accepted solution.
-template <int D, class R>
-__device__ __forceinline__ double err_meansq(const R (&e)[D], const R (&y)[D], const R (&yn)[D], double rtol,
-                                             double atol) {
+template <int D>
+__device__ __forceinline__ double err_meansq(const double (&e)[D], const double (&y)[D], const double (&yn)[D],
+                                             double rtol, double atol) {
   double q = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const double sc = fma_(rtol, fmax(fabs((double)y[c]), fabs((double)yn[c])), atol);
-    const double r = mul_((double)e[c], recip_scale(sc));
+    const double sc = fma_(rtol, fmax(fabs(y[c]), fabs(yn[c])), atol);
+    const double r = mul_(e[c], recip_scale(sc));
+    q = fma_(r, r, q);
+  }
+  return mul_(q, 1.0 / D);
+}
+// FP32-mixed form: the error, y and y_new are FP32 stage values, so each ratio
+// e_c / sc_c is formed in FP32 (scale with an IEEE reciprocal); the squares are
+// summed and the mean compared in FP64.
+template <int D>
+__device__ __forceinline__ double err_meansq(const float (&e)[D], const float (&y)[D], const float (&yn)[D],
+                                             double rtol, double atol) {
+  const float rt = (float)rtol, at = (float)atol;
+  double q = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const float sc = fmaf(rt, fmaxf(fabsf(y[c]), fabsf(yn[c])), at);
+    const double r = to_d(__fmul_rn(e[c], __frcp_rn(sc)));
     q = fma_(r, r, q);
   }
   return mul_(q, 1.0 / D);
@@ -442,10 +493,10 @@ __device__ __forceinline__ double err_meansq(const R (&e)[D], const R (&y)[D], c
 // Integral-controller factor from the mean-square error q = err^2:
 // clamp(0.9 err^(-1/5), 0.2, 10) = clamp(0.9 q^(-1/10), 0.2, 10); q = 0 gives 10.
 // FP32 with the hardware log2 / exp2: the factor only scales the next trial step.
-__device__ __forceinline__ double ctrl_factor(double q) {
-  if (!(q > 0.0)) return 10.0;
-  const float f = __fmul_rn(0.9f, ex2_approx(__fmul_rn(-0.1f, lg2_approx(__double2float_rn(q)))));
-  return (double)fminf(10.0f, fmaxf(0.2f, f));
+__device__ __forceinline__ float ctrl_factor(double q) {
+  if (!(q > 0.0)) return 10.0f;
+  const float f = __fmul_rn(0.9f, ex2_approx(__fmul_rn(-0.1f, lg2_approx(to_f(q)))));
+  return fminf(10.0f, fmaxf(0.2f, f));
 }
 
 // Starting step: the algorithm of Hairer, Norsett & Wanner, Vol. I, Sec. II.4

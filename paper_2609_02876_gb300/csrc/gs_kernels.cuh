@@ -60,19 +60,19 @@ __device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bo
                                                const R (&ynew)[Pb::D], const R (&lam)[Pb::D], R (&cv)[Pb::D],
                                                double& loss) {
   constexpr int D = Pb::D;
-  double l2 = 0.0;
+  R l2 = R(0);  // ||y(t_s)||^2 in the unit's precision; only side units add it to the FP64 loss
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     R cs = R(0);
     if (USER_COT) {
-      if (active && side) cs = (R)a.y_save_bar[((long long)us * D + c) * a.n + k];
+      if (active && side) cs = to_r<R>(a.y_save_bar[((long long)us * D + c) * a.n + k]);
     } else {
       cs = add_(ynew[c], ynew[c]);  // d/dy of ||y||^2
-      l2 = fma_((double)ynew[c], (double)ynew[c], l2);
+      l2 = fma_(ynew[c], ynew[c], l2);
     }
     cv[c] = active ? (side ? cs : lam[c]) : R(0);
   }
-  if (!USER_COT && active && side) loss = add_(loss, l2);
+  if (!USER_COT && active && side) loss = add_(loss, to_d(l2));
 }
 
 // ---------------------------------------------------------------------------
@@ -98,8 +98,8 @@ struct Tsit5Method {
     R Y[7][D], K[7][D];
 #pragma unroll
     for (int c = 0; c < D; ++c) K[0][c] = cy.k1[c];
-    tsit5_stages<Pb, R, 7>(y, p, (R)h, Y, K);
-    tsit5_error<Pb, R>(K, (R)h, e);
+    tsit5_stages<Pb, R, 7>(y, p, to_r<R>(h), Y, K);
+    tsit5_error<Pb, R>(K, to_r<R>(h), e);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       ynew[c] = Y[6][c];
@@ -114,7 +114,7 @@ struct Tsit5Method {
     R Y[7][D], K[7][D];
 #pragma unroll
     for (int c = 0; c < D; ++c) K[0][c] = cy.k1[c];
-    tsit5_stages<Pb, R, 6>(y, p, (R)h, Y, K);
+    tsit5_stages<Pb, R, 6>(y, p, to_r<R>(h), Y, K);
 #pragma unroll
     for (int c = 0; c < D; ++c) ys[c] = Y[6][c];
     return true;
@@ -131,14 +131,14 @@ struct Tsit5Method {
     constexpr int D = Pb::D;
     R Y[7][D], K[7][D];
     Pb::f(x, p, K[0]);
-    tsit5_stages<Pb, R, 6>(x, p, (R)h, Y, K);
+    tsit5_stages<Pb, R, 6>(x, p, to_r<R>(h), Y, K);
 #pragma unroll
     for (int c = 0; c < D; ++c) ynew[c] = Y[6][c];
     if (mode == U_RECOMP) return true;
     const bool side = (mode == U_SIDE);
     R cv[D], v[D];
     unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
-    tsit5_reverse<Pb, R>(Y, p, (R)h, cv, v, pacc);
+    tsit5_reverse<Pb, R>(Y, p, to_r<R>(h), cv, v, pacc);
 #pragma unroll
     for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
     return true;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           if (!fin) status = TRAJ_NONFINITE;
           stg[1 * TB] = t;
 #pragma unroll
-          for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = (double)y[c];
+          for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = to_d(y[c]);
         } else {
           drained = true;
         }
@@ -332,9 +332,9 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       // rejection), rejected ones shrink by the same rule, x0.2 on a non-finite
       // error, x0.25 when the step's linear system is singular
       const bool nf = solved && !isfinite(q);
-      double fac = !solved ? 0.25 : (nf ? 0.2 : ctrl_factor(q));
-      if (accept && rej) fac = fmin(fac, 1.0);
-      h = mul_(h, fac);
+      float fac = !solved ? 0.25f : (nf ? 0.2f : ctrl_factor(q));
+      if (accept && rej) fac = fminf(fac, 1.0f);
+      h = mul_(h, to_d(fac));
       rej = !accept;
       lastnf = !accept && nf;
       lastsing = !solved;
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
         slot = 0;
         stg[1 * TB] = t;
 #pragma unroll
-        for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = (double)y[c];
+        for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = to_d(y[c]);
       }
     }
 
@@ -418,10 +418,10 @@ __device__ __forceinline__ bool next_save(const RevArgs& a, const double* s_save
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         if (USER_COT) {
-          lam[c] = add_(lam[c], (R)a.y_save_bar[((long long)js * D + c) * a.n + k]);
+          lam[c] = add_(lam[c], to_r<R>(a.y_save_bar[((long long)js * D + c) * a.n + k]));
         } else {
           lam[c] = add_(lam[c], add_(yx[c], yx[c]));
-          loss = fma_((double)yx[c], (double)yx[c], loss);
+          loss = add_(loss, to_d(mul_(yx[c], yx[c])));
         }
       }
       --js;
@@ -524,8 +524,8 @@ __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
           for (int w = 1; w < (a.segw >> 1); ++w) {
             const double2 v = src[w];
             const int i0 = 2 * w, i1 = 2 * w + 1;
-            if (i0 < 2 + D) ys[0][i0 - 2] = (R)v.x; else if (i0 - 2 - D < m) hs[i0 - 2 - D] = v.x;
-            if (i1 < 2 + D) ys[0][i1 - 2] = (R)v.y; else if (i1 - 2 - D < m) hs[i1 - 2 - D] = v.y;
+            if (i0 < 2 + D) ys[0][i0 - 2] = to_r<R>(v.x); else if (i0 - 2 - D < m) hs[i0 - 2 - D] = v.x;
+            if (i1 < 2 + D) ys[0][i1 - 2] = to_r<R>(v.y); else if (i1 - 2 - D < m) hs[i1 - 2 - D] = v.y;
           }
           rj = 1;
           phase = PH_RECOMP;
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
         seg = __double_as_longlong(w0.x);
         tx = w0.y;
 #pragma unroll
-        for (int c = 0; c < D; ++c) yx[c] = (R)sp[2 + c];
+        for (int c = 0; c < D; ++c) yx[c] = to_r<R>(sp[2 + c]);
         uh = sp[2 + D];
         --segs_left;
         mode = U_STEP;
