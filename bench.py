@@ -273,7 +273,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gradsolve", choices=["gradsolve", "reference"])
     ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp", "robertson", "hires"])
-    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--traj", type=int, default=1 << 24, help="trajectories per GPU")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -296,7 +296,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    n = args.n
+    n = args.traj
     wl = W.make(args.problem, n, rtol=args.rtol, seed=rank)
     P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
     Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")

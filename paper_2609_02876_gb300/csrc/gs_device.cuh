@@ -63,6 +63,21 @@ __device__ __forceinline__ float to_f(double x) {
   r = (e > 1150u) ? (s | 0x7f800000u | (e == 0x7ffu && (b << 12) ? 0x400000u : 0u)) : r;  // inf / nan
   return __uint_as_float(r);
 }
+// Order tests on FP64 values done on the integer ALU: for IEEE doubles that
+// are >= +0 (or NaN), the bit patterns order exactly as the values do, and NaN
+// patterns lie above +inf.
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ unsigned long long abs_bits(double x) { return dbits(x) & 0x7fffffffffffffffull; }
+__device__ __forceinline__ double max_abs(double a, double b) {  // max(|a|, |b|) for finite or inf a, b
+  const unsigned long long ua = abs_bits(a), ub = abs_bits(b);
+  return __longlong_as_double((long long)(ua > ub ? ua : ub));
+}
+constexpr unsigned long long DBITS_ONE = 0x3ff0000000000000ull;  // 1.0
+constexpr unsigned long long DBITS_INF = 0x7ff0000000000000ull;  // +inf
+__device__ __forceinline__ bool le_one(double q) { return dbits(q) <= DBITS_ONE; }      // q >= 0: q <= 1, NaN false
+__device__ __forceinline__ bool finite_nonneg(double q) { return dbits(q) < DBITS_INF; }  // q >= 0 finite
+__device__ __forceinline__ bool positive(double q) { return dbits(q) != 0ull && dbits(q) < 0x8000000000000000ull; }
+
 template <class R>
 __device__ __forceinline__ R to_r(double x);
 template <>
@@ -452,7 +467,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // hardware FP32 reciprocal of the rounded value, converted back. Scales below
 // 1e-30 (outside the FP32 normal range) take the exact FP64 division.
 __device__ __forceinline__ double recip_scale(double sc) {
-  if (sc < 1e-30) return 1.0 / sc;
+  if (dbits(sc) < 0x39b4484bfeebc2a0ull) return 1.0 / sc;  // sc < 1e-30 (sc > 0)
   return (double)__frcp_rn(__double2float_rn(sc));
 }
 
@@ -467,7 +482,7 @@ __device__ __forceinline__ double err_meansq(const double (&e)[D], const double 
   double q = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const double sc = fma_(rtol, fmax(fabs(y[c]), fabs(yn[c])), atol);
+    const double sc = fma_(rtol, max_abs(y[c], yn[c]), atol);
     const double r = mul_(e[c], recip_scale(sc));
     q = fma_(r, r, q);
   }
@@ -494,7 +509,7 @@ __device__ __forceinline__ double err_meansq(const float (&e)[D], const float (&
 // clamp(0.9 err^(-1/5), 0.2, 10) = clamp(0.9 q^(-1/10), 0.2, 10); q = 0 gives 10.
 // FP32 with the hardware log2 / exp2: the factor only scales the next trial step.
 __device__ __forceinline__ float ctrl_factor(double q) {
-  if (!(q > 0.0)) return 10.0f;
+  if (!positive(q)) return 10.0f;
   const float f = __fmul_rn(0.9f, ex2_approx(__fmul_rn(-0.1f, lg2_approx(to_f(q)))));
   return fminf(10.0f, fmaxf(0.2f, f));
 }

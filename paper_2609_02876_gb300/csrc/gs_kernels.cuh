@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       solved = M::template trial<Pb, R>(y, p, h, cy, yn, e, next);
       q = err_meansq<D>(e, y, yn, a.rtol, a.atol);
     }
-    const bool accept = trial && solved && (q <= 1.0);  // NaN rejects
+    const bool accept = trial && solved && le_one(q);  // q >= 0; NaN rejects
     if (accept) {
       const double tn = last ? t1 : add_(t, h);
       if (SAVES) {
@@ -331,14 +331,15 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       // integral controller: accepted steps grow at most x10 (x1 right after a
       // rejection), rejected ones shrink by the same rule, x0.2 on a non-finite
       // error, x0.25 when the step's linear system is singular
-      const bool nf = solved && !isfinite(q);
+      const bool nf = solved && !finite_nonneg(q);
       float fac = !solved ? 0.25f : (nf ? 0.2f : ctrl_factor(q));
       if (accept && rej) fac = fminf(fac, 1.0f);
       h = mul_(h, to_d(fac));
       rej = !accept;
       lastnf = !accept && nf;
       lastsing = !solved;
-      if (fabs(h) < 1e-14 * fmax(1.0, fabs(t))) {
+      // |h| < 1e-14 max(1, |t|), evaluated in FP32 (a threshold test, not arithmetic of the solution)
+      if (fabsf(to_f(h)) < 1e-14f * fmaxf(1.0f, fabsf(to_f(t)))) {
         status = lastsing ? TRAJ_SINGULAR : (lastnf ? TRAJ_NONFINITE : TRAJ_DT_UNDERFLOW);
         done = true;
       }
