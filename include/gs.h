@@ -78,6 +78,10 @@ typedef struct {
   float* kernel_ms;     /* optional HOST [2] output of gs_forward_record / gs_solve_grad:
                            device time (ms) of the record kernel and of the reverse kernel
                            (gs_solve_grad only) of this call, from CUDA events on `stream` */
+  double timeout_ms;    /* bound on each host wait of gs_solve_grad / gs_solve_grad_ctx;
+                           0 = no bound. When it runs out the call returns GS_ERR_TIMEOUT
+                           while its work continues on `stream`: synchronise `stream`
+                           before using the outputs or calling the library again */
 } gs_options;
 
 /* A readable name for a status code (static storage, never NULL). */
@@ -117,7 +121,8 @@ gs_status gs_forward_record(int problem_id, int64_t n, const double* params, con
  * checkpoint, stages are recomputed per step, and the stage cotangents are
  * propagated back (for Rodas5P with one transposed LU solve per stage).
  *
- * params may differ from the recorded ones (a frozen-mesh gradient, Sec. 3.1).
+ * params (and shared_w) must be the values the record's states were computed
+ * with: those of gs_forward_record, or those of the last gs_record_refresh.
  * y_save_bar [n_save][d][n] is dL/dy(t_s); NULL selects the built-in loss
  * L = sum_k sum_s ||y_k(t_s)||^2, whose per-trajectory values are written to
  * loss_out [n] if it is not NULL. Outputs params_bar [P][n] and y0_bar [d][n]
@@ -127,6 +132,20 @@ gs_status gs_forward_record(int problem_id, int64_t n, const double* params, con
 gs_status gs_reverse(const gs_record* rec, const double* params, const double* y0, const float* shared_w,
                      const double* y_save_bar, double* loss_out, double* params_bar, double* y0_bar,
                      float* shared_w_bar, gs_stream stream);
+
+/*
+ * Frozen-mesh reuse (paper Sec. 3.1): re-runs every trajectory's replay chain
+ * y_i = Phi(y_{i-1}; h_i, theta) over its recorded mesh with new params [P][n],
+ * y0 [d][n] (and shared_w for GS_LV_UDE), replacing the record's states. A
+ * following gs_reverse with the same params returns the derivative at theta on
+ * the mesh R(theta_0) that was recorded, d Psi(theta; sg[R(theta_0)]) / d theta,
+ * as a fitting loop that reuses one record needs. The mesh, the save times and
+ * the trajectory status words are unchanged; a step whose linear system is
+ * singular at the new parameters leaves that trajectory's y(t1) NaN (its
+ * gradient is then NaN). Enqueued on `stream`, not synchronised.
+ */
+gs_status gs_record_refresh(gs_record* rec, const double* params, const double* y0, const float* shared_w,
+                            gs_stream stream);
 
 /*
  * Record then reverse in one call with the built-in loss (the hot path):

@@ -21,7 +21,8 @@ TRAJ_STATUS = {0: "ok", 1: "maxsteps", 2: "dt_underflow", 3: "nonfinite", 4: "si
 
 class GsOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("ckpt_k", C.c_int), ("max_steps", C.c_int64),
-                ("h0", C.c_double), ("step_counts", C.c_void_p), ("kernel_ms", C.POINTER(C.c_float))]
+                ("h0", C.c_double), ("step_counts", C.c_void_p), ("kernel_ms", C.POINTER(C.c_float)),
+                ("timeout_ms", C.c_double)]
 
 
 class GsError(RuntimeError):
@@ -61,6 +62,8 @@ def lib():
         L.gs_record_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.gs_record_export_mesh.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         L.gs_record_free.argtypes = [vp]
+        L.gs_record_refresh.argtypes = [vp, vp, vp, vp, vp]
+        L.gs_record_refresh.restype = C.c_int
         L.gs_context_create.argtypes = [C.POINTER(vp)]
         L.gs_context_destroy.argtypes = [vp]
         L.gs_context_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]

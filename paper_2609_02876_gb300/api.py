@@ -31,7 +31,7 @@ def problem_info(problem):
 
 
 def _opts(precision="fp64", method=None, ckpt_k=0, max_steps=0, h0=0.0, step_counts=None,
-          kernel_ms=None) -> N.GsOptions:
+          kernel_ms=None, timeout_ms=0.0) -> N.GsOptions:
     o = N.GsOptions()
     N.lib().gs_default_options(C.byref(o))
     o.precision = {"fp64": N.GS_FP64, "fp32_mixed": N.GS_FP32_MIXED}[precision]
@@ -39,6 +39,7 @@ def _opts(precision="fp64", method=None, ckpt_k=0, max_steps=0, h0=0.0, step_cou
     o.ckpt_k = int(ckpt_k)
     o.max_steps = int(max_steps)
     o.h0 = float(h0)
+    o.timeout_ms = float(timeout_ms)
     o.step_counts = step_counts.data_ptr() if step_counts is not None else None
     if kernel_ms is not None:  # a (2,) float32 numpy array filled with the kernels' device times
         o.kernel_ms = kernel_ms.ctypes.data_as(C.POINTER(C.c_float))
@@ -184,6 +185,19 @@ def reverse(record: Record, params, y0, y_save_bar=None, *, shared_w=None, layou
     if nw:
         out["shared_w_bar"] = wb
     return out
+
+
+def refresh(record: Record, params, y0, *, shared_w=None, layout="aos"):
+    """gs_record_refresh: re-run the record's state chains on its frozen mesh with new
+    (params, y0); a following reverse() at the same params gives the frozen-mesh gradient."""
+    d, P = record.d, record.P
+    p = _soa_in(params, P, layout, "params")
+    y = _soa_in(y0, d, layout, "y0")
+    nw = problem_info(record.problem)[3]
+    w = _dev(shared_w, "shared_w", torch.float32) if nw else None
+    rc = N.lib().gs_record_refresh(record.handle, p.data_ptr(), y.data_ptr(), _ptr(w), _stream())
+    if rc != N.GS_OK:
+        raise N.GsError(rc, "gs_record_refresh")
 
 
 class Context:

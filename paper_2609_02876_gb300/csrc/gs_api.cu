@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <chrono>
+#include <thread>
 #include <vector>
 
 #include "../../include/gs.h"
@@ -178,7 +180,22 @@ struct Call {
   double h0;
   int32_t* step_counts;
   float* kernel_ms;
+  double timeout_ms;
 };
+
+// Waits for the work queued on s, polling with a deadline when timeout_ms > 0.
+gs_status wait_stream(cudaStream_t s, double timeout_ms) {
+  if (!(timeout_ms > 0.0)) return cudaStreamSynchronize(s) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  const auto start = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) return GS_OK;
+    if (e != cudaErrorNotReady) return GS_ERR_CUDA;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - start).count();
+    if (ms > timeout_ms) return GS_ERR_TIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
 
 gs_status check_common(int problem_id, int64_t n, const double* params, const double* y0, const float* shared_w,
                        double t0, double t1, const double* save_t, int n_save, double rtol, double atol,
@@ -212,6 +229,8 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   c->h0 = o.h0;
   c->step_counts = o.step_counts;
   c->kernel_ms = o.kernel_ms;
+  if (!std::isfinite(o.timeout_ms) || o.timeout_ms < 0) return GS_ERR_INVALID_ARG;
+  c->timeout_ms = o.timeout_ms;
   if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_RODAS5P && !rodas_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   return GS_OK;
@@ -259,8 +278,8 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
     if (c.kernel_ms) cudaEventRecord(r->ev[1], s);
     e = cudaMemcpyAsync(r->ctr_host, r->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return GS_ERR_CUDA;
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return GS_ERR_CUDA;
+    const gs_status ws = wait_stream(s, c.timeout_ms);
+    if (ws != GS_OK) return ws;
     if (!r->ctr_host->overflow) {
       if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[0], r->ev[0], r->ev[1]);
       return GS_OK;
@@ -379,8 +398,9 @@ gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* pa
   if (st != GS_OK) return st;
   if (c.kernel_ms) cudaEventRecord(r->ev[3], s);
   cudaError_t e = cudaMemcpyAsync(traj_status, r->status, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
+  st = wait_stream(s, c.timeout_ms);
+  if (st != GS_OK) return st;
   if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[1], r->ev[2], r->ev[3]);
   return r->ctr_host->any_failed ? GS_ERR_TRAJ_FAILED : GS_OK;
 }
@@ -440,6 +460,7 @@ gs_status gs_forward_record(int problem_id, int64_t n, const double* params, con
   gs_status st = check_common(problem_id, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, opt, &c);
   if (st != GS_OK) return st;
   if (n > 0 && !traj_status) return GS_ERR_INVALID_ARG;
+  c.timeout_ms = 0.0;  // the record handle owns the work: wait for it
   gs_record* r = new (std::nothrow) gs_record();
   if (!r) return GS_ERR_OOM;
   st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol);
@@ -472,6 +493,37 @@ gs_status gs_reverse(const gs_record* rec, const double* params, const double* y
   if (dev != rec->device) return GS_ERR_INVALID_ARG;
   return launch_reverse(rec, params, shared_w, y_save_bar, loss_out, params_bar, y0_bar, shared_w_bar,
                         (cudaStream_t)stream);
+}
+
+gs_status gs_record_refresh(gs_record* rec, const double* params, const double* y0, const float* shared_w,
+                            gs_stream stream) {
+  if (!rec) return GS_ERR_INVALID_ARG;
+  if (rec->n == 0) return GS_OK;
+  if (!params || !y0) return GS_ERR_INVALID_ARG;
+  ProblemInfo pi;
+  problem_info(rec->problem, &pi);
+  if (pi.n_shared > 0 && !shared_w) return GS_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != rec->device) return GS_ERR_INVALID_ARG;
+  RevArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = rec->n;
+  a.params = params;
+  a.shared_w = shared_w;
+  a.status = rec->status;
+  a.arena = rec->arena;
+  a.arena_cap = rec->arena_cap;
+  a.head = rec->head;
+  a.S = rec->S;
+  a.k = rec->k;
+  a.segw = rec->segw;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e =
+      (rec->method == GS_METHOD_RODAS5P)
+          ? launch_rodas_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s)
+          : launch_tsit5_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s);
+  return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
 gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const double* y0,

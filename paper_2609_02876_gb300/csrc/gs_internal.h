@@ -76,6 +76,12 @@ bool tsit5_supports(int problem, int precision);
 cudaError_t launch_rodas_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_rodas_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
 bool rodas_supports(int problem, int precision);
+// Frozen-mesh refresh: re-run each trajectory's state chain over its recorded
+// mesh with a.params and y0, rewriting the record's states and y(t1).
+cudaError_t launch_tsit5_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
+                                 const double* y0, cudaStream_t s);
+cudaError_t launch_rodas_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
+                                 const double* y0, cudaStream_t s);
 // Upper bound on the warps of a persistent reverse grid (the number of
 // per-warp weight-gradient partials a shared-weight problem can produce).
 int ude_max_warps();

@@ -119,6 +119,18 @@ struct Tsit5Method {
     for (int c = 0; c < D; ++c) ys[c] = Y[6][c];
     return true;
   }
+  // One step of the replay chain, y_new = Phi(y; h) (no carried state).
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool replay_step(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                     R (&ynew)[Pb::D]) {
+    constexpr int D = Pb::D;
+    R Y[7][D], K[7][D];
+    Pb::f(y, p, K[0]);
+    tsit5_stages<Pb, R, 6>(y, p, to_r<R>(h), Y, K);
+#pragma unroll
+    for (int c = 0; c < D; ++c) ynew[c] = Y[6][c];
+    return true;
+  }
   // Reverse unit: stages from x with step h; a step unit replaces lambda with
   // dPhi/dy^T lambda, a side unit adds dPhi/dy^T ybar_s. Returns y_new in ynew.
   // `active` is false only for the lanes without work that join a
@@ -176,6 +188,14 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
     double Y[8][D], U[8][D], LU[D][D], rinv[D];
     int piv[D];
     return rodas_step<Pb>(y, p, h, Y, U, LU, piv, rinv, ys);
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool replay_step(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                     R (&ynew)[Pb::D]) {
+    constexpr int D = Pb::D;
+    double Y[8][D], U[8][D], LU[D][D], rinv[D];
+    int piv[D];
+    return rodas_step<Pb>(y, p, h, Y, U, LU, piv, rinv, ynew);
   }
   template <class Pb, class R, bool USER_COT, class Acc>
   __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, bool active, int us,
@@ -723,6 +743,74 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
   if constexpr (COLL) {
     if (a.wpart) pacc.finish(a.wpart + ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * UDE_NW);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Refresh kernel (frozen-mesh reuse, paper Sec. 3.1): re-runs the state chain
+// y_i = Phi(y_{i-1}; h_i, theta) of every trajectory over its recorded mesh
+// with new (theta, y0), rewriting the state checkpoints and y(t1). Segments are
+// linked last to first, so the lane finds them in forward order a window of
+// RING segments at a time (one backward walk per window).
+// ---------------------------------------------------------------------------
+constexpr int REFRESH_RING = 64;
+
+template <class M, class Pb, class R>
+__global__ void __launch_bounds__(TPB_REV) refresh_kernel(const RevArgs a, double* arena, double* y_final,
+                                                          const double* y0) {
+  constexpr int D = Pb::D, NP = Pb::NP;
+  if constexpr (HasWeights<Pb>::value) Pb::block_setup(a.shared_w);
+  __syncthreads();
+  const long long n = a.n;
+  long long ring[REFRESH_RING];
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    if (a.status[k] != TRAJ_OK || a.head[k] < 0) continue;
+    R p[NP], y[D];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) p[q] = (R)a.params[q * n + k];
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = (R)y0[c * n + k];
+    const int S = a.S[k];
+    const int nseg = (S + a.k - 1) / a.k;
+    bool ok = true;
+    for (int c0 = 0; c0 < nseg && ok; c0 += REFRESH_RING) {
+      const int c1 = min(nseg, c0 + REFRESH_RING);
+      long long seg = a.head[k];
+      for (int pos = nseg - 1; pos >= c0; --pos) {
+        if (seg < 0 || seg >= a.arena_cap) { ok = false; break; }
+        if (pos < c1) ring[pos - c0] = seg;
+        seg = __double_as_longlong(arena[seg * a.segw]);
+      }
+      for (int pos = c0; pos < c1 && ok; ++pos) {
+        double* sp = arena + ring[pos - c0] * a.segw;
+#pragma unroll
+        for (int c = 0; c < D; ++c) sp[2 + c] = to_d(y[c]);
+        const int m = (pos == nseg - 1) ? S - (nseg - 1) * a.k : a.k;
+        for (int j = 0; j < m; ++j) {
+          R yn[D];
+          ok = ok && M::template replay_step<Pb, R>(y, p, sp[2 + D + j], yn);
+#pragma unroll
+          for (int c = 0; c < D; ++c) y[c] = yn[c];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) y_final[c * n + k] = ok ? to_d(y[c]) : nan_d();
+  }
+}
+
+inline int sm_count();
+
+template <class M, class Pb, class R>
+inline cudaError_t refresh_dispatch(const RevArgs& a, double* arena, double* y_final, const double* y0,
+                                    cudaStream_t s) {
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refresh_kernel<M, Pb, R>, TPB_REV, 0);
+  long long blocks = (long long)sm_count() * (bps > 0 ? bps : 1);
+  const long long need = (a.n + TPB_REV - 1) / TPB_REV;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  refresh_kernel<M, Pb, R><<<(unsigned)blocks, TPB_REV, 0, s>>>(a, arena, y_final, y0);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -29,4 +29,15 @@ cudaError_t launch_rodas_reverse(int problem, int precision, const RevArgs& a, c
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_rodas_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
+                                 const double* y0, cudaStream_t s) {
+  if (precision != 0) return cudaErrorInvalidValue;
+  switch (problem) {
+    case 2: return refresh_dispatch<Rodas5PMethod, Robertson, double>(a, arena, y_final, y0, s);
+    case 3: return refresh_dispatch<Rodas5PMethod, Hires, double>(a, arena, y_final, y0, s);
+    case 4: return refresh_dispatch<Rodas5PMethod, Linear2, double>(a, arena, y_final, y0, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace gs

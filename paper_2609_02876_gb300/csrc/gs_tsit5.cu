@@ -35,6 +35,20 @@ cudaError_t launch_tsit5_reverse(int problem, int precision, const RevArgs& a, c
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_tsit5_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
+                                 const double* y0, cudaStream_t s) {
+  switch (problem * 2 + precision) {
+    case 0: return refresh_dispatch<Tsit5Method, Lorenz, double>(a, arena, y_final, y0, s);
+    case 1: return refresh_dispatch<Tsit5Method, Lorenz, float>(a, arena, y_final, y0, s);
+    case 2: return refresh_dispatch<Tsit5Method, VanDerPol, double>(a, arena, y_final, y0, s);
+    case 3: return refresh_dispatch<Tsit5Method, VanDerPol, float>(a, arena, y_final, y0, s);
+    case 8: return refresh_dispatch<Tsit5Method, Linear2, double>(a, arena, y_final, y0, s);
+    case 9: return refresh_dispatch<Tsit5Method, Linear2, float>(a, arena, y_final, y0, s);
+    case 11: return refresh_dispatch<Tsit5Method, LvUde, float>(a, arena, y_final, y0, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 int ude_max_warps() {
   int dev = 0, sms = 0, threads = 0;
   cudaGetDevice(&dev);

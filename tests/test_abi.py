@@ -69,6 +69,9 @@ def _call(lib, **kw):
     (dict(opt=dict(ckpt_k=33)), N.GS_ERR_INVALID_ARG),
     (dict(opt=dict(max_steps=-2)), N.GS_ERR_INVALID_ARG),
     (dict(opt=dict(method=9)), N.GS_ERR_INVALID_ARG),
+    (dict(opt=dict(timeout_ms=-1.0)), N.GS_ERR_INVALID_ARG),
+    (dict(pid=5, w=1, opt=dict(precision=0)), N.GS_ERR_INVALID_ARG),  # the UDE runs FP32-mixed only
+    (dict(pid=0, opt=dict(method=2)), N.GS_ERR_INVALID_ARG),  # no Rodas5P kernel for Lorenz
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, kw, code):
     assert _call(lib, **kw) == code

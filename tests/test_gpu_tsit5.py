@@ -257,3 +257,46 @@ def test_full_size_sampled_parity():
     assert_close(g["params_bar"].cpu().numpy().T[idx], o["params_bar"], "params_bar")
     assert_close(g["y0_bar"].cpu().numpy().T[idx], o["y0_bar"], "y0_bar")
     rec.free()
+
+
+@pytest.mark.parametrize("name,method", [("lorenz", None), ("vdp", None), ("robertson", None), ("hires", None)])
+def test_frozen_mesh_refresh_gives_gradient_at_new_parameters(name, method):
+    """Paper Sec. 3.1: the gradient at theta on the mesh R(theta_0). Refresh the record
+    with (theta_1, y0_1), reverse at theta_1, compare with the oracle replaying the
+    SAME mesh at theta_1. Refreshing with the recorded values changes nothing."""
+    n = 256
+    wl = W.make(name, n)
+    rec, _, st = record(wl, want_saves=False)
+    g0 = reverse(rec, wl)
+    api.refresh(rec, dev(wl["params"].T), dev(wl["y0"].T), layout="soa")
+    g0b = reverse(rec, wl)
+    np.testing.assert_array_equal(g0["params_bar"], g0b["params_bar"])
+    rng = np.random.default_rng(12)
+    wl1 = dict(wl, params=wl["params"] * (1 + 0.01 * rng.standard_normal(wl["params"].shape)))
+    if name not in ("robertson", "hires"):
+        wl1["y0"] = wl["y0"] + 0.01 * rng.standard_normal(wl["y0"].shape)
+    api.refresh(rec, dev(wl1["params"].T), dev(wl1["y0"].T), layout="soa")
+    g1 = reverse(rec, wl1)
+    off, h = rec.export_mesh()
+    o = oracle.replay_grad(name, wl1["params"], wl1["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h)
+    assert o["ok"].all()
+    assert_close(g1["loss"], o["loss"], "loss")
+    assert_close(g1["params_bar"].T, o["params_bar"], "params_bar")
+    assert_close(g1["y0_bar"].T, o["y0_bar"], "y0_bar")
+
+
+def test_bounded_wait_returns_timeout_and_leaves_work_intact():
+    """A completion wait with a deadline that runs out returns GS_ERR_TIMEOUT; the
+    work finishes on the stream and later calls are unaffected (no device fault)."""
+    from paper_2609_02876_gb300 import _native as N
+    wl = W.make("lorenz", 1 << 22)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    with pytest.raises(N.GsError) as ei:
+        api.solve_grad("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                       timeout_ms=0.05)
+    assert ei.value.code == N.GS_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    small = W.make("lorenz", 64)
+    s = api.solve_grad("lorenz", dev(small["params"].T), dev(small["y0"].T), small["t0"], small["t1"],
+                       small["save_t"], small["rtol"], small["atol"], layout="soa", timeout_ms=60000.0)
+    assert (s["status"].cpu().numpy() == 0).all()
