@@ -37,7 +37,7 @@ from paper_2609_02876_gb300 import workloads as W  # noqa: E402
 METRIC = "gradient trajectories/s on 1 GB300 at matched error vs FP64 oracle; p50/p99 latency"
 UNIT = "trajectories/s"
 
-# Hand-counted algorithmic flops (FMA = 2) per unit; derivation in the design doc.
+# Hand-counted algorithmic flops (FMA = 2) per unit, from the operations each step performs.
 # Per problem: f = one right-hand side, vjp = one J^T v + f_theta^T v,
 # jac = the dense Jacobian, con = one gradient of r^T J u (stiff problems), D.
 RHS_FLOPS = {"lorenz": dict(f=8, vjp=20, D=3), "vdp": dict(f=5, vjp=15, D=2),
@@ -68,12 +68,12 @@ def unit_flops(problem):
 
 def fp_peak_tflops(precision):
     """ALU peak from unit counts and clock: 152 SMs x FMA lanes/clk/SM x 2 x 2.07 GHz.
-    FP64 lanes/clk/SM were measured on this part with a dependent-FMA probe (DESIGN.md)."""
+    FP64 lanes/clk/SM were measured on this part with a dependent-FMA probe."""
     lanes = {"fp64": FP64_LANES_PER_SM, "fp32_mixed": 128}[precision]
     return 152 * lanes * 2 * 2.070e9 / 1e12
 
 
-FP64_LANES_PER_SM = 2  # DFMA probe on this part: 1.06 TFLOP/s sustained (DESIGN.md)
+FP64_LANES_PER_SM = 2  # DFMA probe on this part: 1.06 TFLOP/s sustained
 
 
 class ClockSampler:
@@ -251,6 +251,48 @@ def run_reference(args):
     return 0
 
 
+def forward_measure(args, steps=5):
+    """Forward-only solve (gs_solve, nothing recorded) on the paper's forward timing
+    ensemble: Lorenz, rho evenly over [0, 21], sigma 10, beta 8/3, y0 (1, 0, 0),
+    t in [0, 1], rtol 1e-6, atol 1e-9, solved to the final state, n = 2^24."""
+    import torch
+    from paper_2609_02876_gb300 import api
+    n = args.forward_traj
+    wl = W.make("lorenz_paper", n)
+    P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
+    Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
+    uf = unit_flops("lorenz")
+    res = {"workload": f"lorenz_paper n={n} t=[0,1] rtol=1e-6 atol=1e-9, final state only",
+           "unit": "trajectories/s"}
+    kms = np.zeros(2, np.float32)
+    for prec in ("fp64", "fp32_mixed"):
+        def run(**kw):
+            return api.solve("lorenz", P, Y, wl["t0"], wl["t1"], [], wl["rtol"], wl["atol"], layout="soa",
+                             want_saves=False, precision=prec, **kw)
+        for _ in range(3):
+            run()
+        r = run(step_counts=True)
+        assert (r["status"] == 0).all().item(), "trajectory failures in the forward workload"
+        A_tot = int(r["step_counts"][1].to(torch.int64).sum().item())
+        ms = []
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            run(kernel_ms=kms)
+            ms.append(float(kms[0]))
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        ks = statistics.mean(ms) / 1e3
+        ach = A_tot * uf["trial"] / ks / 1e12
+        res[prec] = {"value": n / t, "us_per_traj": t / n * 1e6, "kernel_ms": ks * 1e3,
+                     "attempted_steps_per_traj": A_tot / n, "achieved_tflops": ach,
+                     "frac": ach / fp_peak_tflops(prec)}
+    del P, Y
+    return res
+
+
 def config_of(args, n):
     wl = {"lorenz": "Lorenz-63 (sigma~U[8,12], rho~U[20,30], beta~U[2,3], y0~N((1,1,1),0.1^2 I), t in [0,1], "
                     "10 uniform saves)",
@@ -280,6 +322,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1 << 15)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-forward", action="store_true")
+    ap.add_argument("--forward-traj", type=int, default=1 << 24)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-log2n-max", type=int, default=18)
     args = ap.parse_args()
@@ -384,7 +428,7 @@ def main():
             "config": config_of(args, n),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                          "traffic": None, "kernel": f"{dominant}_kernel<{'Rodas5P' if args.problem in STIFF else 'Tsit5'}>",
-                         "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz (DESIGN.md)"},
+                         "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz"},
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
                      "reverse_tflops": rev_flops / rev_s / 1e12},
@@ -408,6 +452,8 @@ def main():
         line["fp32_mixed"] = {"value": n * args.steps / tm, "unit": UNIT, "ms_per_step": tm / args.steps * 1e3,
                               "dtype": "f32 stages/adjoint + f64 control",
                               "accuracy": accuracy_sample(args, "fp32_mixed")}
+    if rank == 0 and ws == 1 and not args.no_forward:
+        line["forward_only"] = forward_measure(args)
     if rank == 0 and ws == 1 and not args.no_serve:
         line["serving"] = serving_measure(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -159,6 +159,22 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
                         double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status);
 
 /*
+ * Forward-only solve (paper Sec. 2.1, the adaptive solve of map R without a
+ * record): the same accepted mesh, save states and statuses as
+ * gs_forward_record, bit for bit, but nothing is stored for a reverse sweep.
+ * Arguments as gs_forward_record; y_save_out [n_save][d][n] may be NULL;
+ * y_final_out [d][n] (device) receives y(t1) and traj_status [n] (device) the
+ * trajectory status, both required when n > 0. ckpt_k is ignored.
+ * Uses only the small counter block of the per-device workspace of
+ * gs_solve_grad (no record arena). Synchronises `stream`; returns
+ * GS_ERR_TRAJ_FAILED if any trajectory ended with a non-OK status.
+ */
+gs_status gs_solve(int problem_id, int64_t n, const double* params, const double* y0, const float* shared_w,
+                   double t0, double t1, const double* save_t, int n_save, double rtol, double atol,
+                   const gs_options* opt, gs_stream stream, double* y_save_out, double* y_final_out,
+                   int32_t* traj_status);
+
+/*
  * gs_solve_grad without any device allocation. This entry point has no
  * counterpart in the paper; it exists for callers that cannot call cudaMalloc:
  * for example a process that has handed all free device memory to another

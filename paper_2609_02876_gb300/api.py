@@ -235,6 +235,36 @@ class Context:
         return solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, context=self, **kw)
 
 
+def solve(problem, params, y0, t0, t1, save_t, rtol, atol, *, shared_w=None, layout="aos", want_saves=True,
+          check=True, **opts):
+    """gs_solve (forward only, nothing recorded). Returns dict(y_save, y_final, status, rc)."""
+    pid = _pid(problem)
+    d, P, _, nw = problem_info(pid)
+    p = _soa_in(params, P, layout, "params")
+    y = _soa_in(y0, d, layout, "y0")
+    n = p.shape[1]
+    st, stp = _save_t(save_t)
+    ns = st.size
+    ysv = torch.empty((ns, d, n), dtype=torch.float64, device=p.device) if want_saves else None
+    yf = torch.empty((d, n), dtype=torch.float64, device=p.device)
+    status = torch.empty(n, dtype=torch.int32, device=p.device)
+    w = _dev(shared_w, "shared_w", torch.float32) if nw else None
+    counts = torch.empty((2, n), dtype=torch.int32, device=p.device) if opts.pop("step_counts", False) else None
+    o = _opts(step_counts=counts, **opts)
+    rc = N.lib().gs_solve(pid, n, p.data_ptr(), y.data_ptr(), _ptr(w), float(t0), float(t1), stp, ns, float(rtol),
+                          float(atol), C.byref(o), _stream(), _ptr(ysv), yf.data_ptr(), status.data_ptr())
+    if rc not in (N.GS_OK, N.GS_ERR_TRAJ_FAILED) or (check and rc != N.GS_OK):
+        raise N.GsError(rc, "gs_solve")
+    if layout == "aos":
+        yf = yf.t()
+        if ysv is not None:
+            ysv = ysv.permute(2, 0, 1)
+    res = {"y_save": ysv, "y_final": yf, "status": status, "rc": rc}
+    if counts is not None:
+        res["step_counts"] = counts
+    return res
+
+
 def solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, *, shared_w=None, layout="aos", check=True,
                out=None, context=None, **opts):
     """gs_solve_grad (record + reverse, built-in loss); with `context`, gs_solve_grad_ctx.

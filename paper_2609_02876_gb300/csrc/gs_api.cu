@@ -544,6 +544,61 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
                        loss_out, params_bar, y0_bar, shared_w_bar, traj_status);
 }
 
+gs_status gs_solve(int problem_id, int64_t n, const double* params, const double* y0, const float* shared_w,
+                   double t0, double t1, const double* save_t, int n_save, double rtol, double atol,
+                   const gs_options* opt, gs_stream stream, double* y_save_out, double* y_final_out,
+                   int32_t* traj_status) {
+  Call c;
+  gs_status st = check_common(problem_id, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, opt, &c);
+  if (st != GS_OK) return st;
+  if (n == 0) return GS_OK;
+  if (!traj_status || !y_final_out) return GS_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  gs_record* r = workspace(dev);
+  if (!r) return GS_ERR_OOM;
+  if ((st = ensure_counters(r)) != GS_OK) return st;
+  if (c.kernel_ms && (st = ensure_events(r)) != GS_OK) return st;
+  FwdArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.params = params;
+  a.y0 = y0;
+  a.shared_w = shared_w;
+  a.t0 = t0;
+  a.t1 = t1;
+  a.rtol = rtol;
+  a.atol = atol;
+  a.h0 = c.h0;
+  a.max_steps = c.max_steps;
+  a.n_save = n_save;
+  if (n_save) std::memcpy(a.save_t, save_t, sizeof(double) * n_save);
+  a.y_save = y_save_out;
+  a.step_counts = c.step_counts;
+  a.k = 0;  // nothing recorded: no arena, no per-trajectory record arrays
+  a.segw = 0;
+  a.arena_top = &r->ctr->arena_top;
+  a.overflow = &r->ctr->overflow;
+  a.any_failed = &r->ctr->any_failed;
+  a.status = traj_status;
+  a.y_final = y_final_out;
+  a.work = &r->ctr->work_fwd;
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(r->ctr, 0, sizeof(Counters), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (c.kernel_ms) cudaEventRecord(r->ev[0], s);
+  e = (c.method == GS_METHOD_RODAS5P) ? launch_rodas_forward(c.problem, c.precision, a, s)
+                                      : launch_tsit5_forward(c.problem, c.precision, a, s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (c.kernel_ms) cudaEventRecord(r->ev[1], s);
+  e = cudaMemcpyAsync(r->ctr_host, r->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if ((st = wait_stream(s, c.timeout_ms)) != GS_OK) return st;
+  if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[0], r->ev[0], r->ev[1]);
+  return r->ctr_host->any_failed ? GS_ERR_TRAJ_FAILED : GS_OK;
+}
+
 gs_status gs_context_create(gs_context** ctx) {
   if (!ctx) return GS_ERR_INVALID_ARG;
   *ctx = nullptr;

@@ -279,9 +279,11 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           fin = fin && isfinite(h) && h > 0.0;
           pending_fail = !fin;
           if (!fin) status = TRAJ_NONFINITE;
-          stg[1 * TB] = t;
+          if (a.k > 0) {
+            stg[1 * TB] = t;
 #pragma unroll
-          for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = to_d(y[c]);
+            for (int c = 0; c < D; ++c) stg[(2 + c) * TB] = to_d(y[c]);
+          }
         } else {
           drained = true;
         }
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           ++js;
         }
       }
-      stg[(2 + D + slot) * TB] = h;
+      if (a.k > 0) stg[(2 + D + slot) * TB] = h;
       ++slot;
       t = tn;
 #pragma unroll
@@ -364,7 +366,8 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
         done = true;
       }
     }
-    const bool flush = (k >= 0) && ((slot == a.k) || (done && slot > 0));
+    // (a.k == 0: forward-only solve, nothing is recorded)
+    const bool flush = (a.k > 0) && (k >= 0) && ((slot == a.k) || (done && slot > 0));
 
     // ---- segment write-out: one arena slot per flushing lane, one atomic per warp
     if (__any_sync(FULL_MASK, flush)) {
@@ -386,9 +389,9 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
     }
 
     if (done) {
-      a.head[k] = prev;
-      a.S[k] = S;
-      a.natt[k] = natt;
+      if (a.head) a.head[k] = prev;
+      if (a.S) a.S[k] = S;
+      if (a.natt) a.natt[k] = natt;
       a.status[k] = status;
 #pragma unroll
       for (int c = 0; c < D; ++c) a.y_final[c * n + k] = (double)y[c];

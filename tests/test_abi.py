@@ -83,3 +83,30 @@ def test_too_many_save_times(lib):
 
 def test_empty_ensemble_is_a_no_op(lib):
     assert _call(lib, n=0, params=None, y0=None) == N.GS_OK
+
+
+def _call_solve(lib, **kw):
+    a = dict(pid=0, n=4, params=1, y0=1, w=None, t0=0.0, t1=1.0, save=[0.5, 1.0], rtol=1e-6, atol=1e-8,
+             y_final=1, status=1)
+    a.update(kw)
+    st = np.asarray(a["save"], dtype=np.float64)
+    return lib.gs_solve(a["pid"], a["n"], a["params"], a["y0"], a["w"], a["t0"], a["t1"],
+                        st.ctypes.data_as(C.POINTER(C.c_double)), st.size, a["rtol"], a["atol"], None, None,
+                        None, a["y_final"], a["status"])
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(pid=42), N.GS_ERR_UNKNOWN_PROBLEM),
+    (dict(n=-1), N.GS_ERR_INVALID_ARG),
+    (dict(y0=None), N.GS_ERR_INVALID_ARG),
+    (dict(t1=-1.0), N.GS_ERR_INVALID_ARG),
+    (dict(save=[0.7, 0.2]), N.GS_ERR_INVALID_ARG),
+    (dict(y_final=None), N.GS_ERR_INVALID_ARG),
+    (dict(status=None), N.GS_ERR_INVALID_ARG),
+])
+def test_forward_only_solve_rejects_invalid_arguments(lib, kw, code):
+    assert _call_solve(lib, **kw) == code
+
+
+def test_forward_only_solve_of_an_empty_ensemble_is_a_no_op(lib):
+    assert _call_solve(lib, n=0, params=None, y0=None, y_final=None, status=None) == N.GS_OK

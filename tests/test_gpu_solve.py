@@ -1,0 +1,77 @@
+"""GPU forward-only solve (gs_solve): the record kernel with nothing recorded.
+
+It must take exactly the steps gs_forward_record takes (the same kernel with
+the record writes switched off), so save states, statuses and step counts are
+compared bit for bit; y(t1) is compared with the oracle stepping along the
+exported mesh (normwise relative error 1e-11 per trajectory, as for the other
+FP64 parity tests).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_02876_gb300 import api, build
+from paper_2609_02876_gb300 import workloads as W
+from tests.test_gpu_tsit5 import assert_close, dev, record
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def oracle_final_state(wl, off, h):
+    """y(t1) of every trajectory by the oracle's single steps along the mesh (offsets, h)."""
+    y = np.array(wl["y0"], dtype=np.float64)
+    p = np.asarray(wl["params"], dtype=np.float64)
+    S = np.diff(off)
+    for i in range(int(S.max()) if S.size else 0):
+        act = np.nonzero(S > i)[0]
+        yn, _ = oracle.step(wl["problem"], oracle.METHOD_AUTO, p[act], y[act], h[off[act] + i], w=wl["w"])
+        y[act] = yn
+    return y
+
+
+def solve(wl, **opts):
+    return api.solve(wl["problem"], dev(wl["params"].T), dev(wl["y0"].T), wl["t0"], wl["t1"], wl["save_t"],
+                     wl["rtol"], wl["atol"], layout="soa", **opts)
+
+
+@pytest.mark.parametrize("name,n", [("lorenz", 1000), ("vdp", 333), ("robertson", 257), ("hires", 129)])
+def test_forward_only_solve_takes_the_recorded_steps(name, n):
+    wl = W.make(name, n)
+    rec, ysv, st = record(wl, step_counts=True)
+    s = solve(wl, step_counts=True)
+    assert s["rc"] == 0
+    np.testing.assert_array_equal(s["status"].cpu().numpy(), st.cpu().numpy())
+    np.testing.assert_array_equal(s["step_counts"].cpu().numpy(), rec.step_counts.cpu().numpy())
+    np.testing.assert_array_equal(s["y_save"].cpu().numpy(), ysv.cpu().numpy())
+    off, h = rec.export_mesh()
+    assert_close(s["y_final"].cpu().numpy().T, oracle_final_state(wl, off, h), "y_final")
+
+
+def test_forward_only_solve_fp32_mixed_takes_the_recorded_steps():
+    wl = W.make("lorenz", 4099)
+    rec, ysv, st = record(wl, step_counts=True, precision="fp32_mixed")
+    s = solve(wl, step_counts=True, precision="fp32_mixed")
+    np.testing.assert_array_equal(s["status"].cpu().numpy(), st.cpu().numpy())
+    np.testing.assert_array_equal(s["step_counts"].cpu().numpy(), rec.step_counts.cpu().numpy())
+    np.testing.assert_array_equal(s["y_save"].cpu().numpy(), ysv.cpu().numpy())
+
+
+def test_forward_only_solve_without_saves_and_failed_trajectories():
+    wl = W.make("vdp", 64)
+    p = wl["params"].copy()
+    p[7, 0] = np.inf
+    wl2 = dict(wl, params=p)
+    s = solve(wl2, want_saves=False, check=False)
+    st = s["status"].cpu().numpy()
+    assert s["rc"] == 5 and s["y_save"] is None
+    assert st[7] == 3 and (np.delete(st, 7) == 0).all()
+    full = solve(wl)
+    yf = s["y_final"].cpu().numpy()
+    np.testing.assert_array_equal(np.delete(yf, 7, axis=1), np.delete(full["y_final"].cpu().numpy(), 7, axis=1))
