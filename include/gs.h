@@ -148,6 +148,40 @@ gs_status gs_record_refresh(gs_record* rec, const double* params, const double* 
                             gs_stream stream);
 
 /*
+ * Forward mode of the replay (paper Sec. 5, forward mode for few inputs): the
+ * replay chain y_i = Phi(y_{i-1}; h_i, theta) is re-run from y0 over the
+ * record's mesh (h held as data) with tangents carried alongside, giving for
+ * each direction (params_dot, y0_dot) the directional derivative of the
+ * built-in loss L = sum_s ||y(t_s)||^2 and of the save-time states. One pass
+ * moves the same direction index of every trajectory at once.
+ *
+ * params [P][n], y0 [d][n]: the point of evaluation (any values: the mesh is
+ * the record's, the states are recomputed). n_dir >= 1 directions, laid out
+ * direction-major: params_dot [n_dir][P][n] and y0_dot [n_dir][d][n] (either
+ * may be NULL: a zero tangent). Outputs: loss_dot [n_dir][n] (required),
+ * loss_out [n] and y_save_dot [n_dir][n_save][d][n] (either may be NULL).
+ * Trajectories whose record is not GS_TRAJ_OK, or whose linear system turns
+ * singular, get NaN. Lorenz, Van der Pol and GS_LINEAR (Tsit5), Robertson,
+ * HIRES and GS_LINEAR (Rodas5P) records; GS_ERR_INVALID_ARG for others.
+ * FP64 whatever the record's precision. Enqueued on `stream`, not
+ * synchronised.
+ */
+gs_status gs_replay_jvp(const gs_record* rec, const double* params, const double* y0, int n_dir,
+                        const double* params_dot, const double* y0_dot, double* loss_out, double* loss_dot,
+                        double* y_save_dot, gs_stream stream);
+
+/*
+ * The gradient of the built-in loss by forward mode: gs_replay_jvp along the
+ * unit directions of theta (when params_bar [P][n] is not NULL) and of y0
+ * (when y0_bar [d][n] is not NULL), P and/or d passes (three directions per
+ * kernel launch). Equal to gs_reverse's gradient up to rounding. At least one
+ * of params_bar and y0_bar is required; loss_out [n] may be NULL. Enqueued on
+ * `stream`, not synchronised.
+ */
+gs_status gs_forward_grad(const gs_record* rec, const double* params, const double* y0, double* loss_out,
+                          double* params_bar, double* y0_bar, gs_stream stream);
+
+/*
  * Record then reverse in one call with the built-in loss (the hot path):
  * loss_out [n], params_bar [P][n], y0_bar [d][n], traj_status [n]. The record
  * lives in a library-owned workspace that is reused by later calls on the same

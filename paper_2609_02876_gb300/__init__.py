@@ -6,7 +6,8 @@ Python face (argument marshalling, a torch.autograd.Function, the request
 server) plus the seeded workload generator.
 """
 from . import workloads
-from .api import (GsFunction, Record, forward_record, odeint_ensemble, problem_info, reverse, solve, solve_grad)
+from .api import (GsFunction, Record, forward_grad, forward_record, odeint_ensemble, problem_info, replay_jvp,
+                  reverse, solve, solve_grad)
 
-__all__ = ["GsFunction", "Record", "forward_record", "odeint_ensemble", "problem_info", "reverse", "solve",
-           "solve_grad", "workloads"]
+__all__ = ["GsFunction", "Record", "forward_grad", "forward_record", "odeint_ensemble", "problem_info",
+           "replay_jvp", "reverse", "solve", "solve_grad", "workloads"]

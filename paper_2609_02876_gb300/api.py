@@ -200,6 +200,72 @@ def refresh(record: Record, params, y0, *, shared_w=None, layout="aos"):
         raise N.GsError(rc, "gs_record_refresh")
 
 
+def _dirs_in(x, width: int, layout: str, name: str):
+    """Tangent directions: one (n, width) / (width, n) array or a stack (n_dir, ...). Returns [n_dir][width][n]."""
+    if x is None:
+        return None
+    x = _dev(x, name)
+    if x.dim() == 2:
+        x = x.unsqueeze(0)
+    if x.dim() != 3:
+        raise ValueError(f"{name} must have 2 or 3 dimensions")
+    if layout == "aos":
+        if x.shape[2] != width:
+            raise ValueError(f"{name} must have shape (n_dir, n, {width})")
+        return x.permute(0, 2, 1).contiguous()
+    if x.shape[1] != width:
+        raise ValueError(f"{name} must have shape (n_dir, {width}, n)")
+    return x.contiguous()
+
+
+def replay_jvp(record: Record, params, y0, params_dot=None, y0_dot=None, *, layout="aos", want_y_save_dot=False):
+    """gs_replay_jvp: forward mode of the replay on the record's mesh. Returns
+    dict(loss, loss_dot (n_dir, n)[, y_save_dot]); y_save_dot is (n_dir, n, n_save, d)
+    for layout "aos", [n_dir][n_save][d][n] for "soa"."""
+    d, P = record.d, record.P
+    p = _soa_in(params, P, layout, "params")
+    y = _soa_in(y0, d, layout, "y0")
+    n = p.shape[1]
+    pd = _dirs_in(params_dot, P, layout, "params_dot")
+    yd = _dirs_in(y0_dot, d, layout, "y0_dot")
+    if pd is None and yd is None:
+        raise ValueError("at least one of params_dot and y0_dot is required")
+    nd = (pd if pd is not None else yd).shape[0]
+    if pd is not None and yd is not None and pd.shape[0] != yd.shape[0]:
+        raise ValueError("params_dot and y0_dot must hold the same number of directions")
+    loss = torch.empty(n, dtype=torch.float64, device=p.device)
+    ldot = torch.empty((nd, n), dtype=torch.float64, device=p.device)
+    ysd = torch.empty((nd, record.n_save, d, n), dtype=torch.float64, device=p.device) if want_y_save_dot else None
+    rc = N.lib().gs_replay_jvp(record.handle, p.data_ptr(), y.data_ptr(), nd, _ptr(pd), _ptr(yd), loss.data_ptr(),
+                               ldot.data_ptr(), _ptr(ysd), _stream())
+    if rc != N.GS_OK:
+        raise N.GsError(rc, "gs_replay_jvp")
+    out = {"loss": loss, "loss_dot": ldot}
+    if ysd is not None:
+        out["y_save_dot"] = ysd.permute(0, 3, 1, 2) if layout == "aos" else ysd
+    return out
+
+
+def forward_grad(record: Record, params, y0, *, wrt=("params", "y0"), layout="aos"):
+    """gs_forward_grad: the built-in loss's gradient by forward mode (one pass per input
+    of a trajectory). Returns dict(loss, params_bar, y0_bar) (None for inputs not in wrt)."""
+    d, P = record.d, record.P
+    p = _soa_in(params, P, layout, "params")
+    y = _soa_in(y0, d, layout, "y0")
+    n = p.shape[1]
+    loss = torch.empty(n, dtype=torch.float64, device=p.device)
+    pb = torch.empty((P, n), dtype=torch.float64, device=p.device) if "params" in wrt else None
+    y0b = torch.empty((d, n), dtype=torch.float64, device=p.device) if "y0" in wrt else None
+    rc = N.lib().gs_forward_grad(record.handle, p.data_ptr(), y.data_ptr(), loss.data_ptr(), _ptr(pb), _ptr(y0b),
+                                 _stream())
+    if rc != N.GS_OK:
+        raise N.GsError(rc, "gs_forward_grad")
+    if layout == "aos":
+        pb = pb.t() if pb is not None else None
+        y0b = y0b.t() if y0b is not None else None
+    return {"loss": loss, "params_bar": pb, "y0_bar": y0b}
+
+
 class Context:
     """A gs_context: its own device workspace, so solves on different contexts
     (and streams) run concurrently."""

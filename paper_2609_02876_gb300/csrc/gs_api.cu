@@ -51,6 +51,7 @@ int step_guess(int pid) {
 struct Counters {
   unsigned long long work_fwd;
   unsigned long long work_rev;
+  unsigned long long work_jvp;
   unsigned long long arena_top;
   int overflow;
   int any_failed;
@@ -384,6 +385,60 @@ gs_status launch_reverse(const gs_record* r, const double* params, const float* 
   return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
+// Forward-mode replay launches over directions [g0, g1) of the call, at most
+// JVP_MAX_DIR per launch; `a` carries everything but the per-launch fields.
+gs_status launch_jvp_range(const gs_record* r, JvpArgs a, int g0, int g1, double* loss_out, cudaStream_t s) {
+  const int64_t n = r->n;
+  const double* pdot = a.params_dot;
+  const double* ydot = a.y0_dot;
+  double* ldot = a.loss_dot;
+  double* ysd = a.y_save_dot;
+  for (int g = g0; g < g1; g += JVP_MAX_DIR) {
+    const int nd = (g1 - g) < JVP_MAX_DIR ? (g1 - g) : JVP_MAX_DIR;
+    a.dir0 = g;
+    a.nd = nd;
+    a.loss = (g == g0) ? loss_out : nullptr;
+    if (!a.basis) {
+      const int64_t q = g - g0;
+      a.params_dot = pdot ? pdot + q * r->P * n : nullptr;
+      a.y0_dot = ydot ? ydot + q * r->d * n : nullptr;
+      a.loss_dot = ldot + q * n;
+      a.y_save_dot = ysd ? ysd + q * (int64_t)r->n_save * r->d * n : nullptr;
+    }
+    cudaError_t e = cudaMemsetAsync(&r->ctr->work_jvp, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    e = launch_jvp(r->method, r->problem, a, s);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+  }
+  return GS_OK;
+}
+
+// The parts of the forward-mode arguments that come from the record.
+gs_status jvp_common(const gs_record* r, const double* params, const double* y0, JvpArgs* a) {
+  if (!params || !y0) return GS_ERR_INVALID_ARG;
+  if (!jvp_supports(r->method, r->problem)) return GS_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != r->device) return GS_ERR_INVALID_ARG;
+  std::memset(a, 0, sizeof(*a));
+  a->n = r->n;
+  a->params = params;
+  a->y0 = y0;
+  a->t0 = r->t0;
+  a->t1 = r->t1;
+  a->n_save = r->n_save;
+  std::memcpy(a->save_t, r->save_t, sizeof(double) * r->n_save);
+  a->status = r->status;
+  a->arena = r->arena;
+  a->arena_cap = r->arena_cap;
+  a->head = r->head;
+  a->S = r->S;
+  a->work = &r->ctr->work_jvp;
+  a->k = r->k;
+  a->segw = r->segw;
+  return GS_OK;
+}
+
 // Record then reverse into workspace r (the body of gs_solve_grad[_ctx]).
 gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* params, const double* y0,
                         const float* shared_w, double t0, double t1, const double* save_t, int n_save, double rtol,
@@ -493,6 +548,38 @@ gs_status gs_reverse(const gs_record* rec, const double* params, const double* y
   if (dev != rec->device) return GS_ERR_INVALID_ARG;
   return launch_reverse(rec, params, shared_w, y_save_bar, loss_out, params_bar, y0_bar, shared_w_bar,
                         (cudaStream_t)stream);
+}
+
+gs_status gs_replay_jvp(const gs_record* rec, const double* params, const double* y0, int n_dir,
+                        const double* params_dot, const double* y0_dot, double* loss_out, double* loss_dot,
+                        double* y_save_dot, gs_stream stream) {
+  if (!rec) return GS_ERR_INVALID_ARG;
+  if (n_dir < 1 || !loss_dot) return GS_ERR_INVALID_ARG;
+  if (rec->n == 0) return GS_OK;
+  JvpArgs a;
+  const gs_status st = jvp_common(rec, params, y0, &a);
+  if (st != GS_OK) return st;
+  a.params_dot = params_dot;
+  a.y0_dot = y0_dot;
+  a.loss_dot = loss_dot;
+  a.y_save_dot = y_save_dot;
+  return launch_jvp_range(rec, a, 0, n_dir, loss_out, (cudaStream_t)stream);
+}
+
+gs_status gs_forward_grad(const gs_record* rec, const double* params, const double* y0, double* loss_out,
+                          double* params_bar, double* y0_bar, gs_stream stream) {
+  if (!rec) return GS_ERR_INVALID_ARG;
+  if (!params_bar && !y0_bar) return GS_ERR_INVALID_ARG;
+  if (rec->n == 0) return GS_OK;
+  JvpArgs a;
+  const gs_status st = jvp_common(rec, params, y0, &a);
+  if (st != GS_OK) return st;
+  a.basis = 1;
+  a.grad_p = params_bar;
+  a.grad_y = y0_bar;
+  const int g0 = params_bar ? 0 : rec->P;
+  const int g1 = y0_bar ? rec->P + rec->d : rec->P;
+  return launch_jvp_range(rec, a, g0, g1, loss_out, (cudaStream_t)stream);
 }
 
 gs_status gs_record_refresh(gs_record* rec, const double* params, const double* y0, const float* shared_w,

@@ -112,6 +112,14 @@ struct Lorenz {  // sigma (y - x), x (rho - z) - y, x y - beta z; theta = (sigma
     pb[1] = fma_(y[0], v[1], pb[1]);
     pb[2] = fma_(-y[2], v[2], pb[2]);
   }
+  // Tangent: o = J(y) yd + (df/dtheta) pd.
+  template <class R>
+  __device__ __forceinline__ static void jvp(const R (&y)[D], const R (&p)[NP], const R (&yd)[D], const R (&pd)[NP],
+                                             R (&o)[D]) {
+    o[0] = fma_(pd[0], sub_(y[1], y[0]), mul_(p[0], sub_(yd[1], yd[0])));
+    o[1] = fma_(yd[0], sub_(p[1], y[2]), fma_(y[0], sub_(pd[1], yd[2]), -yd[1]));
+    o[2] = fma_(yd[0], y[1], fma_(y[0], yd[1], -fma_(pd[2], y[2], mul_(p[2], yd[2]))));
+  }
 };
 
 struct VanDerPol {  // x' = v, v' = mu ((1 - x^2) v - x); theta = (mu)
@@ -130,6 +138,15 @@ struct VanDerPol {  // x' = v, v' = mu ((1 - x^2) v - x); theta = (mu)
     yb[0] = -mul_(mv, fma_(add_(y[0], y[0]), y[1], R(1)));
     yb[1] = fma_(mv, w, v[0]);
     pb[0] = fma_(fma_(w, y[1], -y[0]), v[1], pb[0]);
+  }
+  template <class R>
+  __device__ __forceinline__ static void jvp(const R (&y)[D], const R (&p)[NP], const R (&yd)[D], const R (&pd)[NP],
+                                             R (&o)[D]) {
+    const R w = fma_(-y[0], y[0], R(1));
+    const R g = fma_(w, y[1], -y[0]);                                              // (1 - x^2) v - x
+    const R gd = fma_(w, yd[1], fma_(mul_(-add_(y[0], y[0]), yd[0]), y[1], -yd[0]));  // its tangent
+    o[0] = yd[1];
+    o[1] = fma_(pd[0], g, mul_(p[0], gd));
   }
 };
 
@@ -164,6 +181,19 @@ struct Linear2 {  // y' = A y, A = [[p0, p1], [p2, p3]]
     gp[1] = fma_(r[0], u[1], gp[1]);
     gp[2] = fma_(r[1], u[0], gp[2]);
     gp[3] = fma_(r[1], u[1], gp[3]);
+  }
+  template <class R>
+  __device__ __forceinline__ static void jvp(const R (&y)[D], const R (&p)[NP], const R (&yd)[D], const R (&pd)[NP],
+                                             R (&o)[D]) {
+    o[0] = fma_(p[0], yd[0], fma_(p[1], yd[1], fma_(pd[0], y[0], mul_(pd[1], y[1]))));
+    o[1] = fma_(p[2], yd[0], fma_(p[3], yd[1], fma_(pd[2], y[0], mul_(pd[3], y[1]))));
+  }
+  // Directional derivative of the Jacobian applied to u: o = (dJ/dy[yd] + dJ/dtheta[pd]) u.
+  template <class R>
+  __device__ __forceinline__ static void jac_dir(const R (&y)[D], const R (&p)[NP], const R (&yd)[D],
+                                                 const R (&pd)[NP], const R (&u)[D], R (&o)[D]) {
+    o[0] = fma_(pd[0], u[0], mul_(pd[1], u[1]));
+    o[1] = fma_(pd[2], u[0], mul_(pd[3], u[1]));
   }
 };
 
@@ -208,6 +238,26 @@ struct Robertson {
     gp[0] = fma_(u[0], -r01, gp[0]);
     gp[1] = fma_(mul_(add_(y[1], y[1]), u[1]), r21, gp[1]);
     gp[2] = fma_(fma_(y[2], u[1], mul_(y[1], u[2])), r01, gp[2]);
+  }
+  template <class R>
+  __device__ __forceinline__ static void jvp(const R (&y)[D], const R (&p)[NP], const R (&yd)[D], const R (&pd)[NP],
+                                             R (&o)[D]) {
+    const R ad = fma_(pd[0], y[0], mul_(p[0], yd[0]));                                       // d(k1 y1)
+    const R bd = fma_(mul_(pd[2], y[1]), y[2], mul_(p[2], fma_(yd[1], y[2], mul_(y[1], yd[2]))));  // d(k3 y2 y3)
+    const R cd = fma_(mul_(pd[1], y[1]), y[1], mul_(add_(p[1], p[1]), mul_(y[1], yd[1])));        // d(k2 y2^2)
+    o[0] = sub_(bd, ad);
+    o[1] = sub_(sub_(ad, bd), cd);
+    o[2] = cd;
+  }
+  template <class R>
+  __device__ __forceinline__ static void jac_dir(const R (&y)[D], const R (&p)[NP], const R (&yd)[D],
+                                                 const R (&pd)[NP], const R (&u)[D], R (&o)[D]) {
+    const R e = fma_(pd[2], y[2], mul_(p[2], yd[2]));                   // d(k3 y3)
+    const R g = fma_(pd[2], y[1], mul_(p[2], yd[1]));                   // d(k3 y2)
+    const R q = mul_(R(2), fma_(pd[1], y[1], mul_(p[1], yd[1])));       // d(2 k2 y2)
+    o[0] = fma_(-pd[0], u[0], fma_(e, u[1], mul_(g, u[2])));
+    o[1] = fma_(pd[0], u[0], fma_(-add_(e, q), u[1], -mul_(g, u[2])));
+    o[2] = mul_(q, u[1]);
   }
 };
 
@@ -290,6 +340,39 @@ struct Hires {
     gp[10] = fma_(r[5], add_(u[3], u[6]), gp[10]);
     gp[11] = fma_(u[6], sub_(r[7], r[6]), gp[11]);
   }
+  template <class R>
+  __device__ __forceinline__ static void jvp(const R (&y)[D], const R (&p)[NP], const R (&yd)[D], const R (&pd)[NP],
+                                             R (&o)[D]) {
+    // each bilinear term p_i y_j contributes pd_i y_j + p_i yd_j; w = p9 y5 y7 (0-based)
+    auto dl = [](R pp, R ppd, R yy, R yyd) { return fma_(ppd, yy, mul_(pp, yyd)); };
+    const R wd = fma_(mul_(pd[9], y[5]), y[7], mul_(p[9], fma_(yd[5], y[7], mul_(y[5], yd[7]))));
+    o[0] = add_(sub_(add_(dl(p[2], pd[2], y[2], yd[2]), dl(p[1], pd[1], y[1], yd[1])), dl(p[0], pd[0], y[0], yd[0])),
+                pd[3]);
+    o[1] = sub_(dl(p[0], pd[0], y[0], yd[0]), dl(p[4], pd[4], y[1], yd[1]));
+    o[2] = sub_(add_(dl(p[6], pd[6], y[4], yd[4]), dl(p[1], pd[1], y[3], yd[3])), dl(p[5], pd[5], y[2], yd[2]));
+    o[3] = sub_(add_(dl(p[2], pd[2], y[1], yd[1]), dl(p[0], pd[0], y[2], yd[2])), dl(p[7], pd[7], y[3], yd[3]));
+    o[4] = sub_(dl(p[1], pd[1], add_(y[5], y[6]), add_(yd[5], yd[6])), dl(p[8], pd[8], y[4], yd[4]));
+    o[5] = sub_(sub_(add_(dl(p[10], pd[10], add_(y[3], y[6]), add_(yd[3], yd[6])), dl(p[0], pd[0], y[4], yd[4])),
+                     dl(p[1], pd[1], y[5], yd[5])),
+                wd);
+    const R z = dl(p[11], pd[11], y[6], yd[6]);
+    o[6] = sub_(wd, z);
+    o[7] = sub_(z, wd);
+  }
+  template <class R>
+  __device__ __forceinline__ static void jac_dir(const R (&y)[D], const R (&p)[NP], const R (&yd)[D],
+                                                 const R (&pd)[NP], const R (&u)[D], R (&o)[D]) {
+    const R a = fma_(pd[9], y[7], mul_(p[9], yd[7]));  // d(p9 y7)
+    const R b = fma_(pd[9], y[5], mul_(p[9], yd[5]));  // d(p9 y5)
+    o[0] = fma_(-pd[0], u[0], fma_(pd[1], u[1], mul_(pd[2], u[2])));
+    o[1] = fma_(pd[0], u[0], -mul_(pd[4], u[1]));
+    o[2] = fma_(-pd[5], u[2], fma_(pd[1], u[3], mul_(pd[6], u[4])));
+    o[3] = fma_(pd[2], u[1], fma_(pd[0], u[2], -mul_(pd[7], u[3])));
+    o[4] = fma_(-pd[8], u[4], mul_(pd[1], add_(u[5], u[6])));
+    o[5] = fma_(pd[10], add_(u[3], u[6]), fma_(pd[0], u[4], fma_(-add_(a, pd[1]), u[5], -mul_(b, u[7]))));
+    o[6] = fma_(a, u[5], fma_(-pd[11], u[6], mul_(b, u[7])));
+    o[7] = fma_(-a, u[5], fma_(pd[11], u[6], -mul_(b, u[7])));
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -365,6 +448,53 @@ __device__ __forceinline__ void tsit5_error(const R (&K)[7][Pb::D], R h, R (&e)[
 #pragma unroll
     for (int j = 1; j < 7; ++j) s = fma_(R(tsit5::Btilde(j)), K[j][c], s);
     e[c] = mul_(h, s);
+  }
+}
+
+// Forward mode of one Tsit5 step with h held as data: y_new (the same
+// arithmetic as tsit5_stages) and, for each of ND tangent directions
+// (yd, pd), yd_new = dPhi/dy yd + dPhi/dtheta pd, from the stage tangents
+// Yd_i = yd + h sum_j a_ij Kd_j, Kd_i = J(Y_i) Yd_i + f_theta(Y_i) pd.
+template <class Pb, int ND>
+__device__ __forceinline__ void tsit5_tangent(const double (&y)[Pb::D], const double (&yd)[ND][Pb::D],
+                                              const double (&p)[Pb::NP], const double (&pd)[ND][Pb::NP], double h,
+                                              double (&yn)[Pb::D], double (&ydn)[ND][Pb::D]) {
+  constexpr int D = Pb::D;
+  double K[6][D], Kd[6][ND][D];
+  Pb::f(y, p, K[0]);
+#pragma unroll
+  for (int q = 0; q < ND; ++q) Pb::jvp(y, p, yd[q], pd[q], Kd[0][q]);
+#pragma unroll
+  for (int i = 1; i < 7; ++i) {
+    double Y[D], Yd[ND][D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double s = mul_(tsit5::A(i, 0), K[0][c]);
+#pragma unroll
+      for (int j = 1; j < i; ++j) s = fma_(tsit5::A(i, j), K[j][c], s);
+      Y[c] = fma_(h, s, y[c]);
+    }
+#pragma unroll
+    for (int q = 0; q < ND; ++q)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        double s = mul_(tsit5::A(i, 0), Kd[0][q][c]);
+#pragma unroll
+        for (int j = 1; j < i; ++j) s = fma_(tsit5::A(i, j), Kd[j][q][c], s);
+        Yd[q][c] = fma_(h, s, yd[q][c]);
+      }
+    if (i < 6) {
+      Pb::f(Y, p, K[i]);
+#pragma unroll
+      for (int q = 0; q < ND; ++q) Pb::jvp(Y, p, Yd[q], pd[q], Kd[i][q]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < D; ++c) yn[c] = Y[c];
+#pragma unroll
+      for (int q = 0; q < ND; ++q)
+#pragma unroll
+        for (int c = 0; c < D; ++c) ydn[q][c] = Yd[q][c];
+    }
   }
 }
 

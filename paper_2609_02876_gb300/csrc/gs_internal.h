@@ -62,6 +62,39 @@ struct RevArgs {
   double save_t[MAX_SAVE_HOST];
 };
 
+// Arguments of the forward-mode (tangent) replay kernels. Direction q of a
+// launch is direction dir0 + q of the call.
+struct JvpArgs {
+  int64_t n;
+  const double* params;      // [P][n]
+  const double* y0;          // [d][n]
+  const double* params_dot;  // [ND][P][n] of this launch, or nullptr (zero); unused when basis
+  const double* y0_dot;      // [ND][d][n] of this launch, or nullptr (zero); unused when basis
+  int basis;                 // 1: direction g is the unit vector g of (theta, y0), g = dir0 + q
+  int dir0, nd;              // first direction of this launch, directions in it
+  double t0, t1;
+  int n_save;
+  double* loss;              // [n] or nullptr
+  double* loss_dot;          // [ND][n] of this launch (not basis), or nullptr
+  double* y_save_dot;        // [ND][n_save][d][n] of this launch (not basis), or nullptr
+  double* grad_p;            // basis: [P][n] or nullptr
+  double* grad_y;            // basis: [d][n] or nullptr
+  const int32_t* status;
+  const double* arena;
+  long long arena_cap;
+  const long long* head;
+  const int32_t* S;
+  unsigned long long* work;
+  int k, segw;
+  double save_t[MAX_SAVE_HOST];
+};
+
+constexpr int JVP_MAX_DIR = 3;  // tangent directions carried by one launch
+
+// Forward-mode replay: method GS_METHOD_TSIT5 (1) or GS_METHOD_RODAS5P (2).
+bool jvp_supports(int method, int problem);
+cudaError_t launch_jvp(int method, int problem, const JvpArgs& a, cudaStream_t s);
+
 struct LaunchCfg {
   int blocks;
   int threads;

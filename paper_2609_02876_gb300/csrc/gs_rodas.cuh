@@ -226,6 +226,89 @@ __device__ __forceinline__ bool rodas_step(const double (&y)[Pb::D], const doubl
   return ok;
 }
 
+// Forward mode of one Rodas5P step with h held as data: y_new (the arithmetic
+// of rodas_step) and, for each of ND tangent directions (yd, pd),
+//   W Ud_i = Fd_i + (1/h) sum_{j<i} C_ij Ud_j + Jd U_i,
+//   Fd_i = J(Y_i) Yd_i + f_theta(Y_i) pd,  Yd_i = yd + sum_{j<i} a_ij Ud_j,
+// where Jd = dJ(y)[yd, pd] (W = I/(h gamma) - J(y), so dW = -Jd), and
+// yd_new = Yd_8 + Ud_8. false if W is singular.
+template <class Pb, int ND>
+__device__ __forceinline__ bool rodas_tangent(const double (&y)[Pb::D], const double (&yd)[ND][Pb::D],
+                                              const double (&p)[Pb::NP], const double (&pd)[ND][Pb::NP], double h,
+                                              double (&yn)[Pb::D], double (&ydn)[ND][Pb::D]) {
+  constexpr int D = Pb::D;
+  double LU[D][D], rinv[D], U[8][D], Ud[8][ND][D];
+  int piv[D];
+  Pb::jac(y, p, LU);
+  const double inv_hg = 1.0 / mul_(h, rodas::GAMMA);
+  const double inv_h = 1.0 / h;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) LU[i][j] = -LU[i][j];
+    LU[i][i] = add_(LU[i][i], inv_hg);
+  }
+  const bool ok = lu_factor<D>(LU, piv, rinv);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    double Y[D], F[D], Rhs[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double s = y[c];
+#pragma unroll
+      for (int j = 0; j < i; ++j) s = fma_(rodas::a(i, j), U[j][c], s);
+      Y[c] = s;
+    }
+    Pb::f(Y, p, F);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      if (i == 0) {
+        Rhs[c] = F[c];
+      } else {
+        double s = mul_(rodas::C(i, 0), U[0][c]);
+#pragma unroll
+        for (int j = 1; j < i; ++j) s = fma_(rodas::C(i, j), U[j][c], s);
+        Rhs[c] = fma_(inv_h, s, F[c]);
+      }
+    }
+    lu_solve<D>(LU, piv, rinv, Rhs, U[i]);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      double Yd[D], Fd[D], JdU[D], Rd[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        double s = yd[q][c];
+#pragma unroll
+        for (int j = 0; j < i; ++j) s = fma_(rodas::a(i, j), Ud[j][q][c], s);
+        Yd[c] = s;
+      }
+      Pb::jvp(Y, p, Yd, pd[q], Fd);
+      Pb::jac_dir(y, p, yd[q], pd[q], U[i], JdU);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (i == 0) {
+          Rd[c] = add_(Fd[c], JdU[c]);
+        } else {
+          double s = mul_(rodas::C(i, 0), Ud[0][q][c]);
+#pragma unroll
+          for (int j = 1; j < i; ++j) s = fma_(rodas::C(i, j), Ud[j][q][c], s);
+          Rd[c] = add_(fma_(inv_h, s, Fd[c]), JdU[c]);
+        }
+      }
+      lu_solve<D>(LU, piv, rinv, Rd, Ud[i][q]);
+      if (i == 7) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) ydn[q][c] = add_(Yd[c], Ud[7][q][c]);
+      }
+    }
+    if (i == 7) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) yn[c] = add_(Y[c], U[7][c]);
+    }
+  }
+  return ok;
+}
+
 // Reverse of one Rodas5P step (h held as data) over its recomputed stages:
 // given the cotangent lam of y_new, returns v = dL/dy and accumulates dL/dtheta.
 //   Ubar_j = m_j lam;  for i = 8..1: Rbar_i = W^{-T} Ubar_i,

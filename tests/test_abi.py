@@ -110,3 +110,8 @@ def test_forward_only_solve_rejects_invalid_arguments(lib, kw, code):
 
 def test_forward_only_solve_of_an_empty_ensemble_is_a_no_op(lib):
     assert _call_solve(lib, n=0, params=None, y0=None, y_final=None, status=None) == N.GS_OK
+
+
+def test_forward_mode_entry_points_reject_invalid_arguments(lib):
+    assert lib.gs_replay_jvp(None, 1, 1, 1, None, None, None, 1, None, None) == N.GS_ERR_INVALID_ARG
+    assert lib.gs_forward_grad(None, 1, 1, None, 1, None, None) == N.GS_ERR_INVALID_ARG
