@@ -293,6 +293,40 @@ def forward_measure(args, steps=5):
     return res
 
 
+def forward_mode_measure(args, P, Y, wl, steps=3):
+    """The gradient with respect to theta by forward mode (gs_forward_grad: one pass
+    carrying the P unit directions) against the reverse sweep (gs_reverse) on the same
+    record of the bench workload; the paper's comparison of the two modes."""
+    import torch
+    from paper_2609_02876_gb300 import api
+    n = P.shape[1]
+    rec, _, st = api.forward_record(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                    layout="soa", want_saves=False)
+
+    def timed(f):
+        for _ in range(2):
+            f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    t_fwd = timed(lambda: api.forward_grad(rec, P, Y, wrt=("params",), layout="soa"))
+    t_rev = timed(lambda: api.reverse(rec, P, Y, layout="soa"))
+    fw = api.forward_grad(rec, P, Y, wrt=("params",), layout="soa")["params_bar"]
+    rv = api.reverse(rec, P, Y, layout="soa")["params_bar"]
+    den = rv.abs().amax(0).clamp_min(1e-300)
+    agree = ((fw - rv).abs().amax(0) / den).max().item()
+    rec.free()
+    return {"unit": "gradient trajectories/s (d loss / d theta, on a recorded mesh)",
+            "forward_mode": n / t_fwd, "reverse_mode": n / t_rev, "forward_ms": t_fwd * 1e3,
+            "reverse_ms": t_rev * 1e3, "max_rel_diff_forward_vs_reverse": agree}
+
+
 def config_of(args, n):
     wl = {"lorenz": "Lorenz-63 (sigma~U[8,12], rho~U[20,30], beta~U[2,3], y0~N((1,1,1),0.1^2 I), t in [0,1], "
                     "10 uniform saves)",
@@ -323,6 +357,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-forward", action="store_true")
+    ap.add_argument("--no-forward-mode", action="store_true")
     ap.add_argument("--forward-traj", type=int, default=1 << 24)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-log2n-max", type=int, default=18)
@@ -452,6 +487,8 @@ def main():
         line["fp32_mixed"] = {"value": n * args.steps / tm, "unit": UNIT, "ms_per_step": tm / args.steps * 1e3,
                               "dtype": "f32 stages/adjoint + f64 control",
                               "accuracy": accuracy_sample(args, "fp32_mixed")}
+    if rank == 0 and ws == 1 and not args.no_forward_mode and args.problem in ("lorenz", "vdp", "robertson"):
+        line["forward_vs_reverse_mode"] = forward_mode_measure(args, P, Y, wl)
     if rank == 0 and ws == 1 and not args.no_forward:
         line["forward_only"] = forward_measure(args)
     if rank == 0 and ws == 1 and not args.no_serve:

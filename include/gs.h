@@ -163,8 +163,10 @@ gs_status gs_record_refresh(gs_record* rec, const double* params, const double* 
  * Trajectories whose record is not GS_TRAJ_OK, or whose linear system turns
  * singular, get NaN. Lorenz, Van der Pol and GS_LINEAR (Tsit5), Robertson,
  * HIRES and GS_LINEAR (Rodas5P) records; GS_ERR_INVALID_ARG for others.
- * FP64 whatever the record's precision. Enqueued on `stream`, not
- * synchronised.
+ * FP64 whatever the record's precision. The first forward-mode call on a
+ * record allocates and fills an index of its segments in forward order (8
+ * bytes per segment and per trajectory, then included in gs_record_bytes).
+ * Enqueued on `stream`, not synchronised.
  */
 gs_status gs_replay_jvp(const gs_record* rec, const double* params, const double* y0, int n_dir,
                         const double* params_dot, const double* y0_dot, double* loss_out, double* loss_dot,

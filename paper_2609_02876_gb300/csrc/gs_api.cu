@@ -79,7 +79,11 @@ struct gs_record {
   Counters* ctr = nullptr;
   Counters* ctr_host = nullptr;  // pinned
   int64_t n_cap = 0;             // capacity of the per-trajectory arrays
-  size_t bytes = 0;
+  long long nseg_total = 0;      // segments the record holds
+  mutable size_t bytes = 0;
+  // forward-order segment index, built on the first forward-mode call
+  mutable long long* fwd_base = nullptr;
+  mutable long long* fwd_seg = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (optional)
 };
 
@@ -167,6 +171,8 @@ void destroy(gs_record* r) {
     if (r->ev[i]) cudaEventDestroy(r->ev[i]);
   free_arrays(r);
   cudaFree(r->arena);
+  cudaFree(r->fwd_base);
+  cudaFree(r->fwd_seg);
   cudaFree(r->ctr);
   cudaFree(r->wpart);
   cudaFreeHost(r->ctr_host);
@@ -283,6 +289,7 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
     if (ws != GS_OK) return ws;
     if (!r->ctr_host->overflow) {
       if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[0], r->ev[0], r->ev[1]);
+      r->nseg_total = (long long)r->ctr_host->arena_top;
       return GS_OK;
     }
     // The arena was too small: size it to the demand just measured (+1/8) and rerun.
@@ -413,13 +420,38 @@ gs_status launch_jvp_range(const gs_record* r, JvpArgs a, int g0, int g1, double
   return GS_OK;
 }
 
+// The record's segments in forward order (built once, on the stream of the
+// first forward-mode call).
+gs_status ensure_fwd_index(const gs_record* r, cudaStream_t s) {
+  if (r->fwd_base) return GS_OK;
+  long long* base = nullptr;
+  long long* seg = nullptr;
+  cudaError_t e = cudaMalloc(&base, (size_t)r->n * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&seg, (size_t)(r->nseg_total > 0 ? r->nseg_total : 1) * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(&r->ctr->work_jvp, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess)
+    e = launch_fwd_index(r->n, r->head, r->S, r->status, r->arena, r->arena_cap, r->k, r->segw, &r->ctr->work_jvp,
+                         base, seg, r->nseg_total, s);
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    cudaFree(seg);
+    return cuda_fail(e);
+  }
+  r->fwd_base = base;
+  r->fwd_seg = seg;
+  r->bytes += (size_t)(r->n + (r->nseg_total > 0 ? r->nseg_total : 1)) * sizeof(long long);
+  return GS_OK;
+}
+
 // The parts of the forward-mode arguments that come from the record.
-gs_status jvp_common(const gs_record* r, const double* params, const double* y0, JvpArgs* a) {
+gs_status jvp_common(const gs_record* r, const double* params, const double* y0, cudaStream_t s, JvpArgs* a) {
   if (!params || !y0) return GS_ERR_INVALID_ARG;
   if (!jvp_supports(r->method, r->problem)) return GS_ERR_INVALID_ARG;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != r->device) return GS_ERR_INVALID_ARG;
+  const gs_status st = ensure_fwd_index(r, s);
+  if (st != GS_OK) return st;
   std::memset(a, 0, sizeof(*a));
   a->n = r->n;
   a->params = params;
@@ -430,9 +462,9 @@ gs_status jvp_common(const gs_record* r, const double* params, const double* y0,
   std::memcpy(a->save_t, r->save_t, sizeof(double) * r->n_save);
   a->status = r->status;
   a->arena = r->arena;
-  a->arena_cap = r->arena_cap;
-  a->head = r->head;
   a->S = r->S;
+  a->fwd_base = r->fwd_base;
+  a->fwd_seg = r->fwd_seg;
   a->work = &r->ctr->work_jvp;
   a->k = r->k;
   a->segw = r->segw;
@@ -557,7 +589,7 @@ gs_status gs_replay_jvp(const gs_record* rec, const double* params, const double
   if (n_dir < 1 || !loss_dot) return GS_ERR_INVALID_ARG;
   if (rec->n == 0) return GS_OK;
   JvpArgs a;
-  const gs_status st = jvp_common(rec, params, y0, &a);
+  const gs_status st = jvp_common(rec, params, y0, (cudaStream_t)stream, &a);
   if (st != GS_OK) return st;
   a.params_dot = params_dot;
   a.y0_dot = y0_dot;
@@ -572,7 +604,7 @@ gs_status gs_forward_grad(const gs_record* rec, const double* params, const doub
   if (!params_bar && !y0_bar) return GS_ERR_INVALID_ARG;
   if (rec->n == 0) return GS_OK;
   JvpArgs a;
-  const gs_status st = jvp_common(rec, params, y0, &a);
+  const gs_status st = jvp_common(rec, params, y0, (cudaStream_t)stream, &a);
   if (st != GS_OK) return st;
   a.basis = 1;
   a.grad_p = params_bar;

@@ -81,15 +81,23 @@ struct JvpArgs {
   double* grad_y;            // basis: [d][n] or nullptr
   const int32_t* status;
   const double* arena;
-  long long arena_cap;
-  const long long* head;
   const int32_t* S;
+  const long long* fwd_base;  // [n] first entry of each trajectory in fwd_seg (-1: unusable)
+  const long long* fwd_seg;   // segment indices of every trajectory in forward order
   unsigned long long* work;
   int k, segw;
   double save_t[MAX_SAVE_HOST];
 };
 
 constexpr int JVP_MAX_DIR = 3;  // tangent directions carried by one launch
+
+// The record's segments in forward order: for every trajectory k with status
+// OK, fwd_seg[fwd_base[k] + i] is its i-th segment (fwd_base[k] = -1 if not
+// OK or if its chain leaves the arena). `top` is a zeroed counter; cap the
+// capacity of fwd_seg.
+cudaError_t launch_fwd_index(int64_t n, const long long* head, const int32_t* S, const int32_t* status,
+                             const double* arena, long long arena_cap, int k, int segw, unsigned long long* top,
+                             long long* fwd_base, long long* fwd_seg, long long cap, cudaStream_t s);
 
 // Forward-mode replay: method GS_METHOD_TSIT5 (1) or GS_METHOD_RODAS5P (2).
 bool jvp_supports(int method, int problem);

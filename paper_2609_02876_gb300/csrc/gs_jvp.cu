@@ -11,15 +11,44 @@
 // Scheduling follows the record kernel: one lane per trajectory, a warp-
 // aggregated ticket refill when a trajectory ends, and one convergent tangent
 // step per loop iteration for every lane that has a step or a side step to do.
-// The record links its segments last to first, so a lane collects the segment
-// indices of a window of JVP_RING segments in forward order by one backward
-// walk per window.
+// The record links its segments last to first; a separate index kernel lists
+// them in forward order once per record, so that no lane of the compute
+// kernel stalls its warp on a chain of dependent loads.
 #include "gs_kernels.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int JVP_RING = 64;
+// One thread per trajectory walks its chain from the last segment back to the
+// first and writes the indices in forward order. Latency-bound: launched with
+// as many resident threads as fit, so the dependent loads of many chains overlap.
+__global__ void __launch_bounds__(256) fwd_index_kernel(int64_t n, const long long* head, const int32_t* S,
+                                                        const int32_t* status, const double* arena,
+                                                        long long arena_cap, int k, int segw,
+                                                        unsigned long long* top, long long* fwd_base,
+                                                        long long* fwd_seg, long long cap) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long hd = head[t];
+    if (status[t] != TRAJ_OK || hd < 0) {
+      fwd_base[t] = -1;
+      continue;
+    }
+    const long long nseg = (S[t] + k - 1) / k;
+    const long long b = (long long)atomicAdd(top, (unsigned long long)nseg);
+    bool ok = (b + nseg <= cap);
+    long long seg = hd;
+    for (long long q = nseg - 1; q >= 0 && ok; --q) {
+      if (seg < 0 || seg >= arena_cap) {
+        ok = false;
+        break;
+      }
+      fwd_seg[b + q] = seg;
+      seg = __double_as_longlong(arena[seg * segw]);
+    }
+    fwd_base[t] = (ok && seg < 0) ? b : -1;  // the first segment links to -1
+  }
+}
+
 enum { J_NONE = 0, J_STEP, J_SIDE, J_DONE, J_FAIL };
 
 struct Tsit5Tangent {
@@ -104,12 +133,11 @@ __global__ void __launch_bounds__(TPB_REV) jvp_kernel(const JvpArgs a) {
   __syncthreads();
 
   const long long n = a.n;
-  long long ring[JVP_RING];
-  long long k = -1, cur = -1;
+  long long k = -1, cur = -1, fb = 0;
   bool drained = false;
   double y[D], yd[ND][D], p[NP], pd[ND][NP], ldot[ND];
   double t = 0.0, tn = 0.0, loss = 0.0;
-  int S = 0, nseg = 0, pos = -1, c0 = 0, c1 = 0, j = 0, m = 0, i = 0, js = 0;
+  int S = 0, nseg = 0, pos = -1, j = 0, m = 0, i = 0, js = 0;
 
   for (;;) {
     // ---- refill: lanes without a trajectory take the next ticket
@@ -119,7 +147,8 @@ __global__ void __launch_bounds__(TPB_REV) jvp_kernel(const JvpArgs a) {
       if (need) {
         if (got < n) {
           k = got;
-          if (a.status[k] != TRAJ_OK || a.head[k] < 0) {
+          fb = a.fwd_base[k];
+          if (a.status[k] != TRAJ_OK || fb < 0) {
             jvp_fail<D, NP, ND>(a, k);
             k = -1;  // take another ticket next iteration
           } else {
@@ -145,7 +174,6 @@ __global__ void __launch_bounds__(TPB_REV) jvp_kernel(const JvpArgs a) {
             S = a.S[k];
             nseg = (S + a.k - 1) / a.k;
             pos = -1;
-            c0 = c1 = 0;
             j = m = 0;
             i = 0;
             js = 0;
@@ -164,27 +192,9 @@ __global__ void __launch_bounds__(TPB_REV) jvp_kernel(const JvpArgs a) {
       for (;;) {
         double hi = 0.0;
         if (i < S) {  // the step out of mesh point i and the next mesh time
-          if (j == m) {
+          if (j == m) {  // next segment (pos < nseg while i < S; indices checked by the index kernel)
             ++pos;
-            if (pos >= c1) {  // collect the next window of segment indices
-              c0 = pos;
-              c1 = min(nseg, c0 + JVP_RING);
-              long long seg = a.head[k];
-              bool okw = true;
-              for (int q = nseg - 1; q >= c0; --q) {
-                if (seg < 0 || seg >= a.arena_cap) {
-                  okw = false;
-                  break;
-                }
-                if (q < c1) ring[q - c0] = seg;
-                seg = __double_as_longlong(a.arena[seg * a.segw]);
-              }
-              if (!okw) {
-                mode = J_FAIL;
-                break;
-              }
-            }
-            cur = ring[pos - c0];
+            cur = a.fwd_seg[fb + pos];
             m = (pos == nseg - 1) ? S - (nseg - 1) * a.k : a.k;
             j = 0;
           }
@@ -251,6 +261,20 @@ cudaError_t jvp_dispatch(const JvpArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_fwd_index(int64_t n, const long long* head, const int32_t* S, const int32_t* status,
+                             const double* arena, long long arena_cap, int k, int segw, unsigned long long* top,
+                             long long* fwd_base, long long* fwd_seg, long long cap, cudaStream_t s) {
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fwd_index_kernel, 256, 0);
+  long long blocks = (long long)sm_count() * (bps > 0 ? bps : 1);
+  const long long need = (n + 255) / 256;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  fwd_index_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, head, S, status, arena, arena_cap, k, segw, top, fwd_base,
+                                                     fwd_seg, cap);
+  return cudaGetLastError();
+}
 
 bool jvp_supports(int method, int problem) {
   if (method == 1) return problem == 0 || problem == 1 || problem == 4;  // Lorenz, Van der Pol, linear
