@@ -21,7 +21,7 @@ _SRC = os.path.join(_HERE, "gs_oracle.cpp")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 
 PROBLEMS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5}
-METHOD_AUTO, METHOD_TSIT5, METHOD_RODAS5P = 0, 1, 2
+METHOD_AUTO, METHOD_TSIT5, METHOD_RODAS5P, METHOD_ROSENBROCK23 = 0, 1, 2, 3
 TRAJ_OK, TRAJ_MAXSTEPS, TRAJ_DT_UNDERFLOW, TRAJ_NONFINITE, TRAJ_SINGULAR = 0, 1, 2, 3, 4
 
 
@@ -59,7 +59,7 @@ def lib():
         L.or_replay_jvp.argtypes = [i32, i32, i64, dp, dp, dp, d, d, dp, i32, lp, dp, dp, dp, dp, dp, dp, i32]
         L.or_step.argtypes = [i32, i32, i64, dp, dp, dp, dp, dp, dp]
         L.or_rhs.argtypes = [i32, i64, dp, dp, dp, dp, dp]
-        L.or_initial_step.argtypes = [i32, dp, dp, dp, d, d, d, d]
+        L.or_initial_step.argtypes = [i32, dp, dp, dp, d, d, d, d, i32]
         L.or_initial_step.restype = C.c_double
         _lib = L
     return _lib
@@ -197,9 +197,10 @@ def rhs(problem, params, y, w=None):
     return f, J
 
 
-def initial_step(problem, params, y0, t0, t1, rtol, atol, w=None):
+def initial_step(problem, params, y0, t0, t1, rtol, atol, w=None, order=5):
+    """Starting step (Hairer-Norsett-Wanner) for a method of the given order (5: Tsit5, Rodas5P; 2: Rosenbrock23)."""
     pid = _pid(problem)
-    return lib().or_initial_step(pid, _p(_arr(params)), _p(_arr(y0)), _p(_w(pid, w)), t0, t1, rtol, atol)
+    return lib().or_initial_step(pid, _p(_arr(params)), _p(_arr(y0)), _p(_w(pid, w)), t0, t1, rtol, atol, order)
 
 
 def solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, method=METHOD_AUTO, w=None, nthreads=0,

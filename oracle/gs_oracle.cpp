@@ -326,7 +326,7 @@ struct RodasTab {
 };
 const RodasTab& rodas() { static RodasTab t; return t; }
 
-enum { M_TSIT5 = 1, M_RODAS5P = 2 };
+enum { M_TSIT5 = 1, M_RODAS5P = 2, M_ROS23 = 3 };
 enum { TRAJ_OK = 0, TRAJ_MAXSTEPS = 1, TRAJ_DT_UNDERFLOW = 2, TRAJ_NONFINITE = 3, TRAJ_SINGULAR = 4 };
 
 // ---------------------------------------------------------------- Tsit5 step
@@ -539,6 +539,104 @@ bool rodas_step_vjp(const Prob& pr, const double* y, const double* p, double h, 
   return true;
 }
 
+// ---------------------------------------------------------------- Rosenbrock23
+// The second-order linearly implicit method of Shampine & Reichelt (1997), the
+// formulas of MATLAB's ode23s, for autonomous f (paper Sec. 3.2, its stiff
+// default for the fused kernels), with W = I - h d J(y):
+//   F0 = f(y),                  k1 = W^{-1} F0,
+//   F1 = f(y + h/2 k1),         k2 = W^{-1} (F1 - k1) + k1,
+//   y_new = y + h k2,
+//   F2 = f(y_new),              k3 = W^{-1} (F2 - e32 (k2 - F1) - 2 (k1 - F0)),
+//   e = h/6 (k1 - 2 k2 + k3),
+// with d = 1/(2 + sqrt 2) and e32 = 6 + sqrt 2. Outputs k1, u2 = W^{-1}(F1 - k1)
+// (so k2 = u2 + k1), the stage input Y1 = y + h/2 k1 and the LU of W.
+const double ROS23_D = 1.0 / (2.0 + std::sqrt(2.0));
+const double ROS23_E32 = 6.0 + std::sqrt(2.0);
+
+template <class T>
+bool ros23_step(const Prob& pr, const T* y, const T* p, double h, T* ynew, T* err, T* k1, T* u2, T* Y1,
+                T LU[DMAX][DMAX], int* perm) {
+  const int d = pr.d;
+  T J[DMAX][DMAX];
+  jac_y(pr, y, p, J);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) LU[i][j] = (i == j ? T(1.0) : T(0.0)) - (h * ROS23_D) * J[i][j];
+  if (!lu_factor(d, LU, perm)) return false;
+  T F0[DMAX], F1[DMAX], r[DMAX], k2[DMAX];
+  f_eval(pr, y, p, F0);
+  lu_solve(d, LU, perm, F0, k1);
+  for (int c = 0; c < d; ++c) Y1[c] = y[c] + (0.5 * h) * k1[c];
+  f_eval(pr, Y1, p, F1);
+  for (int c = 0; c < d; ++c) r[c] = F1[c] - k1[c];
+  lu_solve(d, LU, perm, r, u2);
+  for (int c = 0; c < d; ++c) {
+    k2[c] = u2[c] + k1[c];
+    ynew[c] = y[c] + h * k2[c];
+  }
+  if (err) {
+    T F2[DMAX], k3[DMAX];
+    f_eval(pr, ynew, p, F2);
+    for (int c = 0; c < d; ++c) r[c] = F2[c] - ROS23_E32 * (k2[c] - F1[c]) - 2.0 * (k1[c] - F0[c]);
+    lu_solve(d, LU, perm, r, k3);
+    for (int c = 0; c < d; ++c) err[c] = (h / 6.0) * (k1[c] - 2.0 * k2[c] + k3[c]);
+  }
+  return true;
+}
+
+// Reverse of one Rosenbrock23 step with h as data: with lam = dL/dy_new,
+//   k2bar = h lam;  r2bar = W^{-T} k2bar (u2 = W^{-1} r2, r2 = F1 - k1);
+//   F1bar = r2bar;  k1bar = k2bar - r2bar;
+//   Y1bar = J(Y1)^T F1bar, theta_bar += f_theta(Y1)^T F1bar;
+//   k1bar += h/2 Y1bar;  r1bar = W^{-T} k1bar (k1 = W^{-1} F0);
+//   ybar = lam + Y1bar + J(y)^T r1bar, theta_bar += f_theta(y)^T r1bar;
+// and W = I - h d J(y) gives dL/dJ = h d (r1bar k1^T + r2bar u2^T), contracted
+// through J(y, theta).
+bool ros23_step_vjp(const Prob& pr, const double* y, const double* p, double h, const double* lam, double* ybar,
+                    double* pbar, double* wbar) {
+  const int d = pr.d, P = pr.P;
+  double yn[DMAX], k1[DMAX], u2[DMAX], Y1[DMAX], LU[DMAX][DMAX];
+  int perm[DMAX];
+  if (!ros23_step(pr, y, p, h, yn, (double*)nullptr, k1, u2, Y1, LU, perm)) return false;
+  double k2b[DMAX], r2b[DMAX], k1b[DMAX], r1b[DMAX];
+  for (int c = 0; c < d; ++c) k2b[c] = h * lam[c];
+  lu_solve_t(d, LU, perm, k2b, r2b);
+  auto vjp_at = [&](const double* x, const double* v, double* xb) {  // xb = J(x)^T v; pbar += f_theta(x)^T v
+    double J[DMAX][DMAX], Fp[DMAX][PMAX];
+    jac_y(pr, x, p, J);
+    jac_p(pr, x, p, Fp);
+    for (int a = 0; a < d; ++a) {
+      double s = 0.0;
+      for (int c = 0; c < d; ++c) s += J[c][a] * v[c];
+      xb[a] = s;
+    }
+    for (int q = 0; q < P; ++q) {
+      double s = 0.0;
+      for (int c = 0; c < d; ++c) s += Fp[c][q] * v[c];
+      pbar[q] += s;
+    }
+    if (wbar) ude_w_vjp(x, pr.w, v, wbar);
+  };
+  double Y1b[DMAX], y0b[DMAX];
+  vjp_at(Y1, r2b, Y1b);
+  for (int c = 0; c < d; ++c) k1b[c] = k2b[c] - r2b[c] + (0.5 * h) * Y1b[c];
+  lu_solve_t(d, LU, perm, k1b, r1b);
+  vjp_at(y, r1b, y0b);
+  for (int c = 0; c < d; ++c) ybar[c] = lam[c] + Y1b[c] + y0b[c];
+  double r1s[DMAX], r2s[DMAX];
+  for (int c = 0; c < d; ++c) {
+    r1s[c] = (h * ROS23_D) * r1b[c];
+    r2s[c] = (h * ROS23_D) * r2b[c];
+  }
+  double gy[DMAX], gp[PMAX];
+  jac_contract_grad(pr, y, p, r1s, k1, gy, gp);
+  for (int c = 0; c < d; ++c) ybar[c] += gy[c];
+  for (int q = 0; q < P; ++q) pbar[q] += gp[q];
+  jac_contract_grad(pr, y, p, r2s, u2, gy, gp);
+  for (int c = 0; c < d; ++c) ybar[c] += gy[c];
+  for (int q = 0; q < P; ++q) pbar[q] += gp[q];
+  return true;
+}
+
 // Generic one-step map Phi(y; h) for the chosen method.
 template <class T>
 bool phi_step(int method, const Prob& pr, const T* y, const T* p, double h, T* ynew) {
@@ -547,6 +645,11 @@ bool phi_step(int method, const Prob& pr, const T* y, const T* p, double h, T* y
     tsit5_step(pr, y, p, h, Ys, K, ynew, (T*)nullptr);
     return true;
   }
+  if (method == M_ROS23) {
+    T k1[DMAX], u2[DMAX], Y1[DMAX], LU[DMAX][DMAX];
+    int perm[DMAX];
+    return ros23_step(pr, y, p, h, ynew, (T*)nullptr, k1, u2, Y1, LU, perm);
+  }
   T Ys[8][DMAX], U[8][DMAX], LU[DMAX][DMAX];
   int perm[DMAX];
   return rodas_step(pr, y, p, h, Ys, U, ynew, (T*)nullptr, LU, perm);
@@ -554,8 +657,14 @@ bool phi_step(int method, const Prob& pr, const T* y, const T* p, double h, T* y
 bool phi_step_vjp(int method, const Prob& pr, const double* y, const double* p, double h, const double* lam,
                   double* ybar, double* pbar, double* wbar) {
   if (method == M_TSIT5) { tsit5_step_vjp(pr, y, p, h, lam, ybar, pbar, wbar); return true; }
+  if (method == M_ROS23) return ros23_step_vjp(pr, y, p, h, lam, ybar, pbar, wbar);
   return rodas_step_vjp(pr, y, p, h, lam, ybar, pbar, wbar);
 }
+// Order of the method's solution (the starting step) and the lower order q of its
+// error estimate (the controller exponent 1/(q+1)): Tsit5 and Rodas5P 5 and 4,
+// Rosenbrock23 2 and 2.
+int method_order(int method) { return method == M_ROS23 ? 2 : 5; }
+int method_err_order(int method) { return method == M_ROS23 ? 2 : 4; }
 
 // ---------------------------------------------------------------- record
 // Weighted RMS norm of the paper's Sec. 2.1: sqrt(mean_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2).
@@ -575,9 +684,9 @@ double rms_scaled(int d, const double* v, const double* sc) {
 }
 
 // Starting step: the algorithm of Hairer, Norsett & Wanner, Vol. I, Sec. II.4,
-// with order p = 5, the same weighted RMS norm, and one explicit Euler probe.
+// with the method's order p, the same weighted RMS norm, and one explicit Euler probe.
 double initial_step(const Prob& pr, const double* y0, const double* p, double t0, double t1, double rtol,
-                    double atol) {
+                    double atol, int order = 5) {
   const int d = pr.d;
   double f0[DMAX], sc[DMAX], y1[DMAX], f1[DMAX], df[DMAX];
   f_eval(pr, y0, p, f0);
@@ -590,15 +699,16 @@ double initial_step(const Prob& pr, const double* y0, const double* p, double t0
   for (int c = 0; c < d; ++c) df[c] = f1[c] - f0[c];
   double d2 = rms_scaled(d, df, sc) / h0;
   double dm = std::max(d1, d2);
-  double h1 = (dm <= 1e-15) ? std::max(1e-6, h0 * 1e-3) : std::pow(0.01 / dm, 1.0 / 6.0);
+  double h1 = (dm <= 1e-15) ? std::max(1e-6, h0 * 1e-3) : std::pow(0.01 / dm, 1.0 / (order + 1));
   return std::min(std::min(100.0 * h0, h1), t1 - t0);
 }
 
-// Step-size factor of the integral controller: clamp(0.9 err^(-1/5), 0.2, 10)
-// (exponent 1/(q+1), q = 4 the embedded order); err = 0 gives 10.
-double ctrl_factor(double err) {
+// Step-size factor of the integral controller: clamp(0.9 err^(-1/(q+1)), 0.2, 10)
+// with q the lower order of the error estimate (4 for Tsit5 and Rodas5P, so
+// err^(-1/5); 2 for Rosenbrock23, err^(-1/3)); err = 0 gives 10.
+double ctrl_factor(double err, int q = 4) {
   if (!(err > 0.0)) return 10.0;
-  double f = 0.9 * std::pow(err, -0.2);
+  double f = 0.9 * std::pow(err, -1.0 / (q + 1));
   return std::min(10.0, std::max(0.2, f));
 }
 
@@ -619,7 +729,7 @@ RecordOut record_one(int method, const Prob& pr, const double* y0, const double*
   double y[DMAX], yn[DMAX], e[DMAX];
   for (int c = 0; c < d; ++c) y[c] = y0[c];
   double t = t0;
-  double h = h_init > 0.0 ? h_init : initial_step(pr, y0, p, t0, t1, rtol, atol);
+  double h = h_init > 0.0 ? h_init : initial_step(pr, y0, p, t0, t1, rtol, atol, method_order(method));
   const double sliver = 1e-12 * std::max(1.0, std::fabs(t1));
   bool reject_prev = false, last_nonfinite = false;
   int js = 0;
@@ -638,6 +748,10 @@ RecordOut record_one(int method, const Prob& pr, const double* y0, const double*
       double Ys[7][DMAX], K[7][DMAX];
       tsit5_step(pr, y, p, h, Ys, K, yn, e);
       ok = true;
+    } else if (method == M_ROS23) {
+      double k1[DMAX], u2[DMAX], Y1[DMAX], LU[DMAX][DMAX];
+      int perm[DMAX];
+      ok = ros23_step(pr, y, p, h, yn, e, k1, u2, Y1, LU, perm);
     } else {
       double Ys[8][DMAX], U[8][DMAX], LU[DMAX][DMAX];
       int perm[DMAX];
@@ -672,14 +786,14 @@ RecordOut record_one(int method, const Prob& pr, const double* y0, const double*
       t = t_new;
       for (int c = 0; c < d; ++c) y[c] = yn[c];
       if (last) return out;
-      double fac = ctrl_factor(err);
+      double fac = ctrl_factor(err, method_err_order(method));
       if (reject_prev) fac = std::min(fac, 1.0);
       reject_prev = false;
       last_nonfinite = false;
       h = h * fac;
     } else {
       last_nonfinite = !std::isfinite(err);
-      double fac = last_nonfinite ? 0.2 : ctrl_factor(err);
+      double fac = last_nonfinite ? 0.2 : ctrl_factor(err, method_err_order(method));
       h = h * fac;
       reject_prev = true;
     }
@@ -937,6 +1051,10 @@ int or_step(int pid, int method, int64_t n, const double* params, const double* 
     if (method == M_TSIT5) {
       double Ys[7][DMAX], K[7][DMAX];
       tsit5_step(pr, yk, pk, h[k], Ys, K, ynew + k * pr.d, err + k * pr.d);
+    } else if (method == M_ROS23) {
+      double k1[DMAX], u2[DMAX], Y1[DMAX], LU[DMAX][DMAX];
+      int perm[DMAX];
+      if (!ros23_step(pr, yk, pk, h[k], ynew + k * pr.d, err + k * pr.d, k1, u2, Y1, LU, perm)) return 2;
     } else {
       double Ys[8][DMAX], U[8][DMAX], LU[DMAX][DMAX];
       int perm[DMAX];
@@ -964,9 +1082,9 @@ int or_rhs(int pid, int64_t n, const double* params, const double* y, const doub
 }
 
 double or_initial_step(int pid, const double* params, const double* y0, const double* w, double t0, double t1,
-                       double rtol, double atol) {
+                       double rtol, double atol, int order) {
   Prob pr{pid, dim_of(pid), npar_of(pid), w};
-  return initial_step(pr, y0, params, t0, t1, rtol, atol);
+  return initial_step(pr, y0, params, t0, t1, rtol, atol, order);
 }
 
 }  // extern "C"
