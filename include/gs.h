@@ -64,8 +64,10 @@ enum { GS_LORENZ = 0, GS_VDP = 1, GS_ROBERTSON = 2, GS_HIRES = 3, GS_LINEAR = 4,
 enum { GS_FP64 = 0, GS_FP32_MIXED = 1 };
 
 /* One-step methods (paper Sec. 3.2): Tsit5 (Tsitouras 2011) for non-stiff
- * problems, Rodas5P (Steinebach 2023) for stiff ones. AUTO picks by problem. */
-enum { GS_METHOD_AUTO = 0, GS_METHOD_TSIT5 = 1, GS_METHOD_RODAS5P = 2 };
+ * problems, Rodas5P (Steinebach 2023) for stiff ones, and the second-order
+ * Rosenbrock23 (Shampine & Reichelt 1997, the ode23s formulas) for stiff
+ * ones on request. AUTO picks Tsit5 or Rodas5P by problem. */
+enum { GS_METHOD_AUTO = 0, GS_METHOD_TSIT5 = 1, GS_METHOD_RODAS5P = 2, GS_METHOD_ROSENBROCK23 = 3 };
 
 typedef struct {
   int precision;        /* GS_FP64 or GS_FP32_MIXED */
@@ -162,7 +164,8 @@ gs_status gs_record_refresh(gs_record* rec, const double* params, const double* 
  * loss_out [n] and y_save_dot [n_dir][n_save][d][n] (either may be NULL).
  * Trajectories whose record is not GS_TRAJ_OK, or whose linear system turns
  * singular, get NaN. Lorenz, Van der Pol and GS_LINEAR (Tsit5), Robertson,
- * HIRES and GS_LINEAR (Rodas5P) records; GS_ERR_INVALID_ARG for others.
+ * HIRES and GS_LINEAR (Rodas5P, Rosenbrock23) records; GS_ERR_INVALID_ARG for
+ * others.
  * FP64 whatever the record's precision. The first forward-mode call on a
  * record allocates and fills an index of its segments in forward order (8
  * bytes per segment and per trajectory, then included in gs_record_bytes).

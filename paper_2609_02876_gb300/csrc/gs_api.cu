@@ -190,6 +190,18 @@ struct Call {
   double timeout_ms;
 };
 
+// Kernel launches by method.
+cudaError_t launch_forward_m(int method, int problem, int precision, const FwdArgs& a, cudaStream_t s) {
+  if (method == GS_METHOD_RODAS5P) return launch_rodas_forward(problem, precision, a, s);
+  if (method == GS_METHOD_ROSENBROCK23) return launch_ros23_forward(problem, precision, a, s);
+  return launch_tsit5_forward(problem, precision, a, s);
+}
+cudaError_t launch_reverse_m(int method, int problem, int precision, const RevArgs& a, cudaStream_t s) {
+  if (method == GS_METHOD_RODAS5P) return launch_rodas_reverse(problem, precision, a, s);
+  if (method == GS_METHOD_ROSENBROCK23) return launch_ros23_reverse(problem, precision, a, s);
+  return launch_tsit5_reverse(problem, precision, a, s);
+}
+
 // Waits for the work queued on s, polling with a deadline when timeout_ms > 0.
 gs_status wait_stream(cudaStream_t s, double timeout_ms) {
   if (!(timeout_ms > 0.0)) return cudaStreamSynchronize(s) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
@@ -225,7 +237,8 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   if (opt) o = *opt;
   if (o.precision != GS_FP64 && o.precision != GS_FP32_MIXED) return GS_ERR_INVALID_ARG;
   int method = o.method == GS_METHOD_AUTO ? (c->pi.stiff ? GS_METHOD_RODAS5P : GS_METHOD_TSIT5) : o.method;
-  if (method != GS_METHOD_TSIT5 && method != GS_METHOD_RODAS5P) return GS_ERR_INVALID_ARG;
+  if (method != GS_METHOD_TSIT5 && method != GS_METHOD_RODAS5P && method != GS_METHOD_ROSENBROCK23)
+    return GS_ERR_INVALID_ARG;
   if (o.ckpt_k < 0 || o.ckpt_k > KMAX_HOST) return GS_ERR_INVALID_ARG;
   if (c->pi.n_shared > 0 && o.ckpt_k > 1) return GS_ERR_INVALID_ARG;  // shared weights: every state stored
   if (o.max_steps < 0 || !std::isfinite(o.h0) || o.h0 < 0) return GS_ERR_INVALID_ARG;
@@ -240,6 +253,7 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   c->timeout_ms = o.timeout_ms;
   if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_RODAS5P && !rodas_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
+  if (method == GS_METHOD_ROSENBROCK23 && !ros23_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   return GS_OK;
 }
 
@@ -279,8 +293,7 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
     a.y_final = r->y_final;
     a.work = &r->ctr->work_fwd;
     if (c.kernel_ms) cudaEventRecord(r->ev[0], s);
-    e = (c.method == GS_METHOD_RODAS5P) ? launch_rodas_forward(c.problem, c.precision, a, s)
-                                        : launch_tsit5_forward(c.problem, c.precision, a, s);
+    e = launch_forward_m(c.method, c.problem, c.precision, a, s);
     if (e != cudaSuccess) return GS_ERR_CUDA;
     if (c.kernel_ms) cudaEventRecord(r->ev[1], s);
     e = cudaMemcpyAsync(r->ctr_host, r->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);
@@ -387,8 +400,7 @@ gs_status launch_reverse(const gs_record* r, const double* params, const float* 
   a.segw = r->segw;
   cudaError_t e = cudaMemsetAsync(&r->ctr->work_rev, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  e = (r->method == GS_METHOD_RODAS5P) ? launch_rodas_reverse(r->problem, r->precision, a, s)
-                                       : launch_tsit5_reverse(r->problem, r->precision, a, s);
+  e = launch_reverse_m(r->method, r->problem, r->precision, a, s);
   return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
@@ -641,6 +653,8 @@ gs_status gs_record_refresh(gs_record* rec, const double* params, const double* 
   const cudaError_t e =
       (rec->method == GS_METHOD_RODAS5P)
           ? launch_rodas_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s)
+      : (rec->method == GS_METHOD_ROSENBROCK23)
+          ? launch_ros23_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s)
           : launch_tsit5_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s);
   return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
@@ -707,8 +721,7 @@ gs_status gs_solve(int problem_id, int64_t n, const double* params, const double
   cudaError_t e = cudaMemsetAsync(r->ctr, 0, sizeof(Counters), s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (c.kernel_ms) cudaEventRecord(r->ev[0], s);
-  e = (c.method == GS_METHOD_RODAS5P) ? launch_rodas_forward(c.problem, c.precision, a, s)
-                                      : launch_tsit5_forward(c.problem, c.precision, a, s);
+  e = launch_forward_m(c.method, c.problem, c.precision, a, s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   if (c.kernel_ms) cudaEventRecord(r->ev[1], s);
   e = cudaMemcpyAsync(r->ctr_host, r->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s);

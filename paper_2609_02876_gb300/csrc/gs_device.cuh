@@ -635,20 +635,24 @@ __device__ __forceinline__ double err_meansq(const float (&e)[D], const float (&
   return mul_(q, 1.0 / D);
 }
 
-// Integral-controller factor from the mean-square error q = err^2:
-// clamp(0.9 err^(-1/5), 0.2, 10) = clamp(0.9 q^(-1/10), 0.2, 10); q = 0 gives 10.
-// FP32 with the hardware log2 / exp2: the factor only scales the next trial step.
+// Integral-controller factor from the mean-square error q = err^2, for an
+// error estimate of lower order Q: clamp(0.9 err^(-1/(Q+1)), 0.2, 10) =
+// clamp(0.9 q^(-1/(2(Q+1))), 0.2, 10) (Q = 4: Tsit5, Rodas5P; Q = 2:
+// Rosenbrock23); q = 0 gives 10. FP32 with the hardware log2 / exp2: the factor
+// only scales the next trial step.
+template <int Q>
 __device__ __forceinline__ float ctrl_factor(double q) {
+  constexpr float EXPO = -0.5f / (Q + 1);
   if (!positive(q)) return 10.0f;
-  const float f = __fmul_rn(0.9f, ex2_approx(__fmul_rn(-0.1f, lg2_approx(to_f(q)))));
+  const float f = __fmul_rn(0.9f, ex2_approx(__fmul_rn(EXPO, lg2_approx(to_f(q)))));
   return fminf(10.0f, fmaxf(0.2f, f));
 }
 
 // Starting step: the algorithm of Hairer, Norsett & Wanner, Vol. I, Sec. II.4
-// (order p = 5, the weighted RMS norm, one explicit Euler probe), evaluated in
-// FP32 from y0, theta and f(y0): it only picks the first trial step. Returns a
-// non-finite value if the inputs overflow FP32.
-template <class Pb>
+// (the method's order p, the weighted RMS norm, one explicit Euler probe),
+// evaluated in FP32 from y0, theta and f(y0): it only picks the first trial
+// step. Returns a non-finite value if the inputs overflow FP32.
+template <class Pb, int ORDER>
 __device__ __forceinline__ double initial_step_f32(const float (&y0)[Pb::D], const float (&p)[Pb::NP],
                                                    const float (&f0)[Pb::D], double t0, double t1, double rtol,
                                                    double atol) {
@@ -678,7 +682,7 @@ __device__ __forceinline__ double initial_step_f32(const float (&y0)[Pb::D], con
   }
   d2 = sqrtf(d2 / D) / h0;
   const float dm = fmaxf(d1, d2);
-  const float h1 = (dm <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : ex2_approx(lg2_approx(0.01f / dm) * (1.0f / 6.0f));
+  const float h1 = (dm <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : ex2_approx(lg2_approx(0.01f / dm) * (1.0f / (ORDER + 1)));
   return (double)fminf(fminf(100.0f * h0, h1), span);
 }
 

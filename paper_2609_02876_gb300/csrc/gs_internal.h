@@ -99,7 +99,7 @@ cudaError_t launch_fwd_index(int64_t n, const long long* head, const int32_t* S,
                              const double* arena, long long arena_cap, int k, int segw, unsigned long long* top,
                              long long* fwd_base, long long* fwd_seg, long long cap, cudaStream_t s);
 
-// Forward-mode replay: method GS_METHOD_TSIT5 (1) or GS_METHOD_RODAS5P (2).
+// Forward-mode replay: method GS_METHOD_TSIT5 (1), GS_METHOD_RODAS5P (2) or GS_METHOD_ROSENBROCK23 (3).
 bool jvp_supports(int method, int problem);
 cudaError_t launch_jvp(int method, int problem, const JvpArgs& a, cudaStream_t s);
 
@@ -117,6 +117,11 @@ bool tsit5_supports(int problem, int precision);
 cudaError_t launch_rodas_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_rodas_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
 bool rodas_supports(int problem, int precision);
+cudaError_t launch_ros23_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_ros23_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
+bool ros23_supports(int problem, int precision);
+cudaError_t launch_ros23_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
+                                 const double* y0, cudaStream_t s);
 // Frozen-mesh refresh: re-run each trajectory's state chain over its recorded
 // mesh with a.params and y0, rewriting the record's states and y(t1).
 cudaError_t launch_tsit5_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,

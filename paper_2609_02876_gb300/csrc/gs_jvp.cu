@@ -70,6 +70,15 @@ struct RodasTangent {
   }
 };
 
+struct Ros23Tangent {
+  template <class Pb, int ND>
+  __device__ __forceinline__ static bool step(const double (&y)[Pb::D], const double (&yd)[ND][Pb::D],
+                                              const double (&p)[Pb::NP], const double (&pd)[ND][Pb::NP], double h,
+                                              double (&yn)[Pb::D], double (&ydn)[ND][Pb::D]) {
+    return ros23_tangent<Pb, ND>(y, yd, p, pd, h, yn, ydn);
+  }
+};
+
 // Outputs of trajectory k: the loss and, per direction, its derivative (into
 // loss_dot, or in basis mode into the gradient row of that input).
 template <int NP, int ND>
@@ -218,7 +227,11 @@ __global__ void __launch_bounds__(TPB_REV) jvp_kernel(const JvpArgs a) {
       }
     }
 
-    // ---- one tangent step for every lane with a step or a side step
+    // ---- one tangent step for every lane with a step or a side step. The
+    // mode is made opaque to the optimiser, so that steps and side steps share
+    // one copy of the unit and the warp runs it once with all its busy lanes.
+    __syncwarp();
+    asm volatile("" : "+r"(mode));
     if (mode == J_STEP || mode == J_SIDE) {
       double yn[D], ydn[ND][D];
       const bool ok = T::template step<Pb, ND>(y, yd, p, pd, uh, yn, ydn);
@@ -278,7 +291,7 @@ cudaError_t launch_fwd_index(int64_t n, const long long* head, const int32_t* S,
 
 bool jvp_supports(int method, int problem) {
   if (method == 1) return problem == 0 || problem == 1 || problem == 4;  // Lorenz, Van der Pol, linear
-  if (method == 2) return problem == 2 || problem == 3 || problem == 4;  // Robertson, HIRES, linear
+  if (method == 2 || method == 3) return problem == 2 || problem == 3 || problem == 4;  // Robertson, HIRES, linear
   return false;
 }
 
@@ -294,6 +307,12 @@ cudaError_t launch_jvp(int method, int problem, const JvpArgs& a, cudaStream_t s
       case 2: return jvp_dispatch<RodasTangent, Robertson>(a, s);
       case 3: return jvp_dispatch<RodasTangent, Hires>(a, s);
       case 4: return jvp_dispatch<RodasTangent, Linear2>(a, s);
+    }
+  } else if (method == 3) {
+    switch (problem) {
+      case 2: return jvp_dispatch<Ros23Tangent, Robertson>(a, s);
+      case 3: return jvp_dispatch<Ros23Tangent, Hires>(a, s);
+      case 4: return jvp_dispatch<Ros23Tangent, Linear2>(a, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -79,6 +79,7 @@ __device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bo
 // Methods
 // ---------------------------------------------------------------------------
 struct Tsit5Method {
+  static constexpr int ORDER = 5, ERR_ORDER = 4;  // solution order; lower order of the error estimate
   template <class Pb, class R>
   struct Carry {
     R k1[Pb::D];  // FSAL: f(y) of the current accepted state
@@ -158,6 +159,7 @@ struct Tsit5Method {
 };
 
 struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
+  static constexpr int ORDER = 5, ERR_ORDER = 4;
   template <class Pb, class R>
   struct Carry {};
   template <class Pb, class R>
@@ -211,6 +213,71 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
     double cv[D], v[D];
     unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
     rodas_reverse<Pb>(x, p, h, Y, U, LU, piv, rinv, cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
+    return ok;
+  }
+};
+
+// Rosenbrock23 (FP64 only): second order, error estimate of order 2 (err^(-1/3)
+// controller), f at the accepted state carried to the next step.
+struct Ros23Method {
+  static constexpr int ORDER = 2, ERR_ORDER = 2;
+  template <class Pb, class R>
+  struct Carry {
+    R F0[Pb::D];  // f(y) of the current accepted state
+  };
+  template <class Pb, class R>
+  __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>& cy,
+                                               float (&f0)[Pb::D]) {
+    Pb::f(y, p, cy.F0);
+#pragma unroll
+    for (int c = 0; c < Pb::D; ++c) f0[c] = (float)cy.F0[c];
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                               const Carry<Pb, R>& cy, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                               Carry<Pb, R>& next) {
+    static_assert(std::is_same<R, double>::value, "Rosenbrock23 runs in FP64");
+    return ros23_trial<Pb>(y, p, h, cy.F0, ynew, e, next.F0);
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool side(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                              const Carry<Pb, R>& cy, R (&ys)[Pb::D]) {
+    constexpr int D = Pb::D;
+    double LU[D][D], rinv[D], k1[D], u2[D], Y1[D], F1[D];
+    int piv[D];
+    const bool ok = ros23_factor<Pb>(y, p, h, LU, piv, rinv);
+    ros23_stages<Pb>(y, p, h, cy.F0, LU, piv, rinv, k1, u2, Y1, F1, ys);
+    return ok;
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool replay_step(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                     R (&ynew)[Pb::D]) {
+    constexpr int D = Pb::D;
+    double LU[D][D], rinv[D], F0[D], k1[D], u2[D], Y1[D], F1[D];
+    int piv[D];
+    const bool ok = ros23_factor<Pb>(y, p, h, LU, piv, rinv);
+    Pb::f(y, p, F0);
+    ros23_stages<Pb>(y, p, h, F0, LU, piv, rinv, k1, u2, Y1, F1, ynew);
+    return ok;
+  }
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, bool active, int us,
+                                              const R (&x)[Pb::D], double h, const R (&p)[Pb::NP], R (&lam)[Pb::D],
+                                              Acc& pacc, double& loss, R (&ynew)[Pb::D]) {
+    static_assert(std::is_same<R, double>::value, "Rosenbrock23 runs in FP64");
+    constexpr int D = Pb::D;
+    double LU[D][D], rinv[D], F0[D], k1[D], u2[D], Y1[D], F1[D];
+    int piv[D];
+    const bool ok = ros23_factor<Pb>(x, p, h, LU, piv, rinv);
+    Pb::f(x, p, F0);
+    ros23_stages<Pb>(x, p, h, F0, LU, piv, rinv, k1, u2, Y1, F1, ynew);
+    if (mode == U_RECOMP) return ok;
+    const bool side = (mode == U_SIDE);
+    double cv[D], v[D];
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
+    ros23_reverse<Pb>(x, p, h, k1, u2, Y1, LU, piv, rinv, cv, v, pacc);
 #pragma unroll
     for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
     return ok;
@@ -275,7 +342,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           rej = lastnf = lastsing = false;
           prev = -1;
           M::template start<Pb, R>(y, p, cy, ff);
-          h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
+          h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
           fin = fin && isfinite(h) && h > 0.0;
           pending_fail = !fin;
           if (!fin) status = TRAJ_NONFINITE;
@@ -354,7 +421,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       // rejection), rejected ones shrink by the same rule, x0.2 on a non-finite
       // error, x0.25 when the step's linear system is singular
       const bool nf = solved && !finite_nonneg(q);
-      float fac = !solved ? 0.25f : (nf ? 0.2f : ctrl_factor(q));
+      float fac = !solved ? 0.25f : (nf ? 0.2f : ctrl_factor<M::ERR_ORDER>(q));
       if (accept && rej) fac = fminf(fac, 1.0f);
       h = mul_(h, to_d(fac));
       rej = !accept;

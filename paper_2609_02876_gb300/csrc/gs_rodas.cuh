@@ -352,4 +352,152 @@ __device__ __forceinline__ void rodas_reverse(const double (&y)[Pb::D], const do
   }
 }
 
+// ---------------------------------------------------------------------------
+// Rosenbrock23 (Shampine & Reichelt 1997, the ode23s formulas; the paper's
+// second-order stiff method, Sec. 3.2), autonomous f, W = I - h d J(y):
+//   k1 = W^{-1} F0 (F0 = f(y)),  Y1 = y + h/2 k1,  F1 = f(Y1),
+//   u2 = W^{-1} (F1 - k1),  k2 = u2 + k1,  y_new = y + h k2,
+//   F2 = f(y_new),  k3 = W^{-1} (F2 - e32 (k2 - F1) - 2 (k1 - F0)),
+//   e = h/6 (k1 - 2 k2 + k3);  d = 1/(2 + sqrt 2), e32 = 6 + sqrt 2.
+// F2 is f at the next accepted state (first-same-as-last).
+// ---------------------------------------------------------------------------
+namespace ros23 {
+constexpr double DC = 0.2928932188134525;   // 1 / (2 + sqrt 2)
+constexpr double E32 = 7.414213562373095;   // 6 + sqrt 2
+}  // namespace ros23
+
+// W = I - h d J(y), factored. false if singular.
+template <class Pb>
+__device__ __forceinline__ bool ros23_factor(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
+                                             double (&LU)[Pb::D][Pb::D], int (&piv)[Pb::D], double (&rinv)[Pb::D]) {
+  constexpr int D = Pb::D;
+  Pb::jac(y, p, LU);
+  const double mhd = -mul_(h, ros23::DC);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) LU[i][j] = mul_(mhd, LU[i][j]);
+    LU[i][i] = add_(LU[i][i], 1.0);
+  }
+  return lu_factor<D>(LU, piv, rinv);
+}
+
+// The replay map with its stage quantities: k1, u2, Y1, F1 and y_new, from
+// y, F0 = f(y) and the factored W.
+template <class Pb>
+__device__ __forceinline__ void ros23_stages(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
+                                             const double (&F0)[Pb::D], const double (&LU)[Pb::D][Pb::D],
+                                             const int (&piv)[Pb::D], const double (&rinv)[Pb::D],
+                                             double (&k1)[Pb::D], double (&u2)[Pb::D], double (&Y1)[Pb::D],
+                                             double (&F1)[Pb::D], double (&ynew)[Pb::D]) {
+  constexpr int D = Pb::D;
+  lu_solve<D>(LU, piv, rinv, F0, k1);
+  const double hh = mul_(0.5, h);
+#pragma unroll
+  for (int c = 0; c < D; ++c) Y1[c] = fma_(hh, k1[c], y[c]);
+  Pb::f(Y1, p, F1);
+  double r[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) r[c] = sub_(F1[c], k1[c]);
+  lu_solve<D>(LU, piv, rinv, r, u2);
+#pragma unroll
+  for (int c = 0; c < D; ++c) ynew[c] = fma_(h, add_(u2[c], k1[c]), y[c]);
+}
+
+// Trial step of the record: y_new, the error estimate e and F2 = f(y_new).
+template <class Pb>
+__device__ __forceinline__ bool ros23_trial(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
+                                            const double (&F0)[Pb::D], double (&ynew)[Pb::D], double (&e)[Pb::D],
+                                            double (&F2)[Pb::D]) {
+  constexpr int D = Pb::D;
+  double LU[D][D], rinv[D], k1[D], u2[D], Y1[D], F1[D], r[D], k3[D];
+  int piv[D];
+  const bool ok = ros23_factor<Pb>(y, p, h, LU, piv, rinv);
+  ros23_stages<Pb>(y, p, h, F0, LU, piv, rinv, k1, u2, Y1, F1, ynew);
+  Pb::f(ynew, p, F2);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const double k2 = add_(u2[c], k1[c]);
+    r[c] = fma_(-ros23::E32, sub_(k2, F1[c]), fma_(-2.0, sub_(k1[c], F0[c]), F2[c]));
+  }
+  lu_solve<D>(LU, piv, rinv, r, k3);
+  const double h6 = h / 6.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) e[c] = mul_(h6, add_(fma_(-2.0, add_(u2[c], k1[c]), k1[c]), k3[c]));
+  return ok;
+}
+
+// Reverse of one Rosenbrock23 step (h held as data): given lam = dL/dy_new,
+// returns v = dL/dy and accumulates dL/dtheta:
+//   k2bar = h lam, r2bar = W^{-T} k2bar, F1bar = r2bar, k1bar = k2bar - r2bar,
+//   Y1bar = J(Y1)^T r2bar (theta_bar += f_theta(Y1)^T r2bar), k1bar += h/2 Y1bar,
+//   r1bar = W^{-T} k1bar, v = lam + Y1bar + J(y)^T r1bar (theta_bar += f_theta(y)^T r1bar),
+// and dL/dJ = h d (r1bar k1^T + r2bar u2^T) contracted through J(y, theta).
+template <class Pb, class Acc>
+__device__ __forceinline__ void ros23_reverse(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
+                                              const double (&k1)[Pb::D], const double (&u2)[Pb::D],
+                                              const double (&Y1)[Pb::D], const double (&LU)[Pb::D][Pb::D],
+                                              const int (&piv)[Pb::D], const double (&rinv)[Pb::D],
+                                              const double (&lam)[Pb::D], double (&v)[Pb::D], Acc& pacc) {
+  constexpr int D = Pb::D;
+  double k2b[D], r2b[D], k1b[D], r1b[D], Y1b[D], y0b[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) k2b[c] = mul_(h, lam[c]);
+  lu_solve_t<D>(LU, piv, rinv, k2b, r2b);
+  pacc.template vjp<Pb>(Y1, p, r2b, Y1b);
+  const double hh = mul_(0.5, h);
+#pragma unroll
+  for (int c = 0; c < D; ++c) k1b[c] = fma_(hh, Y1b[c], sub_(k2b[c], r2b[c]));
+  lu_solve_t<D>(LU, piv, rinv, k1b, r1b);
+  pacc.template vjp<Pb>(y, p, r1b, y0b);
+#pragma unroll
+  for (int c = 0; c < D; ++c) v[c] = add_(add_(lam[c], Y1b[c]), y0b[c]);
+  const double hd = mul_(h, ros23::DC);
+  double r1s[D], r2s[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    r1s[c] = mul_(hd, r1b[c]);
+    r2s[c] = mul_(hd, r2b[c]);
+  }
+  pacc.template jac_contract<Pb>(y, p, r1s, k1, v);
+  pacc.template jac_contract<Pb>(y, p, r2s, u2, v);
+}
+
+// Forward mode of one Rosenbrock23 step (h held as data), ND directions:
+//   Jd = dJ(y)[yd, pd], dW = -h d Jd;
+//   kd1 = W^{-1} (Fd0 + h d Jd k1),  Fd0 = J(y) yd + f_theta(y) pd;
+//   Yd1 = yd + h/2 kd1,  Fd1 = J(Y1) Yd1 + f_theta(Y1) pd;
+//   ud2 = W^{-1} (Fd1 - kd1 + h d Jd u2);  yd_new = yd + h (ud2 + kd1).
+template <class Pb, int ND>
+__device__ __forceinline__ bool ros23_tangent(const double (&y)[Pb::D], const double (&yd)[ND][Pb::D],
+                                              const double (&p)[Pb::NP], const double (&pd)[ND][Pb::NP], double h,
+                                              double (&yn)[Pb::D], double (&ydn)[ND][Pb::D]) {
+  constexpr int D = Pb::D;
+  double LU[D][D], rinv[D], F0[D], k1[D], u2[D], Y1[D], F1[D];
+  int piv[D];
+  const bool ok = ros23_factor<Pb>(y, p, h, LU, piv, rinv);
+  Pb::f(y, p, F0);
+  ros23_stages<Pb>(y, p, h, F0, LU, piv, rinv, k1, u2, Y1, F1, yn);
+  const double hd = mul_(h, ros23::DC), hh = mul_(0.5, h);
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    double Fd[D], JdU[D], r[D], kd1[D], Yd1[D], ud2[D];
+    Pb::jvp(y, p, yd[q], pd[q], Fd);
+    Pb::jac_dir(y, p, yd[q], pd[q], k1, JdU);
+#pragma unroll
+    for (int c = 0; c < D; ++c) r[c] = fma_(hd, JdU[c], Fd[c]);
+    lu_solve<D>(LU, piv, rinv, r, kd1);
+#pragma unroll
+    for (int c = 0; c < D; ++c) Yd1[c] = fma_(hh, kd1[c], yd[q][c]);
+    Pb::jvp(Y1, p, Yd1, pd[q], Fd);
+    Pb::jac_dir(y, p, yd[q], pd[q], u2, JdU);
+#pragma unroll
+    for (int c = 0; c < D; ++c) r[c] = fma_(hd, JdU[c], sub_(Fd[c], kd1[c]));
+    lu_solve<D>(LU, piv, rinv, r, ud2);
+#pragma unroll
+    for (int c = 0; c < D; ++c) ydn[q][c] = fma_(h, add_(ud2[c], kd1[c]), yd[q][c]);
+  }
+  return ok;
+}
+
 }  // namespace gs

@@ -1,0 +1,43 @@
+// Rosenbrock23 (second-order stiff method) instantiations of the record,
+// reverse-sweep and refresh kernels: Robertson, HIRES and the linear test
+// problem, FP64.
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+bool ros23_supports(int problem, int precision) {
+  return (problem == 2 || problem == 3 || problem == 4) && precision == 0;
+}
+
+cudaError_t launch_ros23_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s) {
+  if (precision != 0) return cudaErrorInvalidValue;
+  switch (problem) {
+    case 2: return fwd_dispatch<Ros23Method, Robertson, double>(a, s);
+    case 3: return fwd_dispatch<Ros23Method, Hires, double>(a, s);
+    case 4: return fwd_dispatch<Ros23Method, Linear2, double>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ros23_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s) {
+  if (precision != 0) return cudaErrorInvalidValue;
+  switch (problem) {
+    case 2: return rev_dispatch<Ros23Method, Robertson, double>(a, s);
+    case 3: return rev_dispatch<Ros23Method, Hires, double>(a, s);
+    case 4: return rev_dispatch<Ros23Method, Linear2, double>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ros23_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
+                                 const double* y0, cudaStream_t s) {
+  if (precision != 0) return cudaErrorInvalidValue;
+  switch (problem) {
+    case 2: return refresh_dispatch<Ros23Method, Robertson, double>(a, arena, y_final, y0, s);
+    case 3: return refresh_dispatch<Ros23Method, Hires, double>(a, arena, y_final, y0, s);
+    case 4: return refresh_dispatch<Ros23Method, Linear2, double>(a, arena, y_final, y0, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gs
