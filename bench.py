@@ -46,10 +46,19 @@ RHS_FLOPS = {"lorenz": dict(f=8, vjp=20, D=3), "vdp": dict(f=5, vjp=15, D=2),
 STIFF = {"robertson", "hires"}
 
 
-def unit_flops(problem):
+def unit_flops(problem, method=None):
     c = RHS_FLOPS[problem]
     f, v, D = c["f"], c["vjp"], c["D"]
     norm = 6 * D + 4  # weighted RMS error test and step control
+    if method == "rosenbrock23":
+        # W = I - h d J (J, D^2 scale, D), LU (2/3 D^3); k1 and u2 solves (2 D^2 each),
+        # Y1 (2 D), f(Y1), F1 - k1 (D), y_new (3 D): the replay step with f(y).
+        # Trial adds f(y_new), the k3 right-hand side (6 D), its solve and e (5 D).
+        # Reverse: two transposed solves, two VJPs, 8 D of recursions, two contractions.
+        step = c["jac"] + D * D + D + (2 * D ** 3) // 3 + 4 * D * D + 6 * D + 2 * f
+        trial = step + 2 * D * D + 11 * D + norm  # f(y) carried from the last step, f(y_new) added
+        rev = 4 * D * D + 2 * v + 8 * D + 2 * c["con"]
+        return {"stage_fwd": step, "vjp_unit": step + rev, "trial": trial}
     if problem not in STIFF:
         # Tsit5: stage forward (6 slopes + 6 stage inputs) 6 f + 48 D;
         # stage reverse (6 stage VJPs + cotangent recursion) 6 vjp + 54 D
@@ -136,21 +145,27 @@ def dist_env():
     return ws, rank, local
 
 
+def oracle_method(args):
+    import oracle
+    return oracle.METHOD_ROSENBROCK23 if args.method == "rosenbrock23" else oracle.METHOD_AUTO
+
+
 def cpu_baseline(args, budget_s=12.0):
     """The FP64 oracle (record + replay gradient), as it stands, on the host cores,
     over a bounded sample of the same workload."""
     import oracle
     cores = os.cpu_count() or 1
+    om = oracle_method(args)
     probe = W.make(args.problem, 2048, rtol=args.rtol, seed=7)
     t = time.perf_counter()
     oracle.solve_grad(probe["problem"], probe["params"], probe["y0"], probe["t0"], probe["t1"], probe["save_t"],
-                      probe["rtol"], probe["atol"], nthreads=cores)
+                      probe["rtol"], probe["atol"], nthreads=cores, method=om)
     rate = 2048 / (time.perf_counter() - t)
     m = int(min(max(4096, rate * budget_s), 1 << 22))
     wl = W.make(args.problem, m, rtol=args.rtol, seed=0)
     t = time.perf_counter()
     g = oracle.solve_grad(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], wl["rtol"],
-                          wl["atol"], nthreads=cores)
+                          wl["atol"], nthreads=cores, method=om)
     dt = time.perf_counter() - t
     assert g["ok"].all()
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -170,10 +185,11 @@ def accuracy_sample(args, precision, m=512):
     P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
     Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
     rec, _, _ = api.forward_record(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
-                                   layout="soa", want_saves=False, precision=precision)
+                                   layout="soa", want_saves=False, precision=precision, method=args.method)
     g = api.reverse(rec, P, Y, layout="soa")
     off, h = rec.export_mesh()
-    o = oracle.replay_grad(args.problem, wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h)
+    o = oracle.replay_grad(args.problem, wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h,
+                           method=oracle_method(args))
     a = np.concatenate([g["params_bar"].cpu().numpy().T, g["y0_bar"].cpu().numpy().T], 1)
     b = np.concatenate([o["params_bar"], o["y0_bar"]], 1)
     e = np.abs(a - b).max(1) / np.abs(b).max(1)
@@ -230,7 +246,7 @@ def run_reference(args):
 
     def step():
         g = oracle.solve_grad(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"],
-                              wl["rtol"], wl["atol"], nthreads=cores)
+                              wl["rtol"], wl["atol"], nthreads=cores, method=oracle_method(args))
         assert g["ok"].all()
 
     for _ in range(args.warmup):
@@ -327,6 +343,12 @@ def forward_mode_measure(args, P, Y, wl, steps=3):
             "reverse_ms": t_rev * 1e3, "max_rel_diff_forward_vs_reverse": agree}
 
 
+def method_name(args):
+    if args.method == "rosenbrock23":
+        return "Rosenbrock23"
+    return "Rodas5P" if args.problem in STIFF else "Tsit5"
+
+
 def config_of(args, n):
     wl = {"lorenz": "Lorenz-63 (sigma~U[8,12], rho~U[20,30], beta~U[2,3], y0~N((1,1,1),0.1^2 I), t in [0,1], "
                     "10 uniform saves)",
@@ -334,7 +356,7 @@ def config_of(args, n):
           "robertson": "Robertson (k=(0.04,3e7,1e4) x logU[0.9,1.1], y0=(1,0,0), t in [1e-5,1e5], 20 log saves)",
           "hires": "HIRES (12 rates x logU[0.9,1.1], standard y0, t in [0,321.8122], 10 uniform saves)",
           }[args.problem]
-    method = "Rodas5P" if args.problem in STIFF else "Tsit5"
+    method = method_name(args)
     atol = 1e-10 if args.problem in STIFF else args.rtol * 1e-2
     return {"workload": f"{wl}, {method} rtol={args.rtol:g} atol={atol:g}, {args.precision}, "
                         f"n={n} per GPU, loss=sum_s ||y(t_s)||^2, grads wrt theta and y0",
@@ -352,6 +374,8 @@ def main():
     ap.add_argument("--traj", type=int, default=1 << 24, help="trajectories per GPU")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
+    ap.add_argument("--method", default=None, choices=["rodas5p", "rosenbrock23"],
+                    help="stiff method (default: Rodas5P for the stiff problems, Tsit5 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1 << 15)
     ap.add_argument("--no-serve", action="store_true")
@@ -389,7 +413,7 @@ def main():
     def step(kernel_ms=None, counts=False):
         return api.solve_grad(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
                               layout="soa", out=out, precision=args.precision, kernel_ms=kernel_ms,
-                              step_counts=counts)
+                              step_counts=counts, method=args.method)
 
     for _ in range(args.warmup):
         step()
@@ -447,7 +471,7 @@ def main():
     e2e = {"value": ws * n * ke / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel (the reverse sweep), algorithmic flops / event-timed duration
-    uf = unit_flops(args.problem)
+    uf = unit_flops(args.problem, args.method)
     n_side = n * (len(wl["save_t"]) - 1)  # saves strictly inside a step (the last one sits on t1)
     rev_flops = (S_tot + n_side) * uf["vjp_unit"]
     fwd_flops = A_tot * uf["trial"]
@@ -462,7 +486,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": config_of(args, n),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "kernel": f"{dominant}_kernel<{'Rodas5P' if args.problem in STIFF else 'Tsit5'}>",
+                         "traffic": None, "kernel": f"{dominant}_kernel<{method_name(args)}>",
                          "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz"},
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,

@@ -72,6 +72,9 @@ def _call(lib, **kw):
     (dict(opt=dict(timeout_ms=-1.0)), N.GS_ERR_INVALID_ARG),
     (dict(pid=5, w=1, opt=dict(precision=0)), N.GS_ERR_INVALID_ARG),  # the UDE runs FP32-mixed only
     (dict(pid=0, opt=dict(method=2)), N.GS_ERR_INVALID_ARG),  # no Rodas5P kernel for Lorenz
+    (dict(pid=1, opt=dict(method=3)), N.GS_ERR_INVALID_ARG),  # no Rosenbrock23 kernel for Van der Pol
+    (dict(pid=2, opt=dict(method=3, precision=1)), N.GS_ERR_INVALID_ARG),  # Rosenbrock23 runs in FP64
+    (dict(opt=dict(method=4)), N.GS_ERR_INVALID_ARG),
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, kw, code):
     assert _call(lib, **kw) == code
