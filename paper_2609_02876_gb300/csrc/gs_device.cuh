@@ -72,6 +72,16 @@ __device__ __forceinline__ double max_abs(double a, double b) {  // max(|a|, |b|
   const unsigned long long ua = abs_bits(a), ub = abs_bits(b);
   return __longlong_as_double((long long)(ua > ub ? ua : ub));
 }
+// Order key of any non-NaN double as a signed 64-bit integer: negative values
+// get their magnitude bits flipped, so key(a) < key(b) iff a < b (with -0 just
+// below +0). Equality of two doubles that are not zero or NaN is equality of
+// their bits. The solver's time comparisons (end of span, save times) run on
+// the integer ALU this way.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool same_time(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
 constexpr unsigned long long DBITS_ONE = 0x3ff0000000000000ull;  // 1.0
 constexpr unsigned long long DBITS_INF = 0x7ff0000000000000ull;  // +inf
 __device__ __forceinline__ bool le_one(double q) { return dbits(q) <= DBITS_ONE; }      // q >= 0: q <= 1, NaN false
@@ -620,7 +630,8 @@ __device__ __forceinline__ double err_meansq(const double (&e)[D], const double 
 }
 // FP32-mixed form: the error, y and y_new are FP32 stage values, so each ratio
 // e_c / sc_c is formed in FP32 (scale with an IEEE reciprocal); the squares are
-// summed and the mean compared in FP64.
+// summed in FP64 and the mean taken in FP32 (relative error 2^-23, below the
+// 1e-6 the ratios already carry), which keeps the FP64 pipe for the sum alone.
 template <int D>
 __device__ __forceinline__ double err_meansq(const float (&e)[D], const float (&y)[D], const float (&yn)[D],
                                              double rtol, double atol) {
@@ -632,7 +643,7 @@ __device__ __forceinline__ double err_meansq(const float (&e)[D], const float (&
     const double r = to_d(__fmul_rn(e[c], __frcp_rn(sc)));
     q = fma_(r, r, q);
   }
-  return mul_(q, 1.0 / D);
+  return to_d(__fmul_rn(to_f(q), 1.0f / D));
 }
 
 // Integral-controller factor from the mean-square error q = err^2, for an

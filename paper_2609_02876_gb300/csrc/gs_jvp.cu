@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(TPB_REV) jvp_kernel(const JvpArgs a) {
           tn = (i + 1 == S) ? a.t1 : add_(t, hi);
         }
         // saves attached to mesh point i: t_i <= t_s < t_{i+1} (every remaining one at i = S)
-        if (js < ns && (i == S || s_save[js] < tn)) {
-          if (s_save[js] == t) {
+        if (js < ns && (i == S || dkey(s_save[js]) < dkey(tn))) {
+          if (same_time(s_save[js], t)) {
             jvp_save<D, ND>(a, k, js, y, yd, loss, ldot);
             ++js;
             continue;

@@ -303,14 +303,20 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
   const long long n = a.n;
   const double t1 = a.t1;
   const double sliver = 1e-12 * fmax(1.0, fabs(t1));
+  const long long key_end = dkey(t1 - sliver);  // a step reaching past t1 - sliver is the last
   long long k = -1;
   bool drained = false;
   double t = 0.0, h = 0.0;
   R y[D], p[NP];
   Carry cy;
   int S = 0, natt = 0, slot = 0, js = 0, status = TRAJ_OK;
-  bool rej = false, lastnf = false, lastsing = false, pending_fail = false;
+  bool rej = false, lastnf = false, lastsing = false, ended = false;
   long long prev = -1;
+  // pending save-time side steps [jp, je), all from the mesh point (tp, yp)
+  R yp[D];
+  Carry cyp;
+  double tp = 0.0;
+  int jp = 0, je = 0;
 
   for (;;) {
     // ---- refill: lanes without a trajectory take the next ticket
@@ -337,14 +343,14 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
             fin = fin && isfinite(v);
           }
           t = a.t0;
-          S = natt = slot = js = 0;
+          S = natt = slot = js = jp = je = 0;
           status = TRAJ_OK;
           rej = lastnf = lastsing = false;
           prev = -1;
           M::template start<Pb, R>(y, p, cy, ff);
           h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
           fin = fin && isfinite(h) && h > 0.0;
-          pending_fail = !fin;
+          ended = !fin;
           if (!fin) status = TRAJ_NONFINITE;
           if (a.k > 0) {
             stg[1 * TB] = t;
@@ -358,50 +364,79 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
     }
     if (!__any_sync(FULL_MASK, k >= 0)) break;
 
-    bool done = false;
-    if (k >= 0 && pending_fail) done = true;
-    if (k >= 0 && !pending_fail && natt >= a.max_steps) {
-      status = TRAJ_MAXSTEPS;
-      done = true;
-    }
-    const bool trial = (k >= 0) && !done;
+    // ---- this lane's unit: a pending save-time side step (it starts from the
+    // mesh point before the last accepted step), else a trial step
+    int um = U_NONE;
     bool last = false;
-    if (trial && t + h >= t1 - sliver) {
-      h = t1 - t;
-      last = true;
+    double tsum = 0.0;  // t + h of a trial step
+    if (k >= 0) {
+      if (SAVES) {
+        while (jp < je && same_time(s_save[jp], tp)) {  // a save on that mesh point: its state, no step
+#pragma unroll
+          for (int c = 0; c < D; ++c) a.y_save[((long long)jp * D + c) * n + k] = (double)yp[c];
+          ++jp;
+        }
+        if (jp < je) um = U_SIDE;
+      }
+      if (um == U_NONE && !ended) {
+        if (natt >= a.max_steps) {
+          status = TRAJ_MAXSTEPS;
+          ended = true;
+        } else {
+          um = U_STEP;
+          tsum = add_(t, h);
+          if (dkey(tsum) >= key_end) {
+            h = t1 - t;
+            last = true;
+          }
+        }
+      }
     }
 
-    // ---- one trial step (all lanes with a live trajectory, one code path)
+    // ---- one step for every lane with a unit: trial steps and side steps run
+    // the same code (a side step ignores the error estimate). The mode is made
+    // opaque to the optimiser so that the two share one copy of the code and
+    // the warp runs it once with all its busy lanes.
     __syncwarp();
+    asm volatile("" : "+r"(um));
     R yn[D], e[D];
     Carry next;
     double q = 2.0;
     bool solved = true;
-    if (trial) {
-      ++natt;
-      solved = M::template trial<Pb, R>(y, p, h, cy, yn, e, next);
-      q = err_meansq<D>(e, y, yn, a.rtol, a.atol);
+    if (um != U_NONE) {
+      const bool sd = SAVES && (um == U_SIDE);
+      R xin[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) xin[c] = sd ? yp[c] : y[c];
+      const Carry cin = sd ? cyp : cy;
+      const double hx = sd ? s_save[jp] - tp : h;
+      solved = M::template trial<Pb, R>(xin, p, hx, cin, yn, e, next);
+      if (!sd) {
+        ++natt;
+        q = err_meansq<D>(e, y, yn, a.rtol, a.atol);
+      }
     }
+    if (SAVES && um == U_SIDE) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) a.y_save[((long long)jp * D + c) * n + k] = solved ? (double)yn[c] : nan_d();
+      ++jp;
+    }
+    const bool trial = (um == U_STEP);
     const bool accept = trial && solved && le_one(q);  // q >= 0; NaN rejects
     if (accept) {
-      const double tn = last ? t1 : add_(t, h);
+      const double tn = last ? t1 : tsum;
       if (SAVES) {
-        // save times in [t, tn): one extra step from y; exactly tn: y_new
-        while (js < ns && s_save[js] < tn) {
-          const double hs = s_save[js] - t;
-          R ys[D];
-          bool ok = true;
-          if (hs == 0.0) {
+        // save times in [t, tn): side steps from (t, y), taken as units of the
+        // following iterations; exactly tn: y_new
+        jp = js;
+        tp = t;
 #pragma unroll
-            for (int c = 0; c < D; ++c) ys[c] = y[c];
-          } else {
-            ok = M::template side<Pb, R>(y, p, hs, cy, ys);
-          }
-#pragma unroll
-          for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = ok ? (double)ys[c] : nan_d();
-          ++js;
-        }
-        while (js < ns && s_save[js] == tn) {
+        for (int c = 0; c < D; ++c) yp[c] = y[c];
+        cyp = cy;
+        const long long key_tn = dkey(tn);
+        while (js < ns && dkey(s_save[js]) < key_tn) ++js;
+        je = js;
+        while (js < ns && same_time(s_save[js], tn)) {
 #pragma unroll
           for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = (double)yn[c];
           ++js;
@@ -414,9 +449,9 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       for (int c = 0; c < D; ++c) y[c] = yn[c];
       cy = next;
       ++S;
-      if (last) done = true;
+      if (last) ended = true;
     }
-    if (trial && !done) {
+    if (trial && !ended) {
       // integral controller: accepted steps grow at most x10 (x1 right after a
       // rejection), rejected ones shrink by the same rule, x0.2 on a non-finite
       // error, x0.25 when the step's linear system is singular
@@ -430,9 +465,11 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       // |h| < 1e-14 max(1, |t|), evaluated in FP32 (a threshold test, not arithmetic of the solution)
       if (fabsf(to_f(h)) < 1e-14f * fmaxf(1.0f, fabsf(to_f(t)))) {
         status = lastsing ? TRAJ_SINGULAR : (lastnf ? TRAJ_NONFINITE : TRAJ_DT_UNDERFLOW);
-        done = true;
+        ended = true;
       }
     }
+    // the trajectory is done once it has ended and its pending side steps are taken
+    const bool done = (k >= 0) && ended && !(SAVES && jp < je);
     // (a.k == 0: forward-only solve, nothing is recorded)
     const bool flush = (a.k > 0) && (k >= 0) && ((slot == a.k) || (done && slot > 0));
 
@@ -504,8 +541,9 @@ __device__ __forceinline__ void write_grad(const RevArgs& a, long long k, const 
 template <int D, class R, bool USER_COT>
 __device__ __forceinline__ bool next_save(const RevArgs& a, const double* s_save, long long k, int& js, double tx,
                                           const R (&yx)[D], R (&lam)[D], double& loss, int& us) {
-  while (js >= 0 && s_save[js] >= tx) {
-    if (s_save[js] == tx) {
+  const long long key_tx = dkey(tx);
+  while (js >= 0 && dkey(s_save[js]) >= key_tx) {
+    if (same_time(s_save[js], tx)) {
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         if (USER_COT) {
