@@ -41,8 +41,12 @@ struct LvUde {
     float* w = weights();
     for (int i = threadIdx.x; i < UDE_NW; i += blockDim.x) w[i] = shared_w[i];
   }
+  // The weights are read from shared memory at every use: the compiler barrier
+  // keeps it from hoisting the 354 loads out of the solver loops into
+  // registers, which do not hold them (they would spill to local memory).
   __device__ __forceinline__ static void forward(float x, float y, float (&h1)[UDE_H], float (&h2)[UDE_H],
                                                  float (&nn)[2]) {
+    asm volatile("" ::: "memory");
     const float* w = weights();
 #pragma unroll
     for (int i = 0; i < UDE_H; ++i)
@@ -76,6 +80,7 @@ struct LvUde {
   };
   __device__ __forceinline__ static void backprop(const float (&y)[D], const float (&p)[NP], const float (&v)[D],
                                                   float (&yb)[D], float (&pb)[NP], Factors& fa) {
+    asm volatile("" ::: "memory");
     const float* w = weights();
     float nn[2], gh2[UDE_H];
     forward(y[0], y[1], fa.h1, fa.h2, nn);
