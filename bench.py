@@ -42,7 +42,11 @@ UNIT = "trajectories/s"
 # jac = the dense Jacobian, con = one gradient of r^T J u (stiff problems), D.
 RHS_FLOPS = {"lorenz": dict(f=8, vjp=20, D=3), "vdp": dict(f=5, vjp=15, D=2),
              "robertson": dict(f=8, vjp=19, jac=5, con=23, D=3),
-             "hires": dict(f=36, vjp=80, jac=4, con=49, D=8)}
+             "hires": dict(f=36, vjp=80, jac=4, con=49, D=8),
+             # LV UDE: MLP 2-16-16-2 forward (W1 64, W2 512, W3 64 flops, 32 tanh at ~5) plus the
+             # linear terms; the VJP recomputes the forward and back-propagates (~750 more); the
+             # shared-weight gradient contraction runs on the tensor cores and is not counted here
+             "lv_ude": dict(f=804, vjp=1554, D=2)}
 STIFF = {"robertson", "hires"}
 
 
@@ -159,13 +163,13 @@ def cpu_baseline(args, budget_s=12.0):
     probe = W.make(args.problem, 2048, rtol=args.rtol, seed=7)
     t = time.perf_counter()
     oracle.solve_grad(probe["problem"], probe["params"], probe["y0"], probe["t0"], probe["t1"], probe["save_t"],
-                      probe["rtol"], probe["atol"], nthreads=cores, method=om)
+                      probe["rtol"], probe["atol"], nthreads=cores, method=om, w=probe["w"])
     rate = 2048 / (time.perf_counter() - t)
     m = int(min(max(4096, rate * budget_s), 1 << 22))
     wl = W.make(args.problem, m, rtol=args.rtol, seed=0)
     t = time.perf_counter()
     g = oracle.solve_grad(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], wl["rtol"],
-                          wl["atol"], nthreads=cores, method=om)
+                          wl["atol"], nthreads=cores, method=om, w=wl["w"])
     dt = time.perf_counter() - t
     assert g["ok"].all()
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -184,12 +188,15 @@ def accuracy_sample(args, precision, m=512):
     wl = W.make(args.problem, m, rtol=args.rtol, seed=0)
     P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
     Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
+    SW = None if wl["w"] is None else torch.as_tensor(np.asarray(wl["w"], dtype=np.float32), device="cuda")
     rec, _, _ = api.forward_record(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
-                                   layout="soa", want_saves=False, precision=precision, method=args.method)
-    g = api.reverse(rec, P, Y, layout="soa")
+                                   layout="soa", want_saves=False, precision=precision, method=args.method,
+                                   shared_w=SW)
+    g = api.reverse(rec, P, Y, layout="soa", shared_w=SW)
     off, h = rec.export_mesh()
     o = oracle.replay_grad(args.problem, wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h,
-                           method=oracle_method(args))
+                           method=oracle_method(args), w=None if wl["w"] is None else np.asarray(SW.cpu().numpy(),
+                                                                                                dtype=np.float64))
     a = np.concatenate([g["params_bar"].cpu().numpy().T, g["y0_bar"].cpu().numpy().T], 1)
     b = np.concatenate([o["params_bar"], o["y0_bar"]], 1)
     e = np.abs(a - b).max(1) / np.abs(b).max(1)
@@ -246,7 +253,7 @@ def run_reference(args):
 
     def step():
         g = oracle.solve_grad(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"],
-                              wl["rtol"], wl["atol"], nthreads=cores, method=oracle_method(args))
+                              wl["rtol"], wl["atol"], nthreads=cores, method=oracle_method(args), w=wl["w"])
         assert g["ok"].all()
 
     for _ in range(args.warmup):
@@ -370,7 +377,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gradsolve", choices=["gradsolve", "reference"])
-    ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp", "robertson", "hires"])
+    ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp", "robertson", "hires", "lv_ude"])
     ap.add_argument("--traj", type=int, default=1 << 24, help="trajectories per GPU")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
@@ -400,9 +407,12 @@ def main():
     torch.cuda.set_device(local)
     build.build()
     n = args.traj
+    if args.problem == "lv_ude":
+        args.precision = "fp32_mixed"  # FP32 network and state, FP64 step control
     wl = W.make(args.problem, n, rtol=args.rtol, seed=rank)
     P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
     Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
+    SW = None if wl["w"] is None else torch.as_tensor(np.asarray(wl["w"], dtype=np.float32), device="cuda")
     d, Pn, _, _ = api.problem_info(args.problem)
     out = {"loss": torch.empty(n, dtype=torch.float64, device="cuda"),
            "params_bar": torch.empty((Pn, n), dtype=torch.float64, device="cuda"),
@@ -413,7 +423,7 @@ def main():
     def step(kernel_ms=None, counts=False):
         return api.solve_grad(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
                               layout="soa", out=out, precision=args.precision, kernel_ms=kernel_ms,
-                              step_counts=counts, method=args.method)
+                              step_counts=counts, method=args.method, shared_w=SW)
 
     for _ in range(args.warmup):
         step()
@@ -491,7 +501,7 @@ def main():
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
                      "reverse_tflops": rev_flops / rev_s / 1e12},
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks}
+            "e2e": e2e, "gpu_launches": (3 if args.problem == "lv_ude" else 2) * args.steps, "clocks": clocks}
     if rank == 0:
         line["accuracy"] = accuracy_sample(args, args.precision)
     if rank == 0 and ws == 1 and args.precision == "fp64" and args.problem in ("lorenz", "vdp") \
