@@ -362,6 +362,8 @@ def config_of(args, n):
           "vdp": "Van der Pol (mu~U[0.5,2], y0~U[-2,2]^2, t in [0,10], 50 uniform saves)",
           "robertson": "Robertson (k=(0.04,3e7,1e4) x logU[0.9,1.1], y0=(1,0,0), t in [1e-5,1e5], 20 log saves)",
           "hires": "HIRES (12 rates x logU[0.9,1.1], standard y0, t in [0,321.8122], 10 uniform saves)",
+          "lv_ude": "LV UDE (a~U[1,1.5], d~U[2,3], y0~U[0.5,2]^2, t in [0,5], 10 uniform saves, shared MLP "
+                    "2-16-16-2 tanh, Glorot seed 0; grads also wrt the 354 shared weights)",
           }[args.problem]
     method = method_name(args)
     atol = 1e-10 if args.problem in STIFF else args.rtol * 1e-2
