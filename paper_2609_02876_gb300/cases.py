@@ -32,11 +32,13 @@ def main(argv=None) -> int:
     wl = W.make(args.problem, args.traj)
     P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
     Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
+    SW = None if wl["w"] is None else torch.as_tensor(np.asarray(wl["w"], dtype=np.float32), device="cuda")
     common = (wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"])
     if args.case == "solve_grad":
-        run = lambda: api.solve_grad(args.problem, P, Y, *common, layout="soa", precision=args.precision)
+        run = lambda: api.solve_grad(args.problem, P, Y, *common, layout="soa", precision=args.precision,
+                                     shared_w=SW)
     elif args.case == "forward_only":
-        run = lambda: api.solve(args.problem, P, Y, *common, layout="soa", precision=args.precision)
+        run = lambda: api.solve(args.problem, P, Y, *common, layout="soa", precision=args.precision, shared_w=SW)
     else:
         rec, _, _ = api.forward_record(args.problem, P, Y, *common, layout="soa", want_saves=False)
         run = lambda: api.forward_grad(rec, P, Y, wrt=("params",), layout="soa")
