@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.cpp")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 
-PROBLEMS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5}
+PROBLEMS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5, "nrob": 6}
 METHOD_AUTO, METHOD_TSIT5, METHOD_RODAS5P, METHOD_ROSENBROCK23 = 0, 1, 2, 3
 TRAJ_OK, TRAJ_MAXSTEPS, TRAJ_DT_UNDERFLOW, TRAJ_NONFINITE, TRAJ_SINGULAR = 0, 1, 2, 3, 4
 
@@ -61,6 +61,7 @@ def lib():
         L.or_rhs.argtypes = [i32, i64, dp, dp, dp, dp, dp]
         L.or_initial_step.argtypes = [i32, dp, dp, dp, d, d, d, d, i32]
         L.or_initial_step.restype = C.c_double
+        L.or_w_contract.argtypes = [i32, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -98,9 +99,9 @@ def tableau(method: int):
 
 
 def _w(problem, w):
-    if _pid(problem) == PROBLEMS["lv_ude"]:
+    if _pid(problem) in (PROBLEMS["lv_ude"], PROBLEMS["nrob"]):
         if w is None:
-            raise ValueError("lv_ude needs shared weights")
+            raise ValueError("shared-weight problems need their weights")
         return _arr(w)
     return None
 
@@ -212,3 +213,14 @@ def solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, method=METHOD_AU
                     nthreads=nthreads)
     g["record"] = rec
     return g
+
+
+def w_contract(problem, y, w, r, u):
+    """Shared-weight gradient of r^T J(y, w) u at one point (stiff-adjoint contraction term)."""
+    pid = _pid(problem)
+    _, _, _, nw = problem_info(pid)
+    out = np.zeros(nw)
+    rc = lib().or_w_contract(pid, _p(_arr(y)), _p(_arr(w)), _p(_arr(r)), _p(_arr(u)), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"or_w_contract failed: {rc}")
+    return out

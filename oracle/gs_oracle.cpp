@@ -66,13 +66,17 @@ template <class T> double val(const Dual<T>& x) { return val(x.v); }
 
 // ---------------------------------------------------------------- problems
 // Problem ids (match the C-ABI's numbering; the numbers are the interface).
-enum { P_LORENZ = 0, P_VDP = 1, P_ROBERTSON = 2, P_HIRES = 3, P_LINEAR = 4, P_LV_UDE = 5 };
+enum { P_LORENZ = 0, P_VDP = 1, P_ROBERTSON = 2, P_HIRES = 3, P_LINEAR = 4, P_LV_UDE = 5, P_NROB = 6 };
 constexpr int DMAX = 8;
 constexpr int PMAX = 12;
 // LV UDE network: 2 -> 16 -> 16 -> 2, tanh hidden, linear output.
 // Flat weight layout: W1[16][2], b1[16], W2[16][16], b2[16], W3[2][16], b3[2] = 354.
 constexpr int UDE_H = 16;
 constexpr int UDE_NW = UDE_H * 2 + UDE_H + UDE_H * UDE_H + UDE_H + 2 * UDE_H + 2;
+// Robertson neural right-hand side (paper Appendix A): MLP 3 -> 16 -> 16 -> 1,
+// tanh hidden, softplus output. Flat layout: W1[16][3], b1[16], W2[16][16],
+// b2[16], W3[16], b3 = 353.
+constexpr int NR_NW = UDE_H * 3 + UDE_H + UDE_H * UDE_H + UDE_H + UDE_H + 1;
 
 int dim_of(int pid) {
   switch (pid) {
@@ -82,6 +86,7 @@ int dim_of(int pid) {
     case P_HIRES: return 8;
     case P_LINEAR: return 2;
     case P_LV_UDE: return 2;
+    case P_NROB: return 3;
   }
   return -1;
 }
@@ -93,10 +98,44 @@ int npar_of(int pid) {
     case P_HIRES: return 12;
     case P_LINEAR: return 4;
     case P_LV_UDE: return 2;
+    case P_NROB: return 2;  // k1, k3
   }
   return -1;
 }
-int stiff_of(int pid) { return (pid == P_ROBERTSON || pid == P_HIRES) ? 1 : 0; }
+int stiff_of(int pid) { return (pid == P_ROBERTSON || pid == P_HIRES || pid == P_NROB) ? 1 : 0; }
+int nshared_of(int pid) { return pid == P_LV_UDE ? UDE_NW : (pid == P_NROB ? NR_NW : 0); }
+
+// softplus(x) = log(1 + e^x) and its derivative, the logistic function, for
+// plain and dual numbers.
+inline double sigmoid_(double x) { return 1.0 / (1.0 + std::exp(-x)); }
+inline double softplus_(double x) { return x > 0.0 ? x + std::log1p(std::exp(-x)) : std::log1p(std::exp(x)); }
+template <class T> Dual<T> sigmoid_(const Dual<T>& a) {
+  const T s = sigmoid_(a.v);
+  return {s, a.d * (s * (1.0 - s))};
+}
+template <class T> Dual<T> softplus_(const Dual<T>& a) { return {softplus_(a.v), a.d * sigmoid_(a.v)}; }
+
+// The neural term NN(y) of the Robertson neural right-hand side.
+template <class T, class TW>
+T nr_mlp(const T* y, const TW* w) {
+  const TW* W1 = w;
+  const TW* b1 = W1 + UDE_H * 3;
+  const TW* W2 = b1 + UDE_H;
+  const TW* b2 = W2 + UDE_H * UDE_H;
+  const TW* W3 = b2 + UDE_H;
+  const TW* b3 = W3 + UDE_H;
+  T h1[UDE_H], h2[UDE_H];
+  for (int i = 0; i < UDE_H; ++i)
+    h1[i] = tanh_(T(b1[i]) + T(W1[i * 3]) * y[0] + T(W1[i * 3 + 1]) * y[1] + T(W1[i * 3 + 2]) * y[2]);
+  for (int i = 0; i < UDE_H; ++i) {
+    T s = T(b2[i]);
+    for (int j = 0; j < UDE_H; ++j) s = s + T(W2[i * UDE_H + j]) * h1[j];
+    h2[i] = tanh_(s);
+  }
+  T z = T(b3[0]);
+  for (int j = 0; j < UDE_H; ++j) z = z + T(W3[j]) * h2[j];
+  return softplus_(z);
+}
 
 // Shared MLP of the LV UDE (2-16-16-2, tanh, linear output).
 template <class T, class TW>
@@ -162,6 +201,13 @@ void rhs(int pid, const T* y, const T* p, const TW* w, T* f) {
       ude_mlp(y, w, nn);
       f[0] = p[0] * y[0] - nn[0];
       f[1] = -p[1] * y[1] + nn[1];
+      break;
+    }
+    case P_NROB: {  // Robertson with k2 y2^2 replaced by NN(y) in its sink and source; p = (k1, k3)
+      const T nn = nr_mlp(y, w);
+      f[0] = -p[0] * y[0] + p[1] * y[1] * y[2];
+      f[1] = p[0] * y[0] - p[1] * y[1] * y[2] - nn;
+      f[2] = nn;
       break;
     }
   }
@@ -259,6 +305,71 @@ void ude_w_vjp(const double* y, const double* w, const double* v, double* wbar) 
     gW1[i * 2 + 0] += gs * y[0];
     gW1[i * 2 + 1] += gs * y[1];
   }
+}
+
+// Shared-weight VJP of the neural Robertson term: wbar[k] += c dNN/dw_k at y,
+// reverse mode written out by hand. Templated so that, run on dual numbers
+// y = y0 + eps u, the eps-parts of wbar are c d/dw (grad_y NN . u): the
+// weight derivative of the Jacobian contraction the stiff adjoint needs.
+template <class T>
+void nr_w_vjp(const T* y, const double* w, T c, T* wbar) {
+  const double* W1 = w;
+  const double* b1 = W1 + UDE_H * 3;
+  const double* W2 = b1 + UDE_H;
+  const double* b2 = W2 + UDE_H * UDE_H;
+  const double* W3 = b2 + UDE_H;
+  const double* b3 = W3 + UDE_H;
+  T* gW1 = wbar;
+  T* gb1 = gW1 + UDE_H * 3;
+  T* gW2 = gb1 + UDE_H;
+  T* gb2 = gW2 + UDE_H * UDE_H;
+  T* gW3 = gb2 + UDE_H;
+  T* gb3 = gW3 + UDE_H;
+  T h1[UDE_H], h2[UDE_H];
+  for (int i = 0; i < UDE_H; ++i)
+    h1[i] = tanh_(T(b1[i]) + W1[i * 3] * y[0] + W1[i * 3 + 1] * y[1] + W1[i * 3 + 2] * y[2]);
+  for (int i = 0; i < UDE_H; ++i) {
+    T s = T(b2[i]);
+    for (int j = 0; j < UDE_H; ++j) s = s + W2[i * UDE_H + j] * h1[j];
+    h2[i] = tanh_(s);
+  }
+  T z = T(b3[0]);
+  for (int j = 0; j < UDE_H; ++j) z = z + W3[j] * h2[j];
+  const T gz = c * sigmoid_(z);
+  gb3[0] += gz;
+  T gh1[UDE_H];
+  for (int j = 0; j < UDE_H; ++j) gh1[j] = T(0.0);
+  for (int i = 0; i < UDE_H; ++i) {
+    gW3[i] += gz * h2[i];
+    const T gs = (gz * W3[i]) * (1.0 - h2[i] * h2[i]);
+    gb2[i] += gs;
+    for (int j = 0; j < UDE_H; ++j) {
+      gW2[i * UDE_H + j] += gs * h1[j];
+      gh1[j] += gs * W2[i * UDE_H + j];
+    }
+  }
+  for (int i = 0; i < UDE_H; ++i) {
+    const T gs = gh1[i] * (1.0 - h1[i] * h1[i]);
+    gb1[i] += gs;
+    for (int a = 0; a < 3; ++a) gW1[i * 3 + a] += gs * y[a];
+  }
+}
+
+// Shared-weight VJP of f for the problems with shared weights.
+void w_vjp(const Prob& pr, const double* y, const double* v, double* wbar) {
+  if (pr.pid == P_LV_UDE) ude_w_vjp(y, pr.w, v, wbar);
+  if (pr.pid == P_NROB) nr_w_vjp<double>(y, pr.w, v[2] - v[1], wbar);
+}
+// Shared-weight gradient of g = r^T J(y, w) u (stiff adjoint): only the neural
+// term depends on w, through (r_3 - r_2) grad_y NN . u (1-based rows).
+void w_contract(const Prob& pr, const double* y, const double* r, const double* u, double* wbar) {
+  if (pr.pid != P_NROB) return;
+  using D = Dual<double>;
+  D yd[3], gd[NR_NW];
+  for (int a = 0; a < 3; ++a) yd[a] = D(y[a], u[a]);
+  for (int k = 0; k < NR_NW; ++k) gd[k] = D(0.0, 0.0);
+  nr_w_vjp<D>(yd, pr.w, D(r[2] - r[1], 0.0), gd);
+  for (int k = 0; k < NR_NW; ++k) wbar[k] += gd[k].d;
 }
 
 // ---------------------------------------------------------------- tableaus
@@ -387,7 +498,7 @@ void tsit5_step_vjp(const Prob& pr, const double* y, const double* p, double h, 
       for (int c = 0; c < d; ++c) s += Fp[c][q] * kbar[c];
       pbar[q] += s;
     }
-    if (wbar) ude_w_vjp(Ys[j], pr.w, kbar, wbar);
+    if (wbar) w_vjp(pr, Ys[j], kbar, wbar);
   }
   for (int c = 0; c < d; ++c) {
     double s = lam[c];
@@ -524,7 +635,7 @@ bool rodas_step_vjp(const Prob& pr, const double* y, const double* p, double h, 
       for (int c = 0; c < d; ++c) s += Fp[c][q] * Rbar[i][c];
       pbar[q] += s;
     }
-    if (wbar) ude_w_vjp(Ys[i], pr.w, Rbar[i], wbar);
+    if (wbar) w_vjp(pr, Ys[i], Rbar[i], wbar);
     for (int c = 0; c < d; ++c) ybar[c] += Yb[c];
     for (int j = 0; j < i; ++j)
       for (int c = 0; c < d; ++c) Ubar[j][c] += tb.a[i][j] * Yb[c];
@@ -533,6 +644,7 @@ bool rodas_step_vjp(const Prob& pr, const double* y, const double* p, double h, 
   for (int i = 0; i < 8; ++i) {
     double gy[DMAX], gp[PMAX];
     jac_contract_grad(pr, y, p, Rbar[i], U[i], gy, gp);
+    if (wbar) w_contract(pr, y, Rbar[i], U[i], wbar);
     for (int c = 0; c < d; ++c) ybar[c] += gy[c];
     for (int q = 0; q < P; ++q) pbar[q] += gp[q];
   }
@@ -614,7 +726,7 @@ bool ros23_step_vjp(const Prob& pr, const double* y, const double* p, double h, 
       for (int c = 0; c < d; ++c) s += Fp[c][q] * v[c];
       pbar[q] += s;
     }
-    if (wbar) ude_w_vjp(x, pr.w, v, wbar);
+    if (wbar) w_vjp(pr, x, v, wbar);
   };
   double Y1b[DMAX], y0b[DMAX];
   vjp_at(Y1, r2b, Y1b);
@@ -629,9 +741,11 @@ bool ros23_step_vjp(const Prob& pr, const double* y, const double* p, double h, 
   }
   double gy[DMAX], gp[PMAX];
   jac_contract_grad(pr, y, p, r1s, k1, gy, gp);
+  if (wbar) w_contract(pr, y, r1s, k1, wbar);
   for (int c = 0; c < d; ++c) ybar[c] += gy[c];
   for (int q = 0; q < P; ++q) pbar[q] += gp[q];
   jac_contract_grad(pr, y, p, r2s, u2, gy, gp);
+  if (wbar) w_contract(pr, y, r2s, u2, wbar);
   for (int c = 0; c < d; ++c) ybar[c] += gy[c];
   for (int q = 0; q < P; ++q) pbar[q] += gp[q];
   return true;
@@ -935,7 +1049,7 @@ int or_problem_info(int pid, int* d, int* P, int* stiff, int* n_shared) {
   *d = dim_of(pid);
   *P = npar_of(pid);
   *stiff = stiff_of(pid);
-  *n_shared = pid == P_LV_UDE ? UDE_NW : 0;
+  *n_shared = nshared_of(pid);
   return 0;
 }
 
@@ -989,7 +1103,7 @@ int or_record(int pid, int method, int64_t n, const double* params, const double
 }
 
 // Replay + discrete adjoint on a given ragged mesh. ybar_save may be null
-// (built-in loss). wbar (UDE only) receives the ensemble sum, accumulated in
+// (built-in loss). wbar (shared-weight problems) receives the ensemble sum, accumulated in
 // trajectory order.
 int or_replay_grad(int pid, int method, int64_t n, const double* params, const double* y0, const double* w,
                    double t0, double t1, const double* save_t, int ns, const int64_t* offsets, const double* h,
@@ -998,7 +1112,7 @@ int or_replay_grad(int pid, int method, int64_t n, const double* params, const d
   if (dim_of(pid) < 0) return 1;
   Prob pr{pid, dim_of(pid), npar_of(pid), w};
   method = resolve_method(pid, method);
-  const int nw = (pid == P_LV_UDE && wbar) ? UDE_NW : 0;
+  const int nw = wbar ? nshared_of(pid) : 0;
   std::vector<double> wpart(nw ? (size_t)n * nw : 0, 0.0);
   parallel_for(n, nthreads, [&](int64_t k, int) {
     double* wb = nw ? &wpart[(size_t)k * nw] : nullptr;
@@ -1078,6 +1192,16 @@ int or_rhs(int pid, int64_t n, const double* params, const double* y, const doub
         for (int a = 0; a < d; ++a) J[k * d * d + c * d + a] = Jm[c][a];
     }
   }
+  return 0;
+}
+
+// The shared-weight gradient of g = r^T J(y, w) u at one point (the weight
+// part of the stiff adjoint's Jacobian contraction), for direct tests.
+int or_w_contract(int pid, const double* y, const double* w, const double* r, const double* u, double* wbar) {
+  if (dim_of(pid) < 0) return 1;
+  Prob pr{pid, dim_of(pid), npar_of(pid), w};
+  for (int k = 0; k < nshared_of(pid); ++k) wbar[k] = 0.0;
+  w_contract(pr, y, r, u, wbar);
   return 0;
 }
 

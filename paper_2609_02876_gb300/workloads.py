@@ -18,7 +18,7 @@ _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
-PROBLEM_IDS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5}
+PROBLEM_IDS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5, "nrob": 6}
 
 
 def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
@@ -74,6 +74,12 @@ UDE_HIDDEN = 16
 UDE_NW = UDE_HIDDEN * 2 + UDE_HIDDEN + UDE_HIDDEN * UDE_HIDDEN + UDE_HIDDEN + 2 * UDE_HIDDEN + 2
 
 
+# Output bias of the untrained Robertson neural term: softplus(-9) = 1.2e-4, so the
+# term starts at the size of the rate it replaces (k2 y2^2 with y2 ~ 1e-5 .. 3e-5
+# and k2 = 3e7 is 1e-3 .. 3e-2 early, falling later), not at softplus(0) = 0.69.
+NROB_B3 = -9.0
+
+
 def glorot_mlp(seed: int = 0) -> np.ndarray:
     """Glorot-uniform 2-16-16-2 weights, zero biases, flat layout
     W1[16][2], b1[16], W2[16][16], b2[16], W3[2][16], b3[2]."""
@@ -85,6 +91,24 @@ def glorot_mlp(seed: int = 0) -> np.ndarray:
         parts.append(np.zeros(fo))
     w = np.concatenate(parts)
     assert w.size == UDE_NW
+    return w
+
+
+NROB_NW = 16 * 3 + 16 + 16 * 16 + 16 + 16 + 1  # 353
+
+
+def glorot_nrob(seed: int = 0, b3: float = NROB_B3) -> np.ndarray:
+    """Glorot-uniform 3-16-16-1 weights of the Robertson neural term, zero hidden
+    biases, output bias b3; flat layout W1[16][3], b1[16], W2[16][16], b2[16], W3[16], b3."""
+    H = UDE_HIDDEN
+    parts = []
+    for li, (fi, fo) in enumerate([(3, H), (H, H), (H, 1)]):
+        a = np.sqrt(6.0 / (fi + fo))
+        parts.append(uniform(_stream(98, li, seed), fi * fo, -a, a))
+        parts.append(np.zeros(fo))
+    w = np.concatenate(parts)
+    w[-1] = b3
+    assert w.size == NROB_NW
     return w
 
 
@@ -104,6 +128,9 @@ def make(name: str, n: int, rtol: float | None = None, seed: int = 0) -> dict:
                  10 uniform saves; rtol 1e-6, atol 1e-10.
     lv_ude:      a~U[1,1.5], d~U[2,3]; y0~U[0.5,2]^2; t in [0, 5]; 10 uniform saves;
                  shared Glorot MLP (seed 0); rtol 1e-6, atol 1e-8.
+    nrob:        Robertson with the k2 y2^2 term replaced by a shared MLP 3-16-16-1 (tanh,
+                 softplus output; Glorot seed 0, output bias NROB_B3); k1~U[0.04,0.06], k3 = 1e4;
+                 y0 = (1,0,0); t in [1e-5, 1e5]; 20 log-spaced saves; rtol 1e-6, atol 1e-10.
     lorenz_paper: the paper's timing ensemble (rho evenly over [0, 21], sigma = 10,
                  beta = 8/3, y0 = (1, 0, 0), t in [0, 1], rtol 1e-6, atol 1e-9).
     """
@@ -143,6 +170,13 @@ def make(name: str, n: int, rtol: float | None = None, seed: int = 0) -> dict:
         y0 = uniform(_stream(ci, 2, seed), 2 * n, 0.5, 2.0).reshape(n, 2)
         return dict(problem="lv_ude", params=p, y0=y0, t0=0.0, t1=5.0, save_t=uniform_saves(0.0, 5.0, 10),
                     rtol=rtol, atol=1e-2 * rtol, w=glorot_mlp(0))
+    if name == "nrob":
+        ci = 6
+        rtol = 1e-6 if rtol is None else rtol
+        p = np.stack([uniform(_stream(ci, 0, seed), n, 0.04, 0.06), np.full(n, 1e4)], 1)
+        y0 = np.tile(np.array([1.0, 0.0, 0.0]), (n, 1))
+        return dict(problem="nrob", params=p, y0=y0, t0=1e-5, t1=1e5, save_t=log_saves(1e-5, 1e5, 20),
+                    rtol=rtol, atol=1e-10, w=glorot_nrob(0))
     if name == "lorenz_paper":
         rtol = 1e-6 if rtol is None else rtol
         rho = np.linspace(0.0, 21.0, n)
