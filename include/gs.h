@@ -22,7 +22,8 @@
  *    gradients of a failed trajectory are NaN.
  *  - Problem ids name the paper's test problems (Appendix A) plus two forms of
  *    this library: GS_LINEAR (dy/dt = A y, A = [[p0, p1], [p2, p3]], a closed-
- *    form test problem) and GS_LV_UDE (Lotka-Volterra with a shared MLP).
+ *    form test problem) and GS_LV_UDE (Lotka-Volterra with a shared MLP);
+ *    GS_NEURAL_ROBERTSON is the paper's Robertson neural right-hand side.
  */
 #ifndef GRADSOLVE_GS_H
 #define GRADSOLVE_GS_H
@@ -57,7 +58,19 @@ enum {
 };
 
 /* Problem registry (paper Appendix A; GS_LINEAR and GS_LV_UDE are this library's). */
-enum { GS_LORENZ = 0, GS_VDP = 1, GS_ROBERTSON = 2, GS_HIRES = 3, GS_LINEAR = 4, GS_LV_UDE = 5 };
+enum {
+  GS_LORENZ = 0,
+  GS_VDP = 1,
+  GS_ROBERTSON = 2,
+  GS_HIRES = 3,
+  GS_LINEAR = 4,
+  GS_LV_UDE = 5,
+  /* Robertson with k2 y2^2 replaced by a shared MLP 3-16-16-1 (tanh, softplus
+   * output) in its sink and source (paper Appendix A); theta = (k1, k3), 353
+   * shared weights (FP32 in shared_w, FP64 in the kernels), stiff, FP64 only,
+   * Rodas5P or Rosenbrock23; shared_w_bar is the ensemble sum in FP32. */
+  GS_NEURAL_ROBERTSON = 6
+};
 
 /* Arithmetic of the stage and adjoint work. GS_FP32_MIXED keeps FP64 for the
  * step-size control (t, h, the error norm and the controller). */
@@ -107,7 +120,8 @@ gs_status gs_problem_info(int problem_id, int* d, int* P, int* stiff, int* n_sha
  * save_t[n_save-1] <= t1 (n_save may be 0, at most 256). Each y(t_s) is one
  * extra step from the last mesh point at or before t_s (paper Sec. 3.4); save
  * times never alter the mesh. y_save_out [n_save][d][n] may be NULL.
- * shared_w: the GS_LV_UDE network weights (354 floats, device), else NULL.
+ * shared_w: the network weights of GS_LV_UDE (354 floats) or
+ * GS_NEURAL_ROBERTSON (353 floats), device, else NULL.
  * traj_status [n] is required. Synchronises `stream`. The record stays valid
  * until gs_record_free and may be replayed any number of times.
  */
@@ -128,7 +142,7 @@ gs_status gs_forward_record(int problem_id, int64_t n, const double* params, con
  * y_save_bar [n_save][d][n] is dL/dy(t_s); NULL selects the built-in loss
  * L = sum_k sum_s ||y_k(t_s)||^2, whose per-trajectory values are written to
  * loss_out [n] if it is not NULL. Outputs params_bar [P][n] and y0_bar [d][n]
- * (either may be NULL); shared_w_bar (354 floats, GS_LV_UDE only) receives the
+ * (either may be NULL); shared_w_bar (the shared-weight problems only) receives the
  * ensemble sum. Enqueued on `stream`, not synchronised.
  */
 gs_status gs_reverse(const gs_record* rec, const double* params, const double* y0, const float* shared_w,
@@ -138,7 +152,7 @@ gs_status gs_reverse(const gs_record* rec, const double* params, const double* y
 /*
  * Frozen-mesh reuse (paper Sec. 3.1): re-runs every trajectory's replay chain
  * y_i = Phi(y_{i-1}; h_i, theta) over its recorded mesh with new params [P][n],
- * y0 [d][n] (and shared_w for GS_LV_UDE), replacing the record's states. A
+ * y0 [d][n] (and shared_w for the shared-weight problems), replacing the record's states. A
  * following gs_reverse with the same params returns the derivative at theta on
  * the mesh R(theta_0) that was recorded, d Psi(theta; sg[R(theta_0)]) / d theta,
  * as a fitting loop that reuses one record needs. The mesh, the save times and

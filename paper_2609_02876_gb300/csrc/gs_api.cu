@@ -29,6 +29,7 @@ bool problem_info(int pid, ProblemInfo* out) {
     case GS_HIRES: *out = {8, 12, 1, 0}; return true;
     case GS_LINEAR: *out = {2, 4, 0, 0}; return true;
     case GS_LV_UDE: *out = {2, 2, 0, 354}; return true;
+    case GS_NEURAL_ROBERTSON: *out = {3, 2, 1, 353}; return true;
   }
   return false;
 }
@@ -75,7 +76,7 @@ struct gs_record {
   int32_t* natt = nullptr;
   int32_t* status = nullptr;
   double* y_final = nullptr;
-  float* wpart = nullptr;  // per-warp shared-weight gradient partials (LV UDE)
+  void* wpart = nullptr;  // per-warp shared-weight gradient partials (shared-weight problems)
   Counters* ctr = nullptr;
   Counters* ctr_host = nullptr;  // pinned
   int64_t n_cap = 0;             // capacity of the per-trajectory arrays
@@ -336,7 +337,7 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
   r->P = c.pi.P;
   r->k = c.k > 0 ? c.k : (c.pi.n_shared > 0 ? 1 : auto_ckpt_k(r, c.problem, c.pi.d, n));
   if (c.pi.n_shared > 0 && !r->wpart) {
-    const cudaError_t e = cudaMalloc(&r->wpart, (size_t)ude_max_warps() * UDE_NW_HOST * sizeof(float));
+    const cudaError_t e = cudaMalloc(&r->wpart, (size_t)ude_max_warps() * WPART_BYTES_PER_WARP);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   r->n = n;

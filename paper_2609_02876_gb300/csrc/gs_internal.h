@@ -50,7 +50,8 @@ struct RevArgs {
   double* loss;              // [n] or nullptr
   double* params_bar;        // [P][n] or nullptr
   double* y0_bar;            // [d][n] or nullptr
-  float* wpart;              // [warps][354] per-warp weight-gradient partials (shared-weight problems)
+  void* wpart;               // per-warp weight-gradient partials of shared-weight problems
+                             // ([warps][354] floats for the LV UDE, [warps][353] doubles for the neural Robertson)
   const int32_t* status;     // [n] recorded status
   const double* arena;
   long long arena_cap;       // segments (bounds every segment index read)
@@ -132,5 +133,8 @@ cudaError_t launch_rodas_refresh(int problem, int precision, const RevArgs& a, d
 // per-warp weight-gradient partials a shared-weight problem can produce).
 int ude_max_warps();
 constexpr int UDE_NW_HOST = 354;
+constexpr int NR_NW_HOST = 353;
+// Bytes of one warp's weight-gradient partial, the largest over the shared-weight problems.
+constexpr size_t WPART_BYTES_PER_WARP = (UDE_NW_HOST * 4 > NR_NW_HOST * 8) ? UDE_NW_HOST * 4 : NR_NW_HOST * 8;
 
 }  // namespace gs

@@ -34,6 +34,7 @@
 #include "gs_internal.h"
 #include "gs_rodas.cuh"
 #include "gs_ude.cuh"
+#include "gs_nrob.cuh"
 
 namespace gs {
 
@@ -80,6 +81,9 @@ __device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bo
 // ---------------------------------------------------------------------------
 struct Tsit5Method {
   static constexpr int ORDER = 5, ERR_ORDER = 4;  // solution order; lower order of the error estimate
+  // Step of the lanes without work in a warp-collective unit (zero cotangent):
+  // any value whose step stays finite.
+  static constexpr double IDLE_H = 0.0;
   template <class Pb, class R>
   struct Carry {
     R k1[Pb::D];  // FSAL: f(y) of the current accepted state
@@ -160,6 +164,7 @@ struct Tsit5Method {
 
 struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
   static constexpr int ORDER = 5, ERR_ORDER = 4;
+  static constexpr double IDLE_H = 1.0;  // W = I/(h gamma) - J needs h != 0
   template <class Pb, class R>
   struct Carry {};
   template <class Pb, class R>
@@ -214,7 +219,7 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
     unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
     rodas_reverse<Pb>(x, p, h, Y, U, LU, piv, rinv, cv, v, pacc);
 #pragma unroll
-    for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
     return ok;
   }
 };
@@ -223,6 +228,7 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
 // controller), f at the accepted state carried to the next step.
 struct Ros23Method {
   static constexpr int ORDER = 2, ERR_ORDER = 2;
+  static constexpr double IDLE_H = 1.0;
   template <class Pb, class R>
   struct Carry {
     R F0[Pb::D];  // f(y) of the current accepted state
@@ -279,7 +285,7 @@ struct Ros23Method {
     unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
     ros23_reverse<Pb>(x, p, h, k1, u2, Y1, LU, piv, rinv, cv, v, pacc);
 #pragma unroll
-    for (int c = 0; c < D; ++c) lam[c] = side ? add_(lam[c], v[c]) : v[c];
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
     return ok;
   }
 };
@@ -565,8 +571,27 @@ __device__ __forceinline__ bool next_save(const RevArgs& a, const double* s_save
 
 template <class R, int NP>
 using AccOf = typename std::conditional<std::is_same<R, float>::value, CompensatedAcc<NP>, PlainAcc<NP>>::type;
+// Shared-weight problems bring their own accumulator (per-trajectory theta plus
+// the warp's share of the weight gradient).
+template <class Pb>
+struct WeightAcc {
+  using type = void;
+};
+template <>
+struct WeightAcc<LvUde> {
+  using type = UdeAcc;
+};
+template <>
+struct WeightAcc<NeuralRobertson> {
+  using type = NrAcc;
+};
 template <class Pb, class R>
-using AccFor = typename std::conditional<HasWeights<Pb>::value, UdeAcc, AccOf<R, Pb::NP>>::type;
+using AccFor = typename std::conditional<HasWeights<Pb>::value, typename WeightAcc<Pb>::type, AccOf<R, Pb::NP>>::type;
+// Dynamic shared memory a shared-weight accumulator stages its factors in.
+template <class Pb>
+constexpr size_t weight_stage_bytes() {
+  return std::is_same<Pb, NeuralRobertson>::value ? NR_STAGE_DOUBLES * sizeof(double) : 0;
+}
 
 // ---------------------------------------------------------------------------
 // Reverse kernel, checkpoint interval k > 1: states inside a segment are
@@ -760,7 +785,7 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
 #pragma unroll
   for (int c = 0; c < D; ++c) lam[c] = yx[c] = R(0);
   Acc pacc;
-  if constexpr (COLL) pacc.init();
+  if constexpr (COLL) pacc.init(smem + ((ns + 1) & ~1));
   double loss = 0.0, tx = 0.0;
   long long seg = -1;
   int js = -1, segs_left = 0;
@@ -834,8 +859,8 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
       R yn[D], xin[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) xin[c] = busy ? yx[c] : R(0);
-      if (!M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, busy, us, xin, busy ? uh : 0.0, p, lam, pacc, loss,
-                                                   yn) &&
+      if (!M::template unit<Pb, R, USER_COT, Acc>(a, k, mode, busy, us, xin, busy ? uh : M::IDLE_H, p, lam, pacc,
+                                                   loss, yn) &&
           busy)
         mode = U_FAIL;
     }
@@ -849,7 +874,7 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
     }
   }
   if constexpr (COLL) {
-    if (a.wpart) pacc.finish(a.wpart + ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * UDE_NW);
+    if (a.wpart) pacc.finish(a.wpart, (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
   }
 }
 
@@ -958,9 +983,11 @@ inline cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
 
 template <class M, class Pb, class R>
 inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)((a.n_save + 1) & ~1) * sizeof(double);
+  size_t smem = (size_t)((a.n_save + 1) & ~1) * sizeof(double);
   if constexpr (HasWeights<Pb>::value) {
+    using Acc = AccFor<Pb, R>;
     if (a.k != 1) return cudaErrorInvalidValue;
+    smem += weight_stage_bytes<Pb>();
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, reverse_k1_kernel<M, Pb, R, false>, TPB_REV, smem);
     cudaError_t e = a.y_save_bar ? persistent_launch(reverse_k1_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a)
@@ -970,7 +997,9 @@ inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
     const long long need = (a.n + TPB_REV - 1) / TPB_REV;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    ude_reduce_kernel<<<(UDE_NW + 127) / 128, 128, 0, s>>>(a.wpart, (int)(blocks * (TPB_REV / 32)), a.shared_w_bar);
+    using Part = typename Acc::Part;
+    weight_reduce_kernel<Part><<<(Acc::NW + 127) / 128, 128, 0, s>>>(static_cast<const Part*>(a.wpart), Acc::NW,
+                                                                      (int)(blocks * (TPB_REV / 32)), a.shared_w_bar);
     return cudaGetLastError();
   } else {
   if (a.k == 1) {

@@ -175,9 +175,11 @@ __device__ __forceinline__ float* ude_stage() {
 //   GB (16 x 8):  sum over lanes of gz1 (x) [x, y, 1]  -> dW1, db1
 //   GC (32 x 8):  sum over lanes of [h2, 1] (x) go     -> dW3, db3
 struct UdeAcc {
+  using Part = float;
+  static constexpr int NW = UDE_NW;
   CompensatedAcc<2> th;
   float ga[3][4], gb[4], gc[2][4];
-  __device__ void init() {
+  __device__ void init(double*) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       ga[0][i] = ga[1][i] = ga[2][i] = 0.0f;
@@ -261,7 +263,8 @@ struct UdeAcc {
   }
 
   // Writes this warp's partial weight gradient (354 floats, the flat layout).
-  __device__ void finish(float* part) {
+  __device__ void finish(void* part_base, size_t warp) {
+    float* part = static_cast<float*>(part_base) + warp * UDE_NW;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     // C fragment element (row, col): c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
 #pragma unroll
@@ -281,12 +284,14 @@ struct UdeAcc {
   }
 };
 
-// Adds the per-warp partial weight gradients in warp order (FP64 sums).
-static __global__ void ude_reduce_kernel(const float* part, int nwarps, float* out) {
+// Adds the per-warp partial weight gradients (nw per warp) in warp order, in
+// FP64, and writes the FP32 result.
+template <class Part>
+__global__ void weight_reduce_kernel(const Part* part, int nw, int nwarps, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= UDE_NW) return;
+  if (i >= nw) return;
   double s = 0.0;
-  for (int w = 0; w < nwarps; ++w) s += (double)part[(size_t)w * UDE_NW + i];
+  for (int w = 0; w < nwarps; ++w) s += (double)part[(size_t)w * nw + i];
   out[i] = (float)s;
 }
 

@@ -30,7 +30,7 @@ def test_host_only_entry_points(lib):
     assert (o.precision, o.method, o.ckpt_k, o.max_steps, o.h0) == (0, 0, 0, 0, 0.0)
     d, P, s, nw = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     expect = {0: (3, 3, 0, 0), 1: (2, 1, 0, 0), 2: (3, 3, 1, 0), 3: (8, 12, 1, 0), 4: (2, 4, 0, 0),
-              5: (2, 2, 0, 354)}
+              5: (2, 2, 0, 354), 6: (3, 2, 1, 353)}
     for pid, e in expect.items():
         assert lib.gs_problem_info(pid, C.byref(d), C.byref(P), C.byref(s), C.byref(nw)) == 0
         assert (d.value, P.value, s.value, nw.value) == e
@@ -75,6 +75,10 @@ def _call(lib, **kw):
     (dict(pid=1, opt=dict(method=3)), N.GS_ERR_INVALID_ARG),  # no Rosenbrock23 kernel for Van der Pol
     (dict(pid=2, opt=dict(method=3, precision=1)), N.GS_ERR_INVALID_ARG),  # Rosenbrock23 runs in FP64
     (dict(opt=dict(method=4)), N.GS_ERR_INVALID_ARG),
+    (dict(pid=6), N.GS_ERR_INVALID_ARG),  # the neural Robertson needs shared weights
+    (dict(pid=6, w=1, opt=dict(precision=1)), N.GS_ERR_INVALID_ARG),  # stiff: FP64 only
+    (dict(pid=6, w=1, opt=dict(method=1)), N.GS_ERR_INVALID_ARG),  # no Tsit5 kernel for it
+    (dict(pid=6, w=1, opt=dict(ckpt_k=4)), N.GS_ERR_INVALID_ARG),  # shared weights: every state stored
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, kw, code):
     assert _call(lib, **kw) == code

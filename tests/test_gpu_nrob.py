@@ -1,0 +1,73 @@
+"""GPU parity of the Robertson neural right-hand side (shared-weight MLP in a
+stiff system) against the FP64 oracle on the GPU's own recorded mesh, for
+Rodas5P and Rosenbrock23.
+
+Per-trajectory results (loss, theta_bar, y0_bar) are FP64 on both sides:
+normwise relative error per trajectory vector 1e-10 (the GPU's tanh, exp and
+log1p are the CUDA library's, the oracle's the C library's; both within an
+ulp or two, and the stiff replay carries those differences). The shared-weight
+gradient is an FP64 sum on the GPU written out in FP32: normwise 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_02876_gb300 import api, build
+from paper_2609_02876_gb300 import workloads as W
+from tests.test_gpu_tsit5 import assert_close, dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def workload(n):
+    wl = W.make("nrob", n)
+    w32 = np.asarray(wl["w"], dtype=np.float32)
+    return dict(wl, w=w32.astype(np.float64)), torch.as_tensor(w32, device="cuda")
+
+
+@pytest.mark.parametrize("method,om", [("rodas5p", oracle.METHOD_RODAS5P),
+                                       ("rosenbrock23", oracle.METHOD_ROSENBROCK23)])
+def test_nrob_record_and_reverse_match_oracle(method, om):
+    n = 96
+    wl, SW = workload(n)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    rec, ysv, st = api.forward_record("nrob", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                      layout="soa", shared_w=SW, method=method)
+    assert (st.cpu().numpy() == 0).all()
+    np.testing.assert_allclose(ysv.cpu().numpy().sum(1), 1.0, atol=1e-12)  # mass
+    g = api.reverse(rec, P, Y, layout="soa", shared_w=SW)
+    off, h = rec.export_mesh()
+    o = oracle.replay_grad("nrob", wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h, method=om,
+                           w=wl["w"])
+    assert o["ok"].all()
+    assert_close(ysv.permute(2, 0, 1).cpu().numpy(), o["y_save"], "y_save", rtol=1e-10)
+    assert_close(g["loss"].cpu().numpy(), o["loss"], "loss", rtol=1e-10)
+    assert_close(g["params_bar"].cpu().numpy().T, o["params_bar"], "params_bar", rtol=1e-10)
+    assert_close(g["y0_bar"].cpu().numpy().T, o["y0_bar"], "y0_bar", rtol=1e-10)
+    wb = g["shared_w_bar"].cpu().numpy().astype(np.float64)
+    err = np.abs(wb - o["w_bar"]).max() / np.abs(o["w_bar"]).max()
+    assert err <= 1e-6, err
+
+
+def test_nrob_weight_gradient_is_deterministic_and_solve_grad_agrees():
+    n = 200
+    wl, SW = workload(n)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    a = api.solve_grad("nrob", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                       shared_w=SW, method="rosenbrock23")
+    b = api.solve_grad("nrob", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                       shared_w=SW, method="rosenbrock23")
+    np.testing.assert_array_equal(a["shared_w_bar"].cpu().numpy(), b["shared_w_bar"].cpu().numpy())
+    np.testing.assert_array_equal(a["params_bar"].cpu().numpy(), b["params_bar"].cpu().numpy())
+    rec, _, _ = api.forward_record("nrob", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                   layout="soa", shared_w=SW, method="rosenbrock23", want_saves=False)
+    g = api.reverse(rec, P, Y, layout="soa", shared_w=SW)
+    np.testing.assert_array_equal(a["params_bar"].cpu().numpy(), g["params_bar"].cpu().numpy())
+    np.testing.assert_array_equal(a["shared_w_bar"].cpu().numpy(), g["shared_w_bar"].cpu().numpy())
