@@ -2,10 +2,14 @@
 stiff system) against the FP64 oracle on the GPU's own recorded mesh, for
 Rodas5P and Rosenbrock23.
 
-Per-trajectory results (loss, theta_bar, y0_bar) are FP64 on both sides:
-normwise relative error per trajectory vector 1e-10 (the GPU's tanh, exp and
-log1p are the CUDA library's, the oracle's the C library's; both within an
-ulp or two, and the stiff replay carries those differences). The shared-weight
+Per-trajectory results are FP64 on both sides. States and losses: normwise
+relative error per trajectory vector 1e-10 (the GPU's tanh, exp and log1p are
+the CUDA library's, the oracle's the C library's; both within an ulp or two,
+and the stiff replay carries those differences). Gradients: the problem's own
+rounding floor is measured first, as the normwise disagreement of two exact
+FP64 evaluations of the same derivative in the oracle (forward-mode JVP along
+each input against the adjoint, on the same mesh); it reaches 1.8e-10 for
+Rodas5P here, so the bound is max(1e-10, 20 x floor). The shared-weight
 gradient is an FP64 sum on the GPU written out in FP32: normwise 1e-6.
 """
 import numpy as np
@@ -24,6 +28,23 @@ pytestmark = pytest.mark.gpu
 def _built():
     build.build()
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def rounding_floor(wl, off, h, om):
+    """Normwise fwd-vs-rev disagreement of the oracle's gradient, over theta and y0."""
+    g = oracle.replay_grad("nrob", wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h, method=om,
+                           w=wl["w"])
+    n, P = wl["params"].shape
+    d = wl["y0"].shape[1]
+    full = np.concatenate([g["params_bar"], g["y0_bar"]], 1)
+    worst = np.zeros(n)
+    for q in range(P + d):
+        pd, yd = np.zeros((n, P)), np.zeros((n, d))
+        (pd if q < P else yd)[:, q if q < P else q - P] = 1.0
+        j = oracle.replay_jvp("nrob", wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h, pd, yd,
+                              method=om, w=wl["w"])
+        worst = np.maximum(worst, np.abs(j["loss_dot"] - full[:, q]) / np.abs(full).max(1))
+    return worst.max()
 
 
 def workload(n):
@@ -49,8 +70,9 @@ def test_nrob_record_and_reverse_match_oracle(method, om):
     assert o["ok"].all()
     assert_close(ysv.permute(2, 0, 1).cpu().numpy(), o["y_save"], "y_save", rtol=1e-10)
     assert_close(g["loss"].cpu().numpy(), o["loss"], "loss", rtol=1e-10)
-    assert_close(g["params_bar"].cpu().numpy().T, o["params_bar"], "params_bar", rtol=1e-10)
-    assert_close(g["y0_bar"].cpu().numpy().T, o["y0_bar"], "y0_bar", rtol=1e-10)
+    tol = max(1e-10, 20.0 * rounding_floor(wl, off, h, om))
+    assert_close(g["params_bar"].cpu().numpy().T, o["params_bar"], "params_bar", rtol=tol)
+    assert_close(g["y0_bar"].cpu().numpy().T, o["y0_bar"], "y0_bar", rtol=tol)
     wb = g["shared_w_bar"].cpu().numpy().astype(np.float64)
     err = np.abs(wb - o["w_bar"]).max() / np.abs(o["w_bar"]).max()
     assert err <= 1e-6, err
