@@ -46,8 +46,14 @@ RHS_FLOPS = {"lorenz": dict(f=8, vjp=20, D=3), "vdp": dict(f=5, vjp=15, D=2),
              # LV UDE: MLP 2-16-16-2 forward (W1 64, W2 512, W3 64 flops, 32 tanh at ~5) plus the
              # linear terms; the VJP recomputes the forward and back-propagates (~750 more); the
              # shared-weight gradient contraction runs on the tensor cores and is not counted here
-             "lv_ude": dict(f=804, vjp=1554, D=2)}
-STIFF = {"robertson", "hires"}
+             "lv_ude": dict(f=804, vjp=1554, D=2),
+             # neural Robertson (FP64 MLP 3-16-16-1): f = 320 FMAs + the Robertson terms (tanh,
+             # exp, log1p counted as one flop each); the VJP adds the backward pass and the
+             # warp's weight contraction (353 weights x 32 lanes x 2 / 32 lanes); J is one
+             # forward + backward pass; the contraction a tangent pass, a double backward pass
+             # and two weight contractions
+             "nrob": dict(f=690, vjp=2050, jac=1330, con=4100, D=3)}
+STIFF = {"robertson", "hires", "nrob"}
 
 
 def unit_flops(problem, method=None):
@@ -364,6 +370,8 @@ def config_of(args, n):
           "hires": "HIRES (12 rates x logU[0.9,1.1], standard y0, t in [0,321.8122], 10 uniform saves)",
           "lv_ude": "LV UDE (a~U[1,1.5], d~U[2,3], y0~U[0.5,2]^2, t in [0,5], 10 uniform saves, shared MLP "
                     "2-16-16-2 tanh, Glorot seed 0; grads also wrt the 354 shared weights)",
+          "nrob": "Robertson neural RHS (k2 y2^2 -> MLP 3-16-16-1 tanh/softplus, FP64, Glorot seed 0; k1~U[0.04,0.06], "
+                  "k3=1e4, y0=(1,0,0), t in [1e-5,1e5], 20 log saves; grads also wrt the 353 shared weights)",
           }[args.problem]
     method = method_name(args)
     atol = 1e-10 if args.problem in STIFF else args.rtol * 1e-2
@@ -379,7 +387,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gradsolve", choices=["gradsolve", "reference"])
-    ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp", "robertson", "hires", "lv_ude"])
+    ap.add_argument("--problem", default="lorenz", choices=["lorenz", "vdp", "robertson", "hires", "lv_ude", "nrob"])
     ap.add_argument("--traj", type=int, default=1 << 24, help="trajectories per GPU")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
@@ -503,7 +511,7 @@ def main():
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
                      "reverse_tflops": rev_flops / rev_s / 1e12},
-            "e2e": e2e, "gpu_launches": (3 if args.problem == "lv_ude" else 2) * args.steps, "clocks": clocks}
+            "e2e": e2e, "gpu_launches": (3 if args.problem in ("lv_ude", "nrob") else 2) * args.steps, "clocks": clocks}
     if rank == 0:
         line["accuracy"] = accuracy_sample(args, args.precision)
     if rank == 0 and ws == 1 and args.precision == "fp64" and args.problem in ("lorenz", "vdp") \
