@@ -282,20 +282,17 @@ struct NrAcc {
     }
   }
 
-  // Both calls are kept out of line: one copy of the network passes and the
-  // weight contraction serves every stage of the step, instead of one inlined
-  // copy per stage.
   template <class Pb>
-  __device__ __noinline__ void vjp(const double (&y)[3], const double (&p)[2], const double (&v)[3],
-                                   double (&yb)[3]) {
+  __device__ __forceinline__ void vjp(const double (&y)[3], const double (&p)[2], const double (&v)[3],
+                                      double (&yb)[3]) {
     NeuralRobertson::Fwd F;
     NeuralRobertson::Back B;
     NeuralRobertson::vjp_nn(y, p, v, yb, th.s, F, B);
     accumulate(B.g3, B.g2, B.g1, F.h2, F.h1, y, 1.0);
   }
   template <class Pb>
-  __device__ __noinline__ void jac_contract(const double (&y)[3], const double (&p)[2], const double (&r)[3],
-                                            const double (&u)[3], double (&gy)[3]) {
+  __device__ __forceinline__ void jac_contract(const double (&y)[3], const double (&p)[2], const double (&r)[3],
+                                               const double (&u)[3], double (&gy)[3]) {
     NeuralRobertson::Fwd F;
     NeuralRobertson::Back B;
     NeuralRobertson::Tan T;

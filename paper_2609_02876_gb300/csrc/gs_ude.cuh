@@ -191,12 +191,10 @@ struct UdeAcc {
   __device__ double get(int q) const { return th.get(q); }
 
   // Warp-collective: every lane of the warp calls it (lanes without work pass
-  // v = 0, so their factors contribute exactly zero). Kept out of line: one copy
-  // of the network's backward pass and of the MMA accumulation serves the six
-  // stages, instead of six inlined copies whose interleaving spilled registers.
+  // v = 0, so their factors contribute exactly zero).
   template <class Pb>
-  __device__ __noinline__ void vjp(const float (&y)[2], const float (&p)[2], const float (&v)[2],
-                                   float (&yb)[2]) {
+  __device__ __forceinline__ void vjp(const float (&y)[2], const float (&p)[2], const float (&v)[2],
+                                      float (&yb)[2]) {
     LvUde::Factors fa;
     float x[2] = {0.0f, 0.0f};
     LvUde::backprop(y, p, v, yb, x, fa);
