@@ -56,6 +56,14 @@ RHS_FLOPS = {"lorenz": dict(f=8, vjp=20, D=3), "vdp": dict(f=5, vjp=15, D=2),
 STIFF = {"robertson", "hires", "nrob"}
 
 
+# DRAM bytes per accepted step, read + write, measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, one launch of each kernel) on the first 2^20 trajectories of
+# the same Lorenz FP64 workload (45.15 accepted steps per trajectory); a launch's
+# traffic grows in proportion to its accepted steps.
+TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse"): (4625075712 + 71750656) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "record"): (66017280 + 2269651712) / (45.15 * 2 ** 20)}
+
+
 def unit_flops(problem, method=None):
     c = RHS_FLOPS[problem]
     f, v, D = c["f"], c["vjp"], c["D"]
@@ -506,7 +514,10 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": config_of(args, n),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "kernel": f"{dominant}_kernel<{method_name(args)}>",
+                         "traffic": (TRAFFIC_PER_STEP[(args.problem, args.precision, dominant)] * S_tot
+                                     if (args.problem, args.precision, dominant) in TRAFFIC_PER_STEP
+                                     and args.method is None else None),
+                         "kernel": f"{dominant}_kernel<{method_name(args)}>",
                          "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz"},
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
