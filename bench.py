@@ -532,6 +532,12 @@ def main():
                          "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz"},
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
+                     "record_dram_gbs": (TRAFFIC_PER_STEP[(args.problem, args.precision, "record")] * S_tot / fwd_s / 1e9
+                                         if (args.problem, args.precision, "record") in TRAFFIC_PER_STEP
+                                         and args.method is None else None),
+                     "reverse_dram_gbs": (TRAFFIC_PER_STEP[(args.problem, args.precision, "reverse")] * S_tot / rev_s / 1e9
+                                          if (args.problem, args.precision, "reverse") in TRAFFIC_PER_STEP
+                                          and args.method is None else None),
                      "reverse_tflops": rev_flops / rev_s / 1e12},
             "e2e": e2e, "gpu_launches": (3 if args.problem in ("lv_ude", "nrob") else 2) * args.steps, "clocks": clocks}
     if rank == 0:
