@@ -19,7 +19,16 @@
 // exactly as printed in the paper's Appendix A ("Benchmark problem definitions").
 //
 // Parity pins: see tests/test_oracle_*.py (order conditions, closed-form linear
-// replay, complex-step gradients, finite differences, invariants).
+// replay, complex-step gradients, finite differences, invariants, Rosenbrock23's
+// stability function and error estimate, the neural term's weight derivatives).
+//
+// Parity unpinned (no value outside this file fixes them; they only shape the
+// mesh, which the gradient treats as data): the step-size controller constants
+// (safety 0.9, clamp [0.2, 10], exponent 1/(q+1) with q = 4 for Tsit5 and
+// Rodas5P and q = 2 for Rosenbrock23), the starting-step algorithm's order
+// argument, the end-of-span sliver 1e-12 and the quartered step after a
+// singular linear system; and Rodas5P's coefficients beyond what its order
+// conditions and stiff accuracy fix.
 
 #include <algorithm>
 #include <cmath>
