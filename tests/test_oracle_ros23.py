@@ -5,7 +5,8 @@ own formulas:
 - its stability function R(z) (one step of y' = lambda y) agrees with e^z to
   second order, vanishes at z -> -infinity (L-stability) and keeps |R| <= 1 on
   the imaginary axis (a rotation is never amplified);
-- its error estimate is the step's true local error to leading order;
+- its error estimate is the step's true local error to leading order, and
+  y_new + e is third order;
 - on a nonlinear problem the replay converges with order 2;
 - it conserves Robertson's total mass (a linear invariant of f);
 - its discrete adjoint equals a dual-number JVP of the same replay and central
@@ -52,6 +53,17 @@ def test_error_estimate_is_the_local_error_to_leading_order():
         yn, e = one_step([lam, 0, 0, -2.0], [1.0, 1.0], h)
         true = yn[0] - np.exp(np.array([lam, -2.0]) * h)
         np.testing.assert_allclose(e[0] / true, -1.0, atol=0.01 * h / 0.01)
+
+
+def test_embedded_solution_is_third_order():
+    """y_new + e is the pair's third-order solution: its local error falls by 16
+    per halving of h (against 8 for y_new); a wrong e32 leaves it at 8."""
+    for lam in (-1.3, 0.7):
+        hs = np.array([0.08, 0.04, 0.02, 0.01])
+        yn, e = one_step([lam, 0, 0, 0], [1.0, 0.0], hs)
+        err3 = np.abs(yn[:, 0] + e[:, 0] - np.exp(lam * hs))
+        r = err3[:-1] / err3[1:]
+        assert np.all((r > 14.5) & (r < 18.0)), r
 
 
 def test_replay_converges_with_order_two():
