@@ -38,15 +38,27 @@ bool problem_info(int pid, ProblemInfo* out) {
 // 16-byte multiple for vector stores.
 int segw_of(int d, int k) { return ((2 + d + k) + 1) & ~1; }
 
-// Expected accepted steps per trajectory, used only for the first arena size.
+// Expected accepted steps per trajectory at rtol 1e-6, used for the first arena
+// size and the choice of the record layout; an underestimate costs one rerun.
 int step_guess(int pid) {
   switch (pid) {
-    case GS_LORENZ: return 64;
-    case GS_VDP: return 192;
-    case GS_LV_UDE: return 64;
+    case GS_LORENZ: return 48;
+    case GS_VDP: return 100;
+    case GS_LV_UDE: return 40;
   }
   return 256;
 }
+// The same for a tolerance rtol: a method of error order q takes ~rtol^(-1/(q+1))
+// steps (q = 4 here for the explicit problems).
+int step_guess(int pid, double rtol) {
+  const double scale = std::pow(1e-6 / (rtol > 0.0 ? rtol : 1e-6), 0.2);
+  const double g = step_guess(pid) * (scale < 1.0 ? 1.0 : scale);
+  return (int)std::ceil(g);
+}
+
+// Doubles per segment of a stored-stage record (k = 1): [prev, t, y[d], h,
+// Y_1..Y_5 [5d]], rounded up to a 16-byte multiple.
+int stage_segw_of(int d) { return ((3 + 6 * d) + 1) & ~1; }
 
 // Counters that the kernels update; one small device block per record.
 struct Counters {
@@ -77,6 +89,11 @@ struct gs_record {
   int32_t* status = nullptr;
   double* y_final = nullptr;
   void* wpart = nullptr;  // per-warp shared-weight gradient partials (shared-weight problems)
+  // Stored stages (gs_solve_grad's workspace, Tsit5 FP64, k = 1): segments also
+  // hold each step's stage inputs, side_stg [n_save][6][d][n] the side steps'.
+  int stages = 0;
+  double* side_stg = nullptr;
+  size_t side_cap = 0;  // doubles
   Counters* ctr = nullptr;
   Counters* ctr_host = nullptr;  // pinned
   int64_t n_cap = 0;             // capacity of the per-trajectory arrays
@@ -118,7 +135,7 @@ void free_arrays(gs_record* r) {
 constexpr int kMaxDim = 8;  // largest state dimension of the registry
 
 size_t record_bytes(const gs_record* r) {
-  return (size_t)r->arena_cap * r->segw * sizeof(double) +
+  return (size_t)r->arena_cap * r->segw * sizeof(double) + r->side_cap * sizeof(double) +
          (size_t)r->n_cap * (sizeof(long long) + 3 * sizeof(int32_t) + kMaxDim * sizeof(double)) +
          sizeof(Counters);
 }
@@ -174,6 +191,7 @@ void destroy(gs_record* r) {
   cudaFree(r->arena);
   cudaFree(r->fwd_base);
   cudaFree(r->fwd_seg);
+  cudaFree(r->side_stg);
   cudaFree(r->ctr);
   cudaFree(r->wpart);
   cudaFreeHost(r->ctr_host);
@@ -277,9 +295,11 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
   std::memcpy(a.save_t, r->save_t, sizeof(double) * r->n_save);
   a.y_save = y_save;
   a.step_counts = c.step_counts;
-  a.k = r->k;
-  a.segw = r->segw;
   for (int attempt = 0; attempt < 3; ++attempt) {
+    a.k = r->k;
+    a.segw = r->segw;
+    a.stages = r->stages;
+    a.side_stg = r->stages ? r->side_stg : nullptr;
     cudaError_t e = cudaMemsetAsync(r->ctr, 0, sizeof(Counters), s);
     if (e != cudaSuccess) return cuda_fail(e);
     a.arena = r->arena;
@@ -306,9 +326,15 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
       r->nseg_total = (long long)r->ctr_host->arena_top;
       return GS_OK;
     }
-    // The arena was too small: size it to the demand just measured (+1/8) and rerun.
+    // The arena was too small: size it to the demand just measured (+1/8) and rerun
+    // (as a compact record if the stored-stage one does not fit).
     const long long need = (long long)r->ctr_host->arena_top;
     gs_status st = ensure_arena(r, need + need / 8 + 1024, r->segw);
+    if (st == GS_ERR_OOM && r->stages) {
+      r->stages = 0;
+      r->segw = segw_of(r->d, r->k);
+      st = ensure_arena(r, need + need / 8 + 1024, r->segw);
+    }
     if (st != GS_OK) return st;
   }
   return GS_ERR_OOM;
@@ -327,15 +353,31 @@ int auto_ckpt_k(const gs_record* r, int problem, int d, int64_t n) {
   return 14 - d > 1 ? 14 - d : 1;
 }
 
+// Stored stages when the caller allows them (gs_solve_grad), the method and
+// precision support them (Tsit5, FP64, no shared weights), k is automatic, and
+// the expected record with its side-step stages takes at most 70% of the free
+// device memory (plus what this workspace already holds).
+bool choose_stages(const gs_record* r, const Call& c, int64_t n, int n_save, double rtol) {
+  if (c.method != GS_METHOD_TSIT5 || c.precision != GS_FP64 || c.pi.n_shared > 0 || c.k > 1) return false;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
+  const double held = (double)r->arena_cap * r->segw * sizeof(double) + (double)r->side_cap * sizeof(double);
+  const double m = (double)(n > 0 ? n : 1);
+  const double want = m * (1.1 * step_guess(c.problem, rtol) + 1.0) * stage_segw_of(c.pi.d) * sizeof(double) +
+                      m * n_save * 6.0 * c.pi.d * sizeof(double);
+  return want <= 0.7 * ((double)free_b + held);
+}
+
 gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double t1, const double* save_t,
-                       int n_save, double rtol, double atol) {
+                       int n_save, double rtol, double atol, bool allow_stages = false) {
   cudaGetDevice(&r->device);
   r->problem = c.problem;
   r->method = c.method;
   r->precision = c.precision;
   r->d = c.pi.d;
   r->P = c.pi.P;
-  r->k = c.k > 0 ? c.k : (c.pi.n_shared > 0 ? 1 : auto_ckpt_k(r, c.problem, c.pi.d, n));
+  r->stages = (allow_stages && choose_stages(r, c, n, n_save, rtol)) ? 1 : 0;
+  r->k = r->stages ? 1 : (c.k > 0 ? c.k : (c.pi.n_shared > 0 ? 1 : auto_ckpt_k(r, c.problem, c.pi.d, n)));
   if (c.pi.n_shared > 0 && !r->wpart) {
     const cudaError_t e = cudaMalloc(&r->wpart, (size_t)ude_max_warps() * WPART_BYTES_PER_WARP);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -352,14 +394,29 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
   if (c.kernel_ms && (st = ensure_events(r)) != GS_OK) return st;
   st = ensure_arrays(r, n, r->d);
   if (st != GS_OK) return st;
-  const int segw = segw_of(r->d, r->k);
+  if (r->stages) {
+    const size_t need = (size_t)(n > 0 ? n : 1) * (size_t)(n_save > 0 ? n_save : 1) * 6 * r->d;
+    if (r->side_cap < need) {
+      cudaFree(r->side_stg);
+      r->side_stg = nullptr;
+      r->side_cap = 0;
+      const cudaError_t e = cudaMalloc(&r->side_stg, need * sizeof(double));
+      if (e != cudaSuccess) {
+        r->stages = 0;  // fall back to the compact record
+        r->k = c.k > 0 ? c.k : auto_ckpt_k(r, c.problem, c.pi.d, n);
+      } else {
+        r->side_cap = need;
+      }
+    }
+  }
+  const int segw = r->stages ? stage_segw_of(r->d) : segw_of(r->d, r->k);
   if (r->segw != segw) {
     cudaFree(r->arena);
     r->arena = nullptr;
     r->arena_cap = 0;
     r->segw = segw;
   }
-  const long long want = (long long)(n > 0 ? n : 1) * ((step_guess(c.problem) + r->k - 1) / r->k + 1);
+  const long long want = (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol) + r->k - 1) / r->k + 1);
   if (r->arena_cap > 0 && r->arena_cap < want / 4) {  // far too small for this ensemble: start over
     cudaFree(r->arena);
     r->arena = nullptr;
@@ -367,6 +424,13 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
   }
   if (r->arena_cap == 0) {
     st = ensure_arena(r, want, segw);
+    if (st == GS_ERR_OOM && r->stages) {  // the stored-stage record does not fit: compact record
+      r->stages = 0;
+      r->k = c.k > 0 ? c.k : auto_ckpt_k(r, c.problem, c.pi.d, n);
+      r->segw = segw_of(r->d, r->k);
+      st = ensure_arena(r, (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol) + r->k - 1) / r->k + 1),
+                        r->segw);
+    }
     if (st != GS_OK) return st;
   }
   return GS_OK;
@@ -399,6 +463,8 @@ gs_status launch_reverse(const gs_record* r, const double* params, const float* 
   a.work = &r->ctr->work_rev;
   a.k = r->k;
   a.segw = r->segw;
+  a.stages = r->stages;
+  a.side_stg = r->stages ? r->side_stg : nullptr;
   cudaError_t e = cudaMemsetAsync(&r->ctr->work_rev, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   e = launch_reverse_m(r->method, r->problem, r->precision, a, s);
@@ -488,8 +554,8 @@ gs_status jvp_common(const gs_record* r, const double* params, const double* y0,
 gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* params, const double* y0,
                         const float* shared_w, double t0, double t1, const double* save_t, int n_save, double rtol,
                         double atol, cudaStream_t s, double* loss_out, double* params_bar, double* y0_bar,
-                        float* shared_w_bar, int32_t* traj_status) {
-  gs_status st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol);
+                        float* shared_w_bar, int32_t* traj_status, bool allow_stages) {
+  gs_status st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol, allow_stages);
   if (st != GS_OK) return st;
   st = run_record(r, c, n, params, y0, shared_w, nullptr, s);
   if (st != GS_OK) return st;
@@ -675,7 +741,7 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
   gs_record* r = workspace(dev);
   if (!r) return GS_ERR_OOM;
   return solve_grad_in(r, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
-                       loss_out, params_bar, y0_bar, shared_w_bar, traj_status);
+                       loss_out, params_bar, y0_bar, shared_w_bar, traj_status, true);
 }
 
 gs_status gs_solve(int problem_id, int64_t n, const double* params, const double* y0, const float* shared_w,
@@ -779,7 +845,7 @@ gs_status gs_solve_grad_ctx(gs_context* ctx, int problem_id, int64_t n, const do
   if (dev != ctx->device) return GS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(ctx->mu);
   return solve_grad_in(ctx->ws, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol,
-                       (cudaStream_t)stream, loss_out, params_bar, y0_bar, shared_w_bar, traj_status);
+                       (cudaStream_t)stream, loss_out, params_bar, y0_bar, shared_w_bar, traj_status, false);
 }
 
 gs_status gs_record_bytes(const gs_record* rec, size_t* bytes) {

@@ -35,6 +35,11 @@ struct FwdArgs {
   int* any_failed;                // set when a trajectory ends with a non-OK status
   int k;                          // accepted steps per segment
   int segw;                       // doubles per segment
+  // Stored stages (Tsit5, k = 1): each segment also holds the stage inputs
+  // Y_1..Y_5 of its step after h, and side_stg [n_save][6][d][n] receives
+  // Y_1..Y_6 of every save-time side step (Y_6 = the save state).
+  int stages;
+  double* side_stg;
   double save_t[MAX_SAVE_HOST];
 };
 
@@ -60,6 +65,8 @@ struct RevArgs {
   const double* y_final;
   unsigned long long* work;
   int k, segw;
+  int stages;                // the record holds stage inputs (see FwdArgs)
+  const double* side_stg;
   double save_t[MAX_SAVE_HOST];
 };
 

@@ -81,6 +81,7 @@ __device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bo
 // ---------------------------------------------------------------------------
 struct Tsit5Method {
   static constexpr int ORDER = 5, ERR_ORDER = 4;  // solution order; lower order of the error estimate
+  static constexpr bool kStages = true;           // records may store stage inputs
   // Step of the lanes without work in a warp-collective unit (zero cotangent):
   // any value whose step stays finite.
   static constexpr double IDLE_H = 0.0;
@@ -111,6 +112,38 @@ struct Tsit5Method {
       next.k1[c] = K[6][c];
     }
     return true;
+  }
+  // The trial step that also returns its stage inputs Y_0..Y_6 (Y_6 = y_new).
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial_y(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                 const Carry<Pb, R>& cy, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                                 Carry<Pb, R>& next, R (&Y)[7][Pb::D]) {
+    constexpr int D = Pb::D;
+    R K[7][D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) K[0][c] = cy.k1[c];
+    tsit5_stages<Pb, R, 7>(y, p, to_r<R>(h), Y, K);
+    tsit5_error<Pb, R>(K, to_r<R>(h), e);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      ynew[c] = Y[6][c];
+      next.k1[c] = K[6][c];
+    }
+    return true;
+  }
+  // Reverse unit over stored stage inputs Y_0..Y_5 (and, for a side unit, the
+  // save state Y_6): no stage is recomputed. Same arithmetic as unit().
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static void unit_stored(const RevArgs& a, long long k, int mode, bool active, int us,
+                                                     const R (&Y)[7][Pb::D], double h, const R (&p)[Pb::NP],
+                                                     R (&lam)[Pb::D], Acc& pacc, double& loss) {
+    constexpr int D = Pb::D;
+    const bool side = (mode == U_SIDE);
+    R cv[D], v[D];
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, Y[6], lam, cv, loss);
+    tsit5_reverse<Pb, R>(Y, p, to_r<R>(h), cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
   }
   template <class Pb, class R>
   __device__ __forceinline__ static bool side(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
@@ -164,6 +197,7 @@ struct Tsit5Method {
 
 struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
   static constexpr int ORDER = 5, ERR_ORDER = 4;
+  static constexpr bool kStages = false;
   static constexpr double IDLE_H = 1.0;  // W = I/(h gamma) - J needs h != 0
   template <class Pb, class R>
   struct Carry {};
@@ -228,6 +262,7 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
 // controller), f at the accepted state carried to the next step.
 struct Ros23Method {
   static constexpr int ORDER = 2, ERR_ORDER = 2;
+  static constexpr bool kStages = false;
   static constexpr double IDLE_H = 1.0;
   template <class Pb, class R>
   struct Carry {
@@ -293,8 +328,11 @@ struct Ros23Method {
 // ---------------------------------------------------------------------------
 // Record kernel
 // ---------------------------------------------------------------------------
-template <class M, class Pb, class R, bool SAVES>
+// SAVES: save-time side steps run (for y_save, or for the stored side stages);
+// STAGES: the record stores stage inputs (k = 1).
+template <class M, class Pb, class R, bool SAVES, bool STAGES>
 __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
+  static_assert(!STAGES || (SAVES && M::kStages), "stored stages need side steps and a method that exposes stages");
   constexpr int D = Pb::D, NP = Pb::NP;
   using Carry = typename M::template Carry<Pb, R>;
   extern __shared__ double smem[];
@@ -378,8 +416,10 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
     if (k >= 0) {
       if (SAVES) {
         while (jp < je && same_time(s_save[jp], tp)) {  // a save on that mesh point: its state, no step
+          if (a.y_save) {
 #pragma unroll
-          for (int c = 0; c < D; ++c) a.y_save[((long long)jp * D + c) * n + k] = (double)yp[c];
+            for (int c = 0; c < D; ++c) a.y_save[((long long)jp * D + c) * n + k] = (double)yp[c];
+          }
           ++jp;
         }
         if (jp < je) um = U_SIDE;
@@ -406,6 +446,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
     __syncwarp();
     asm volatile("" : "+r"(um));
     R yn[D], e[D];
+    R Ys[7][D];  // stage inputs of this unit (stored-stage records)
     Carry next;
     double q = 2.0;
     bool solved = true;
@@ -416,15 +457,27 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       for (int c = 0; c < D; ++c) xin[c] = sd ? yp[c] : y[c];
       const Carry cin = sd ? cyp : cy;
       const double hx = sd ? s_save[jp] - tp : h;
-      solved = M::template trial<Pb, R>(xin, p, hx, cin, yn, e, next);
+      if constexpr (STAGES) {
+        solved = M::template trial_y<Pb, R>(xin, p, hx, cin, yn, e, next, Ys);
+      } else {
+        solved = M::template trial<Pb, R>(xin, p, hx, cin, yn, e, next);
+      }
       if (!sd) {
         ++natt;
         q = err_meansq<D>(e, y, yn, a.rtol, a.atol);
       }
     }
     if (SAVES && um == U_SIDE) {
+      if (a.y_save) {
 #pragma unroll
-      for (int c = 0; c < D; ++c) a.y_save[((long long)jp * D + c) * n + k] = solved ? (double)yn[c] : nan_d();
+        for (int c = 0; c < D; ++c) a.y_save[((long long)jp * D + c) * n + k] = solved ? (double)yn[c] : nan_d();
+      }
+      if constexpr (STAGES) {  // Y_1..Y_6 of the side step
+#pragma unroll
+        for (int j = 1; j < 7; ++j)
+#pragma unroll
+          for (int c = 0; c < D; ++c) a.side_stg[(((long long)jp * 6 + (j - 1)) * D + c) * n + k] = to_d(Ys[j][c]);
+      }
       ++jp;
     }
     const bool trial = (um == U_STEP);
@@ -443,12 +496,20 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
         while (js < ns && dkey(s_save[js]) < key_tn) ++js;
         je = js;
         while (js < ns && same_time(s_save[js], tn)) {
+          if (a.y_save) {
 #pragma unroll
-          for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = (double)yn[c];
+            for (int c = 0; c < D; ++c) a.y_save[((long long)js * D + c) * n + k] = (double)yn[c];
+          }
           ++js;
         }
       }
       if (a.k > 0) stg[(2 + D + slot) * TB] = h;
+      if constexpr (STAGES) {  // k = 1: the step's stage inputs Y_1..Y_5 follow h
+#pragma unroll
+        for (int j = 1; j < 6; ++j)
+#pragma unroll
+          for (int c = 0; c < D; ++c) stg[(3 + D + (j - 1) * D + c) * TB] = to_d(Ys[j][c]);
+      }
       ++slot;
       t = tn;
 #pragma unroll
@@ -761,7 +822,14 @@ __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
 // state S (y(t1)); then for i = S..1: load segment i, step VJP, the saves
 // attached to state i-1.
 // ---------------------------------------------------------------------------
-template <class M, class Pb, class R, bool USER_COT>
+// STAGES: the record holds every step's stage inputs after h (segments of
+// stage_segw<D>() doubles) and side_stg the side steps' Y_1..Y_6: the units
+// load them instead of recomputing the stages.
+template <int D>
+constexpr int stage_segw() {
+  return ((3 + 6 * D) + 1) & ~1;
+}
+template <class M, class Pb, class R, bool USER_COT, bool STAGES = false>
 __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
   constexpr int D = Pb::D, NP = Pb::NP;
   constexpr bool COLL = HasWeights<Pb>::value;
@@ -831,23 +899,54 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
 
     int mode = U_NONE, us = 0;
     double uh = 0.0;
+    R Yst[7][D];  // stored stage inputs of this unit (STAGES)
     if (k >= 0) {
       if (next_save<D, R, USER_COT>(a, s_save, k, js, tx, yx, lam, loss, us)) {
         mode = U_SIDE;
         uh = s_save[us] - tx;
+        if constexpr (STAGES) {
+#pragma unroll
+          for (int c = 0; c < D; ++c) Yst[0][c] = yx[c];
+#pragma unroll
+          for (int j = 1; j < 7; ++j)
+#pragma unroll
+            for (int c = 0; c < D; ++c) Yst[j][c] = to_r<R>(a.side_stg[(((long long)us * 6 + (j - 1)) * D + c) * a.n + k]);
+        }
       } else if (seg < 0) {
         mode = (segs_left == 0) ? U_DONE : U_FAIL;
       } else if (seg >= a.arena_cap || segs_left <= 0) {
         mode = U_FAIL;  // inconsistent record
       } else {
-        // segment i: [prev, t_{i-1}, y_{i-1}[D], h_i]
+        // segment i: [prev, t_{i-1}, y_{i-1}[D], h_i (, Y_1..Y_5 of step i)]
         const double* sp = a.arena + seg * a.segw;
         const double2 w0 = *reinterpret_cast<const double2*>(sp);
         seg = __double_as_longlong(w0.x);
         tx = w0.y;
+        if constexpr (STAGES) {
+          constexpr int SW = stage_segw<D>();
+          double buf[SW];
 #pragma unroll
-        for (int c = 0; c < D; ++c) yx[c] = to_r<R>(sp[2 + c]);
-        uh = sp[2 + D];
+          for (int w = 1; w < SW / 2; ++w) {
+            const double2 v = reinterpret_cast<const double2*>(sp)[w];
+            buf[2 * w] = v.x;
+            buf[2 * w + 1] = v.y;
+          }
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            yx[c] = to_r<R>(buf[2 + c]);
+            Yst[0][c] = yx[c];
+            Yst[6][c] = yx[c];  // not used by a step unit
+          }
+          uh = buf[2 + D];
+#pragma unroll
+          for (int j = 1; j < 6; ++j)
+#pragma unroll
+            for (int c = 0; c < D; ++c) Yst[j][c] = to_r<R>(buf[3 + D + (j - 1) * D + c]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < D; ++c) yx[c] = to_r<R>(sp[2 + c]);
+          uh = sp[2 + D];
+        }
         --segs_left;
         mode = U_STEP;
       }
@@ -855,7 +954,9 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
 
     __syncwarp();
     const bool busy = (mode == U_STEP || mode == U_SIDE);
-    if (COLL || busy) {
+    if constexpr (STAGES) {
+      if (busy) M::template unit_stored<Pb, R, USER_COT, Acc>(a, k, mode, true, us, Yst, uh, p, lam, pacc, loss);
+    } else if (COLL || busy) {
       R yn[D], xin[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) xin[c] = busy ? yx[c] : R(0);
@@ -977,8 +1078,13 @@ inline cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long 
 template <class M, class Pb, class R>
 inline cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)(((a.n_save + 1) & ~1) + a.segw * TPB_FWD) * sizeof(double);
-  if (a.y_save) return persistent_launch(record_kernel<M, Pb, R, true>, TPB_FWD, smem, a.n, s, &a);
-  return persistent_launch(record_kernel<M, Pb, R, false>, TPB_FWD, smem, a.n, s, &a);
+  if constexpr (M::kStages && std::is_same<R, double>::value && !HasWeights<Pb>::value) {
+    if (a.stages) return persistent_launch(record_kernel<M, Pb, R, true, true>, TPB_FWD, smem, a.n, s, &a);
+  } else {
+    if (a.stages) return cudaErrorInvalidValue;
+  }
+  if (a.y_save) return persistent_launch(record_kernel<M, Pb, R, true, false>, TPB_FWD, smem, a.n, s, &a);
+  return persistent_launch(record_kernel<M, Pb, R, false, false>, TPB_FWD, smem, a.n, s, &a);
 }
 
 template <class M, class Pb, class R>
@@ -1002,6 +1108,16 @@ inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
                                                                       (int)(blocks * (TPB_REV / 32)), a.shared_w_bar);
     return cudaGetLastError();
   } else {
+  if constexpr (M::kStages && std::is_same<R, double>::value) {
+    if (a.stages) {
+      if (a.k != 1 || a.segw != stage_segw<Pb::D>()) return cudaErrorInvalidValue;
+      if (a.y_save_bar)
+        return persistent_launch(reverse_k1_kernel<M, Pb, R, true, true>, TPB_REV, smem, a.n, s, &a);
+      return persistent_launch(reverse_k1_kernel<M, Pb, R, false, true>, TPB_REV, smem, a.n, s, &a);
+    }
+  } else {
+    if (a.stages) return cudaErrorInvalidValue;
+  }
   if (a.k == 1) {
     if (a.y_save_bar) return persistent_launch(reverse_k1_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a);
     return persistent_launch(reverse_k1_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);
