@@ -58,10 +58,10 @@ STIFF = {"robertson", "hires", "nrob"}
 
 # DRAM bytes per accepted step, read + write, measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch of each kernel) on the first 2^20 trajectories of
-# the same Lorenz FP64 workload (45.15 accepted steps per trajectory); a launch's
-# traffic grows in proportion to its accepted steps.
-TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse"): (4625075712 + 71750656) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "record"): (66017280 + 2269651712) / (45.15 * 2 ** 20)}
+# the same Lorenz FP64 workload (45.15 accepted steps per trajectory), per record
+# layout; a launch's traffic grows in proportion to its accepted steps.
+TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "compact"): (4625075712 + 71750656) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "record", "compact"): (66017280 + 2269651712) / (45.15 * 2 ** 20)}
 
 
 def unit_flops(problem, method=None):
@@ -452,11 +452,12 @@ def main():
            "y0_bar": torch.empty((d, n), dtype=torch.float64, device="cuda"),
            "status": torch.empty(n, dtype=torch.int32, device="cuda")}
     kms = np.zeros(2, np.float32)
+    rinfo = np.zeros(2, np.int32)  # checkpoint interval k, stored stages
 
     def step(kernel_ms=None, counts=False):
         return api.solve_grad(args.problem, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
                               layout="soa", out=out, precision=args.precision, kernel_ms=kernel_ms,
-                              step_counts=counts, method=args.method, shared_w=SW)
+                              step_counts=counts, method=args.method, shared_w=SW, record_info=rinfo)
 
     for _ in range(args.warmup):
         step()
@@ -516,8 +517,16 @@ def main():
     # roofline of the dominant kernel (the reverse sweep), algorithmic flops / event-timed duration
     uf = unit_flops(args.problem, args.method)
     n_side = n * (len(wl["save_t"]) - 1)  # saves strictly inside a step (the last one sits on t1)
-    rev_flops = (S_tot + n_side) * uf["vjp_unit"]
-    fwd_flops = A_tot * uf["trial"]
+    stages = bool(rinfo[1])
+    if stages:
+        # stored stages: the record also runs the side steps (trial code) and the reverse
+        # sweep only propagates cotangents through the stored stages
+        rev_flops = (S_tot + n_side) * (uf["vjp_unit"] - uf["stage_fwd"])
+        fwd_flops = (A_tot + n_side) * uf["trial"]
+    else:
+        rev_flops = (S_tot + n_side) * uf["vjp_unit"]
+        fwd_flops = A_tot * uf["trial"]
+    layout = "stages" if stages else "compact"
     rev_s = statistics.mean(rev_ms) / 1e3
     fwd_s = statistics.mean(fwd_ms) / 1e3
     peak = fp_peak_tflops(args.precision)
@@ -529,18 +538,21 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": config_of(args, n),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": (TRAFFIC_PER_STEP[(args.problem, args.precision, dominant)] * S_tot
-                                     if (args.problem, args.precision, dominant) in TRAFFIC_PER_STEP
+                         "traffic": (TRAFFIC_PER_STEP[(args.problem, args.precision, dominant, layout)] * S_tot
+                                     if (args.problem, args.precision, dominant, layout) in TRAFFIC_PER_STEP
                                      and args.method is None else None),
                          "kernel": f"{dominant}_kernel<{method_name(args)}>",
                          "peak_source": "derived: 152 SMs x FMA lanes/clk/SM x 2 x 2070 MHz"},
             "kernels_ms": {"record": statistics.mean(fwd_ms), "reverse": statistics.mean(rev_ms)},
             "work": {"accepted_steps": S_tot, "attempted_steps": A_tot, "record_tflops": fwd_flops / fwd_s / 1e12,
-                     "record_dram_gbs": (TRAFFIC_PER_STEP[(args.problem, args.precision, "record")] * S_tot / fwd_s / 1e9
-                                         if (args.problem, args.precision, "record") in TRAFFIC_PER_STEP
+                     "record_layout": {"k": int(rinfo[0]), "stored_stages": stages},
+                     "record_dram_gbs": (TRAFFIC_PER_STEP[(args.problem, args.precision, "record", layout)] * S_tot
+                                         / fwd_s / 1e9
+                                         if (args.problem, args.precision, "record", layout) in TRAFFIC_PER_STEP
                                          and args.method is None else None),
-                     "reverse_dram_gbs": (TRAFFIC_PER_STEP[(args.problem, args.precision, "reverse")] * S_tot / rev_s / 1e9
-                                          if (args.problem, args.precision, "reverse") in TRAFFIC_PER_STEP
+                     "reverse_dram_gbs": (TRAFFIC_PER_STEP[(args.problem, args.precision, "reverse", layout)] * S_tot
+                                          / rev_s / 1e9
+                                          if (args.problem, args.precision, "reverse", layout) in TRAFFIC_PER_STEP
                                           and args.method is None else None),
                      "reverse_tflops": rev_flops / rev_s / 1e12},
             "e2e": e2e, "gpu_launches": (3 if args.problem in ("lv_ude", "nrob") else 2) * args.steps, "clocks": clocks}

@@ -22,7 +22,7 @@ TRAJ_STATUS = {0: "ok", 1: "maxsteps", 2: "dt_underflow", 3: "nonfinite", 4: "si
 class GsOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("ckpt_k", C.c_int), ("max_steps", C.c_int64),
                 ("h0", C.c_double), ("step_counts", C.c_void_p), ("kernel_ms", C.POINTER(C.c_float)),
-                ("timeout_ms", C.c_double)]
+                ("timeout_ms", C.c_double), ("record_info", C.POINTER(C.c_int32))]
 
 
 class GsError(RuntimeError):

@@ -31,7 +31,7 @@ def problem_info(problem):
 
 
 def _opts(precision="fp64", method=None, ckpt_k=0, max_steps=0, h0=0.0, step_counts=None,
-          kernel_ms=None, timeout_ms=0.0) -> N.GsOptions:
+          kernel_ms=None, timeout_ms=0.0, record_info=None) -> N.GsOptions:
     o = N.GsOptions()
     N.lib().gs_default_options(C.byref(o))
     o.precision = {"fp64": N.GS_FP64, "fp32_mixed": N.GS_FP32_MIXED}[precision]
@@ -44,6 +44,8 @@ def _opts(precision="fp64", method=None, ckpt_k=0, max_steps=0, h0=0.0, step_cou
     o.step_counts = step_counts.data_ptr() if step_counts is not None else None
     if kernel_ms is not None:  # a (2,) float32 numpy array filled with the kernels' device times
         o.kernel_ms = kernel_ms.ctypes.data_as(C.POINTER(C.c_float))
+    if record_info is not None:  # a (2,) int32 numpy array: checkpoint interval k, stored stages (0/1)
+        o.record_info = record_info.ctypes.data_as(C.POINTER(C.c_int32))
     return o
 
 

@@ -207,6 +207,7 @@ struct Call {
   int32_t* step_counts;
   float* kernel_ms;
   double timeout_ms;
+  int32_t* record_info;
 };
 
 // Kernel launches by method.
@@ -270,6 +271,7 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   c->kernel_ms = o.kernel_ms;
   if (!std::isfinite(o.timeout_ms) || o.timeout_ms < 0) return GS_ERR_INVALID_ARG;
   c->timeout_ms = o.timeout_ms;
+  c->record_info = o.record_info;
   if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_RODAS5P && !rodas_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_ROSENBROCK23 && !ros23_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
@@ -323,6 +325,10 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
     if (ws != GS_OK) return ws;
     if (!r->ctr_host->overflow) {
       if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[0], r->ev[0], r->ev[1]);
+      if (c.record_info) {
+        c.record_info[0] = r->k;
+        c.record_info[1] = r->stages;
+      }
       r->nseg_total = (long long)r->ctr_host->arena_top;
       return GS_OK;
     }

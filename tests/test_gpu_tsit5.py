@@ -300,3 +300,27 @@ def test_bounded_wait_returns_timeout_and_leaves_work_intact():
     s = api.solve_grad("lorenz", dev(small["params"].T), dev(small["y0"].T), small["t0"], small["t1"],
                        small["save_t"], small["rtol"], small["atol"], layout="soa", timeout_ms=60000.0)
     assert (s["status"].cpu().numpy() == 0).all()
+
+
+def test_record_layout_report_and_stored_stage_equality():
+    """gs_solve_grad stores stage inputs for Tsit5 in FP64 (when memory allows) and
+    reports it; a forward_record handle keeps the compact layout. Both layouts give
+    bit-identical gradients, also with a user cotangent-free save on a mesh point."""
+    wl = W.make("vdp", 777)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    info = np.zeros(2, np.int32)
+    s = api.solve_grad("vdp", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                       record_info=info)
+    assert tuple(info) == (1, 1)
+    rec_info = np.zeros(2, np.int32)
+    rec, _, _ = api.forward_record("vdp", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                   layout="soa", want_saves=False, record_info=rec_info)
+    assert rec_info[1] == 0
+    g = api.reverse(rec, P, Y, layout="soa")
+    np.testing.assert_array_equal(s["loss"].cpu().numpy(), g["loss"].cpu().numpy())
+    np.testing.assert_array_equal(s["params_bar"].cpu().numpy(), g["params_bar"].cpu().numpy())
+    np.testing.assert_array_equal(s["y0_bar"].cpu().numpy(), g["y0_bar"].cpu().numpy())
+    m = np.zeros(2, np.int32)
+    api.solve_grad("vdp", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                   precision="fp32_mixed", record_info=m)
+    assert m[1] == 0  # the mixed form keeps the compact record
