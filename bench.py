@@ -61,7 +61,9 @@ STIFF = {"robertson", "hires", "nrob"}
 # the same Lorenz FP64 workload (45.15 accepted steps per trajectory), per record
 # layout; a launch's traffic grows in proportion to its accepted steps.
 TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "compact"): (4625075712 + 71750656) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "record", "compact"): (66017280 + 2269651712) / (45.15 * 2 ** 20)}
+                    ("lorenz", "fp64", "record", "compact"): (66017280 + 2269651712) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "reverse", "stages"): (15093851392 + 89244160) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "record", "stages"): (1560973568 + 11288652032) / (45.15 * 2 ** 20)}
 
 
 def unit_flops(problem, method=None):
