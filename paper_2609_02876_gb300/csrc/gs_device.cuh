@@ -603,27 +603,30 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Reciprocal of a positive FP64 scale to FP32 accuracy (relative 2^-23): the
-// hardware FP32 reciprocal of the rounded value, converted back. Scales below
-// 1e-30 (outside the FP32 normal range) take the exact FP64 division.
-__device__ __forceinline__ double recip_scale(double sc) {
-  if (dbits(sc) < 0x39b4484bfeebc2a0ull) return 1.0 / sc;  // sc < 1e-30 (sc > 0)
-  return (double)__frcp_rn(__double2float_rn(sc));
-}
-
 // Weighted RMS error test of the paper's Sec. 2.1, as a mean square:
 // q = (1/D) sum_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2; accept iff q <= 1.
-// The scale and the sum are FP64; each ratio uses an FP32-accurate reciprocal
-// of the scale, so q carries a relative error below 1e-6: it decides accept /
-// reject and scales the next step, and never enters the accepted solution.
+// Each ratio is formed to FP32 accuracy (relative error below 1e-6 in q) and
+// the squares are summed in FP64: q decides accept / reject and scales the
+// next step, and never enters the accepted solution. The FP64 error e is
+// computed in FP64 (its terms cancel); the ratio's scale and reciprocal run on
+// the FP32 pipe with the bit-level conversions, leaving one FP64 FMA per
+// component. Components whose scale or state lies outside the range where
+// that is accurate (scale below 1e-30, |y| above 1e30) take the FP64 division.
 template <int D>
 __device__ __forceinline__ double err_meansq(const double (&e)[D], const double (&y)[D], const double (&yn)[D],
-                                             double rtol, double atol) {
+                                             double rtol, double atol, float rt, float at) {
+  constexpr unsigned long long BITS_1E30 = 0x46293e5939a08ceaull;  // 1e30
   double q = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const double sc = fma_(rtol, max_abs(y[c], yn[c]), atol);
-    const double r = mul_(e[c], recip_scale(sc));
+    const double m = max_abs(y[c], yn[c]);
+    const float sc = fmaf(rt, to_f(m), at);
+    double r;
+    if (dbits(m) < BITS_1E30 && sc >= 1e-30f) {
+      r = to_d(__fmul_rn(to_f(e[c]), __frcp_rn(sc)));
+    } else {
+      r = e[c] / fma_(rtol, m, atol);
+    }
     q = fma_(r, r, q);
   }
   return mul_(q, 1.0 / D);
@@ -634,8 +637,7 @@ __device__ __forceinline__ double err_meansq(const double (&e)[D], const double 
 // 1e-6 the ratios already carry), which keeps the FP64 pipe for the sum alone.
 template <int D>
 __device__ __forceinline__ double err_meansq(const float (&e)[D], const float (&y)[D], const float (&yn)[D],
-                                             double rtol, double atol) {
-  const float rt = (float)rtol, at = (float)atol;
+                                             double, double, float rt, float at) {
   double q = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {

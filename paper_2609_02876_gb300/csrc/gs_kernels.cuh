@@ -348,6 +348,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
   const double t1 = a.t1;
   const double sliver = 1e-12 * fmax(1.0, fabs(t1));
   const long long key_end = dkey(t1 - sliver);  // a step reaching past t1 - sliver is the last
+  const float rtf = (float)a.rtol, atf = (float)a.atol;  // the error norm's FP32 scale factors
   long long k = -1;
   bool drained = false;
   double t = 0.0, h = 0.0;
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       }
       if (!sd) {
         ++natt;
-        q = err_meansq<D>(e, y, yn, a.rtol, a.atol);
+        q = err_meansq<D>(e, y, yn, a.rtol, a.atol, rtf, atf);
       }
     }
     if (SAVES && um == U_SIDE) {
