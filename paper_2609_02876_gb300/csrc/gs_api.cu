@@ -45,6 +45,8 @@ int step_guess(int pid) {
     case GS_LORENZ: return 48;
     case GS_VDP: return 100;
     case GS_LV_UDE: return 40;
+    case GS_ROBERTSON: return 110;
+    case GS_HIRES: return 210;
   }
   return 256;
 }
@@ -56,9 +58,16 @@ int step_guess(int pid, double rtol) {
   return (int)std::ceil(g);
 }
 
-// Doubles per segment of a stored-stage record (k = 1): [prev, t, y[d], h,
-// Y_1..Y_5 [5d]], rounded up to a 16-byte multiple.
-int stage_segw_of(int d) { return ((3 + 6 * d) + 1) & ~1; }
+// Stored-stage records (k = 1): the doubles a step and a side step store (the
+// kernels' StageData payloads), and the segment [prev, t, y[d], h, step payload]
+// rounded up to a 16-byte multiple. Tsit5: Y_1..Y_5 (a side step also Y_6);
+// Rodas5P: U_0..U_7, the LU factors, pivot reciprocals and pivots (the stage
+// inputs and the save state are rebuilt from them).
+int stage_step_payload(int method, int d) { return method == GS_METHOD_RODAS5P ? 10 * d + d * d : 5 * d; }
+int stage_side_payload(int method, int d) {
+  return stage_step_payload(method, d) + (method == GS_METHOD_RODAS5P ? 0 : d);
+}
+int stage_segw_of(int method, int d) { return ((3 + d + stage_step_payload(method, d)) + 1) & ~1; }
 
 // Counters that the kernels update; one small device block per record.
 struct Counters {
@@ -364,13 +373,16 @@ int auto_ckpt_k(const gs_record* r, int problem, int d, int64_t n) {
 // the expected record with its side-step stages takes at most 70% of the free
 // device memory (plus what this workspace already holds).
 bool choose_stages(const gs_record* r, const Call& c, int64_t n, int n_save, double rtol) {
-  if (c.method != GS_METHOD_TSIT5 || c.precision != GS_FP64 || c.pi.n_shared > 0 || c.k > 1) return false;
+  if (c.method != GS_METHOD_TSIT5 && c.method != GS_METHOD_RODAS5P) return false;
+  if (c.precision != GS_FP64 || c.pi.n_shared > 0 || c.k > 1) return false;
+  if (stage_segw_of(c.method, c.pi.d) > MAX_STAGE_SEGW) return false;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
   const double held = (double)r->arena_cap * r->segw * sizeof(double) + (double)r->side_cap * sizeof(double);
   const double m = (double)(n > 0 ? n : 1);
-  const double want = m * (1.1 * step_guess(c.problem, rtol) + 1.0) * stage_segw_of(c.pi.d) * sizeof(double) +
-                      m * n_save * 6.0 * c.pi.d * sizeof(double);
+  const double want =
+      m * (1.1 * step_guess(c.problem, rtol) + 1.0) * stage_segw_of(c.method, c.pi.d) * sizeof(double) +
+      m * n_save * (double)stage_side_payload(c.method, c.pi.d) * sizeof(double);
   return want <= 0.7 * ((double)free_b + held);
 }
 
@@ -401,7 +413,8 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
   st = ensure_arrays(r, n, r->d);
   if (st != GS_OK) return st;
   if (r->stages) {
-    const size_t need = (size_t)(n > 0 ? n : 1) * (size_t)(n_save > 0 ? n_save : 1) * 6 * r->d;
+    const size_t need = (size_t)(n > 0 ? n : 1) * (size_t)(n_save > 0 ? n_save : 1) *
+                        (size_t)stage_side_payload(c.method, r->d);
     if (r->side_cap < need) {
       cudaFree(r->side_stg);
       r->side_stg = nullptr;
@@ -415,7 +428,7 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
       }
     }
   }
-  const int segw = r->stages ? stage_segw_of(r->d) : segw_of(r->d, r->k);
+  const int segw = r->stages ? stage_segw_of(c.method, r->d) : segw_of(r->d, r->k);
   if (r->segw != segw) {
     cudaFree(r->arena);
     r->arena = nullptr;

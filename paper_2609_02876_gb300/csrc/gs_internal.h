@@ -9,6 +9,9 @@ namespace gs {
 
 constexpr int MAX_SAVE_HOST = 256;
 constexpr int KMAX_HOST = 32;  // largest checkpoint interval accepted by the ABI
+// Largest stored-stage segment in doubles: the record kernel stages one segment
+// per lane in shared memory (128 lanes).
+constexpr int MAX_STAGE_SEGW = 72;
 
 // Arguments of the record (forward) kernels. Passed by value.
 struct FwdArgs {
@@ -35,9 +38,10 @@ struct FwdArgs {
   int* any_failed;                // set when a trajectory ends with a non-OK status
   int k;                          // accepted steps per segment
   int segw;                       // doubles per segment
-  // Stored stages (Tsit5, k = 1): each segment also holds the stage inputs
-  // Y_1..Y_5 of its step after h, and side_stg [n_save][6][d][n] receives
-  // Y_1..Y_6 of every save-time side step (Y_6 = the save state).
+  // Stored stages (k = 1, FP64): each segment also holds its step's stage
+  // data after h (Tsit5: Y_1..Y_5; Rodas5P: Y_1..Y_7, U_0..U_7, the LU of W,
+  // pivot reciprocals and pivots), and side_stg [n_save][payload][n] receives
+  // the same for every save-time side step plus its save state.
   int stages;
   double* side_stg;
   double save_t[MAX_SAVE_HOST];

@@ -113,37 +113,77 @@ struct Tsit5Method {
     }
     return true;
   }
-  // The trial step that also returns its stage inputs Y_0..Y_6 (Y_6 = y_new).
+  // ---- stored stages (records that keep every step's stage inputs)
+  // A step stores Y_1..Y_5 (Y_0 is the segment's state); a side step also Y_6,
+  // its save state.
   template <class Pb, class R>
-  __device__ __forceinline__ static bool trial_y(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+  struct StageData {
+    R Y[7][Pb::D];
+  };
+  template <int D>
+  static constexpr int step_payload() {
+    return 5 * D;
+  }
+  template <int D>
+  static constexpr int side_payload() {
+    return 6 * D;
+  }
+  // The trial step that also returns its stage data.
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial_s(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
                                                  const Carry<Pb, R>& cy, R (&ynew)[Pb::D], R (&e)[Pb::D],
-                                                 Carry<Pb, R>& next, R (&Y)[7][Pb::D]) {
+                                                 Carry<Pb, R>& next, StageData<Pb, R>& sd) {
     constexpr int D = Pb::D;
     R K[7][D];
 #pragma unroll
     for (int c = 0; c < D; ++c) K[0][c] = cy.k1[c];
-    tsit5_stages<Pb, R, 7>(y, p, to_r<R>(h), Y, K);
+    tsit5_stages<Pb, R, 7>(y, p, to_r<R>(h), sd.Y, K);
     tsit5_error<Pb, R>(K, to_r<R>(h), e);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      ynew[c] = Y[6][c];
+      ynew[c] = sd.Y[6][c];
       next.k1[c] = K[6][c];
     }
     return true;
   }
-  // Reverse unit over stored stage inputs Y_0..Y_5 (and, for a side unit, the
-  // save state Y_6): no stage is recomputed. Same arithmetic as unit().
+  template <class Pb, class R, class W>
+  __device__ __forceinline__ static void pack(const StageData<Pb, R>& sd, bool side, W&& write) {
+    constexpr int D = Pb::D;
+#pragma unroll
+    for (int j = 1; j < 7; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (j < 6 || side) write((j - 1) * D + c, to_d(sd.Y[j][c]));
+  }
+  template <class Pb, class R, class Rd>
+  __device__ __forceinline__ static void unpack(bool side, const R (&x)[Pb::D], Rd&& read, StageData<Pb, R>& sd) {
+    constexpr int D = Pb::D;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      sd.Y[0][c] = x[c];
+      sd.Y[6][c] = x[c];  // replaced below for a side step; a step unit does not use it
+    }
+#pragma unroll
+    for (int j = 1; j < 7; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (j < 6 || side) sd.Y[j][c] = to_r<R>(read((j - 1) * D + c));
+  }
+  // Reverse unit over stored stage data: no stage is recomputed. Same
+  // arithmetic as unit().
   template <class Pb, class R, bool USER_COT, class Acc>
-  __device__ __forceinline__ static void unit_stored(const RevArgs& a, long long k, int mode, bool active, int us,
-                                                     const R (&Y)[7][Pb::D], double h, const R (&p)[Pb::NP],
-                                                     R (&lam)[Pb::D], Acc& pacc, double& loss) {
+  __device__ __forceinline__ static bool unit_stored(const RevArgs& a, long long k, int mode, bool active, int us,
+                                                     const R (&x)[Pb::D], double h, const R (&p)[Pb::NP],
+                                                     const StageData<Pb, R>& sd, R (&lam)[Pb::D], Acc& pacc,
+                                                     double& loss) {
     constexpr int D = Pb::D;
     const bool side = (mode == U_SIDE);
     R cv[D], v[D];
-    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, Y[6], lam, cv, loss);
-    tsit5_reverse<Pb, R>(Y, p, to_r<R>(h), cv, v, pacc);
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, sd.Y[6], lam, cv, loss);
+    tsit5_reverse<Pb, R>(sd.Y, p, to_r<R>(h), cv, v, pacc);
 #pragma unroll
     for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
+    return true;
   }
   template <class Pb, class R>
   __device__ __forceinline__ static bool side(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
@@ -197,10 +237,87 @@ struct Tsit5Method {
 
 struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
   static constexpr int ORDER = 5, ERR_ORDER = 4;
-  static constexpr bool kStages = false;
-  static constexpr double IDLE_H = 1.0;  // W = I/(h gamma) - J needs h != 0
+  static constexpr bool kStages = true;
   template <class Pb, class R>
   struct Carry {};
+  // ---- stored stages: a step stores U_0..U_7 and the LU of W (factors, pivot
+  // reciprocals, pivots). The stage inputs Y_i = y + sum_j a_ij U_j and the
+  // new state are rebuilt from them by the same operations as the step.
+  template <class Pb, class R>
+  struct StageData {
+    double Y[8][Pb::D], U[8][Pb::D], LU[Pb::D][Pb::D], rinv[Pb::D], ynew[Pb::D];
+    int piv[Pb::D];
+  };
+  template <int D>
+  static constexpr int step_payload() {
+    return 8 * D + D * D + 2 * D;
+  }
+  template <int D>
+  static constexpr int side_payload() {
+    return step_payload<D>();
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial_s(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                 const Carry<Pb, R>&, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                                 Carry<Pb, R>&, StageData<Pb, R>& sd) {
+    constexpr int D = Pb::D;
+    const bool ok = rodas_step<Pb>(y, p, h, sd.Y, sd.U, sd.LU, sd.piv, sd.rinv, ynew);
+#pragma unroll
+    for (int c = 0; c < D; ++c) e[c] = sd.U[7][c];
+    return ok;
+  }
+  template <class Pb, class R, class W>
+  __device__ __forceinline__ static void pack(const StageData<Pb, R>& sd, bool, W&& write) {
+    constexpr int D = Pb::D;
+    int i = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c) write(i++, sd.U[j][c]);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) write(i++, sd.LU[r][c]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) write(i++, sd.rinv[c]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) write(i++, (double)sd.piv[c]);
+  }
+  template <class Pb, class R, class Rd>
+  __device__ __forceinline__ static void unpack(bool side, const R (&x)[Pb::D], Rd&& read, StageData<Pb, R>& sd) {
+    constexpr int D = Pb::D;
+    int i = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c) sd.U[j][c] = read(i++);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) sd.LU[r][c] = read(i++);
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.rinv[c] = read(i++);
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.piv[c] = (int)read(i++);
+    rodas_stage_inputs<D>(x, sd.U, sd.Y);
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.ynew[c] = side ? add_(sd.Y[7][c], sd.U[7][c]) : x[c];
+  }
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static bool unit_stored(const RevArgs& a, long long k, int mode, bool active, int us,
+                                                     const R (&x)[Pb::D], double h, const R (&p)[Pb::NP],
+                                                     const StageData<Pb, R>& sd, R (&lam)[Pb::D], Acc& pacc,
+                                                     double& loss) {
+    constexpr int D = Pb::D;
+    const bool side = (mode == U_SIDE);
+    double cv[D], v[D];
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, sd.ynew, lam, cv, loss);
+    rodas_reverse<Pb>(x, p, h, sd.Y, sd.U, sd.LU, sd.piv, sd.rinv, cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
+    return true;
+  }
+  static constexpr double IDLE_H = 1.0;  // W = I/(h gamma) - J needs h != 0
   template <class Pb, class R>
   __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>&,
                                                float (&f0)[Pb::D]) {
@@ -328,6 +445,33 @@ struct Ros23Method {
 // ---------------------------------------------------------------------------
 // Record kernel
 // ---------------------------------------------------------------------------
+// The stage data type of a method when a kernel stores or loads stages (an
+// empty placeholder otherwise).
+struct NoStages {};
+template <class M, class Pb, class R, bool STAGES>
+struct StageOf {
+  using type = NoStages;
+};
+template <class M, class Pb, class R>
+struct StageOf<M, Pb, R, true> {
+  using type = typename M::template StageData<Pb, R>;
+};
+// Doubles of a stored-stage segment, [prev, t, y[D], h, step payload],
+// rounded up to a 16-byte multiple.
+template <class M, int D>
+constexpr int stage_segw() {
+  return ((3 + D + M::template step_payload<D>()) + 1) & ~1;
+}
+// A (method, problem, precision) stores stages only in FP64, without shared
+// weights and when its segment fits the record kernel's staging buffer.
+template <class M, class Pb, class R>
+constexpr bool stages_possible() {
+  if constexpr (M::kStages && std::is_same<R, double>::value && !HasWeights<Pb>::value)
+    return stage_segw<M, Pb::D>() <= MAX_STAGE_SEGW;
+  else
+    return false;
+}
+
 // SAVES: save-time side steps run (for y_save, or for the stored side stages);
 // STAGES: the record stores stage inputs (k = 1).
 template <class M, class Pb, class R, bool SAVES, bool STAGES>
@@ -447,23 +591,33 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
     __syncwarp();
     asm volatile("" : "+r"(um));
     R yn[D], e[D];
-    R Ys[7][D];  // stage inputs of this unit (stored-stage records)
+    typename StageOf<M, Pb, R, STAGES>::type sd;  // stage data of this unit (stored-stage records)
     Carry next;
     double q = 2.0;
     bool solved = true;
     if (um != U_NONE) {
-      const bool sd = SAVES && (um == U_SIDE);
+      const bool is_side = SAVES && (um == U_SIDE);
       R xin[D];
 #pragma unroll
-      for (int c = 0; c < D; ++c) xin[c] = sd ? yp[c] : y[c];
-      const Carry cin = sd ? cyp : cy;
-      const double hx = sd ? s_save[jp] - tp : h;
+      for (int c = 0; c < D; ++c) xin[c] = is_side ? yp[c] : y[c];
+      const Carry cin = is_side ? cyp : cy;
+      const double hx = is_side ? s_save[jp] - tp : h;
       if constexpr (STAGES) {
-        solved = M::template trial_y<Pb, R>(xin, p, hx, cin, yn, e, next, Ys);
+        // the unit's stage data go out at once (a step's to its staging slot,
+        // overwritten by the next trial if this one is rejected), so that they
+        // are not held in registers across the step-size decision
+        solved = M::template trial_s<Pb, R>(xin, p, hx, cin, yn, e, next, sd);
+        if (is_side) {
+          constexpr int SP = M::template side_payload<D>();
+          double* dst = a.side_stg + (long long)jp * SP * n + k;
+          M::template pack<Pb, R>(sd, true, [&](int i, double v) { dst[(long long)i * n] = v; });
+        } else {
+          M::template pack<Pb, R>(sd, false, [&](int i, double v) { stg[(3 + D + i) * TB] = v; });
+        }
       } else {
         solved = M::template trial<Pb, R>(xin, p, hx, cin, yn, e, next);
       }
-      if (!sd) {
+      if (!is_side) {
         ++natt;
         q = err_meansq<D>(e, y, yn, a.rtol, a.atol, rtf, atf);
       }
@@ -472,12 +626,6 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       if (a.y_save) {
 #pragma unroll
         for (int c = 0; c < D; ++c) a.y_save[((long long)jp * D + c) * n + k] = solved ? (double)yn[c] : nan_d();
-      }
-      if constexpr (STAGES) {  // Y_1..Y_6 of the side step
-#pragma unroll
-        for (int j = 1; j < 7; ++j)
-#pragma unroll
-          for (int c = 0; c < D; ++c) a.side_stg[(((long long)jp * 6 + (j - 1)) * D + c) * n + k] = to_d(Ys[j][c]);
       }
       ++jp;
     }
@@ -504,13 +652,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           ++js;
         }
       }
-      if (a.k > 0) stg[(2 + D + slot) * TB] = h;
-      if constexpr (STAGES) {  // k = 1: the step's stage inputs Y_1..Y_5 follow h
-#pragma unroll
-        for (int j = 1; j < 6; ++j)
-#pragma unroll
-          for (int c = 0; c < D; ++c) stg[(3 + D + (j - 1) * D + c) * TB] = to_d(Ys[j][c]);
-      }
+      if (a.k > 0) stg[(2 + D + slot) * TB] = h;  // (stored stages, k = 1: the step's data follow h)
       ++slot;
       t = tn;
 #pragma unroll
@@ -823,13 +965,9 @@ __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
 // state S (y(t1)); then for i = S..1: load segment i, step VJP, the saves
 // attached to state i-1.
 // ---------------------------------------------------------------------------
-// STAGES: the record holds every step's stage inputs after h (segments of
-// stage_segw<D>() doubles) and side_stg the side steps' Y_1..Y_6: the units
-// load them instead of recomputing the stages.
-template <int D>
-constexpr int stage_segw() {
-  return ((3 + 6 * D) + 1) & ~1;
-}
+// STAGES: the record holds every step's stage data after h (segments of
+// stage_segw<M, D>() doubles) and side_stg the side steps' ([save][payload][n]):
+// the units load them instead of recomputing the stages.
 template <class M, class Pb, class R, bool USER_COT, bool STAGES = false>
 __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
   constexpr int D = Pb::D, NP = Pb::NP;
@@ -900,18 +1038,15 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
 
     int mode = U_NONE, us = 0;
     double uh = 0.0;
-    R Yst[7][D];  // stored stage inputs of this unit (STAGES)
+    typename StageOf<M, Pb, R, STAGES>::type sd;  // stored stage data of this unit (STAGES)
     if (k >= 0) {
       if (next_save<D, R, USER_COT>(a, s_save, k, js, tx, yx, lam, loss, us)) {
         mode = U_SIDE;
         uh = s_save[us] - tx;
         if constexpr (STAGES) {
-#pragma unroll
-          for (int c = 0; c < D; ++c) Yst[0][c] = yx[c];
-#pragma unroll
-          for (int j = 1; j < 7; ++j)
-#pragma unroll
-            for (int c = 0; c < D; ++c) Yst[j][c] = to_r<R>(a.side_stg[(((long long)us * 6 + (j - 1)) * D + c) * a.n + k]);
+          constexpr int SP = M::template side_payload<D>();
+          const double* src = a.side_stg + (long long)us * SP * a.n + k;
+          M::template unpack<Pb, R>(true, yx, [&](int i) { return src[(long long)i * a.n]; }, sd);
         }
       } else if (seg < 0) {
         mode = (segs_left == 0) ? U_DONE : U_FAIL;
@@ -924,7 +1059,7 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
         seg = __double_as_longlong(w0.x);
         tx = w0.y;
         if constexpr (STAGES) {
-          constexpr int SW = stage_segw<D>();
+          constexpr int SW = stage_segw<M, D>();
           double buf[SW];
 #pragma unroll
           for (int w = 1; w < SW / 2; ++w) {
@@ -933,16 +1068,9 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
             buf[2 * w + 1] = v.y;
           }
 #pragma unroll
-          for (int c = 0; c < D; ++c) {
-            yx[c] = to_r<R>(buf[2 + c]);
-            Yst[0][c] = yx[c];
-            Yst[6][c] = yx[c];  // not used by a step unit
-          }
+          for (int c = 0; c < D; ++c) yx[c] = to_r<R>(buf[2 + c]);
           uh = buf[2 + D];
-#pragma unroll
-          for (int j = 1; j < 6; ++j)
-#pragma unroll
-            for (int c = 0; c < D; ++c) Yst[j][c] = to_r<R>(buf[3 + D + (j - 1) * D + c]);
+          M::template unpack<Pb, R>(false, yx, [&](int i) { return buf[3 + D + i]; }, sd);
         } else {
 #pragma unroll
           for (int c = 0; c < D; ++c) yx[c] = to_r<R>(sp[2 + c]);
@@ -956,7 +1084,8 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
     __syncwarp();
     const bool busy = (mode == U_STEP || mode == U_SIDE);
     if constexpr (STAGES) {
-      if (busy) M::template unit_stored<Pb, R, USER_COT, Acc>(a, k, mode, true, us, Yst, uh, p, lam, pacc, loss);
+      if (busy && !M::template unit_stored<Pb, R, USER_COT, Acc>(a, k, mode, true, us, yx, uh, p, sd, lam, pacc, loss))
+        mode = U_FAIL;
     } else if (COLL || busy) {
       R yn[D], xin[D];
 #pragma unroll
@@ -1079,7 +1208,7 @@ inline cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long 
 template <class M, class Pb, class R>
 inline cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)(((a.n_save + 1) & ~1) + a.segw * TPB_FWD) * sizeof(double);
-  if constexpr (M::kStages && std::is_same<R, double>::value && !HasWeights<Pb>::value) {
+  if constexpr (stages_possible<M, Pb, R>()) {
     if (a.stages) return persistent_launch(record_kernel<M, Pb, R, true, true>, TPB_FWD, smem, a.n, s, &a);
   } else {
     if (a.stages) return cudaErrorInvalidValue;
@@ -1109,9 +1238,9 @@ inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
                                                                       (int)(blocks * (TPB_REV / 32)), a.shared_w_bar);
     return cudaGetLastError();
   } else {
-  if constexpr (M::kStages && std::is_same<R, double>::value) {
+  if constexpr (stages_possible<M, Pb, R>()) {
     if (a.stages) {
-      if (a.k != 1 || a.segw != stage_segw<Pb::D>()) return cudaErrorInvalidValue;
+      if (a.k != 1 || a.segw != stage_segw<M, Pb::D>()) return cudaErrorInvalidValue;
       if (a.y_save_bar)
         return persistent_launch(reverse_k1_kernel<M, Pb, R, true, true>, TPB_REV, smem, a.n, s, &a);
       return persistent_launch(reverse_k1_kernel<M, Pb, R, false, true>, TPB_REV, smem, a.n, s, &a);

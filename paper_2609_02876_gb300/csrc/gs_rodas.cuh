@@ -182,6 +182,26 @@ __device__ __forceinline__ void lu_solve_t(const double (&LU)[D][D], const int (
 
 // One Rodas5P step from y with size h: stage inputs Y[0..7], stage solutions
 // U[0..7], the LU of W, y_new and the error estimate U[7]. false if W is singular.
+// Stage input Y_i = y + sum_{j<i} a_ij U_j, in a fixed order (the step and
+// the stored-stage reverse build it the same way).
+template <int D>
+__device__ __forceinline__ void rodas_stage_input(int i, const double (&y)[D], const double (&U)[8][D],
+                                                  double (&Yi)[D]) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    double s = y[c];
+#pragma unroll
+    for (int j = 0; j < i; ++j) s = fma_(rodas::a(i, j), U[j][c], s);
+    Yi[c] = s;
+  }
+}
+template <int D>
+__device__ __forceinline__ void rodas_stage_inputs(const double (&y)[D], const double (&U)[8][D],
+                                                   double (&Y)[8][D]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rodas_stage_input<D>(i, y, U, Y[i]);
+}
+
 template <class Pb>
 __device__ __forceinline__ bool rodas_step(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
                                            double (&Y)[8][Pb::D], double (&U)[8][Pb::D], double (&LU)[Pb::D][Pb::D],
@@ -200,13 +220,7 @@ __device__ __forceinline__ bool rodas_step(const double (&y)[Pb::D], const doubl
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     double F[D], Rhs[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      double s = y[c];
-#pragma unroll
-      for (int j = 0; j < i; ++j) s = fma_(rodas::a(i, j), U[j][c], s);
-      Y[i][c] = s;
-    }
+    rodas_stage_input<D>(i, y, U, Y[i]);
     Pb::f(Y[i], p, F);
 #pragma unroll
     for (int c = 0; c < D; ++c) {

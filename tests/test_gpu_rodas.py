@@ -84,13 +84,17 @@ def test_rodas_conserves_invariants_on_gpu(name, idx, total):
     np.testing.assert_allclose(inv, total, rtol=0, atol=1e-13 * max(1.0, total) + 1e-15)
 
 
-def test_rodas_stiff_linear_problem():
-    n = 32
-    rng = np.random.default_rng(6)
+def stiff_linear(n, seed=6):
+    """2x2 linear system with one fast eigenvalue in [-1e4, -1e2]."""
+    rng = np.random.default_rng(seed)
     lam_fast = -10.0 ** rng.uniform(2, 4, n)
     params = np.stack([lam_fast, rng.uniform(0.5, 1.5, n), rng.uniform(0.1, 0.5, n), -rng.uniform(0.5, 1.5, n)], 1)
-    wl = dict(problem="linear", params=params, y0=rng.uniform(-1, 1, (n, 2)), t0=0.0, t1=3.0,
-              save_t=W.uniform_saves(0.0, 3.0, 6), rtol=1e-7, atol=1e-10, w=None)
+    return dict(problem="linear", params=params, y0=rng.uniform(-1, 1, (n, 2)), t0=0.0, t1=3.0,
+                save_t=W.uniform_saves(0.0, 3.0, 6), rtol=1e-7, atol=1e-10, w=None)
+
+
+def test_rodas_stiff_linear_problem():
+    wl = stiff_linear(32)
     rec, ysv, st = record(wl, method="rodas5p")
     assert (st.cpu().numpy() == 0).all()
     g = reverse(rec, wl)
@@ -110,6 +114,28 @@ def test_rodas_solve_grad_equals_record_then_reverse():
     assert (s["status"].cpu().numpy() == 0).all()
     assert_close(s["params_bar"].cpu().numpy().T, g["params_bar"].T, "params_bar", rtol=1e-14)
     assert_close(s["y0_bar"].cpu().numpy().T, g["y0_bar"].T, "y0_bar", rtol=1e-14)
+
+
+@pytest.mark.parametrize("name,n,stages", [("robertson", 1000, 1), ("linear", 333, 1), ("hires", 200, 0)])
+def test_rodas_stored_stage_layout_is_bit_identical(name, n, stages):
+    """gs_solve_grad keeps every Rodas5P step's U_i and LU of W when the segment
+    fits (Robertson, the linear problem; not HIRES, d = 8) and replays the stage
+    inputs from them; its gradients equal the compact record's bit for bit."""
+    wl = stiff_linear(n) if name == "linear" else W.make(name, n)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    info = np.zeros(2, np.int32)
+    s = api.solve_grad(name, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                       record_info=info, method="rodas5p")
+    assert tuple(info) == (1, stages)
+    assert (s["status"].cpu().numpy() == 0).all()
+    rec_info = np.zeros(2, np.int32)
+    rec, _, _ = api.forward_record(name, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                   layout="soa", want_saves=False, record_info=rec_info, method="rodas5p")
+    assert rec_info[1] == 0
+    g = api.reverse(rec, P, Y, layout="soa")
+    np.testing.assert_array_equal(s["loss"].cpu().numpy(), g["loss"].cpu().numpy())
+    np.testing.assert_array_equal(s["params_bar"].cpu().numpy(), g["params_bar"].cpu().numpy())
+    np.testing.assert_array_equal(s["y0_bar"].cpu().numpy(), g["y0_bar"].cpu().numpy())
 
 
 def test_rodas_mesh_agreement_with_oracle_record():
