@@ -58,12 +58,15 @@ STIFF = {"robertson", "hires", "nrob"}
 
 # DRAM bytes per accepted step, read + write, measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch of each kernel) on the first 2^20 trajectories of
-# the same Lorenz FP64 workload (45.15 accepted steps per trajectory), per record
-# layout; a launch's traffic grows in proportion to its accepted steps.
+# the same FP64 workload (Lorenz: 45.15 accepted steps per trajectory; Robertson:
+# 101243901 accepted steps in all), per record layout; a launch's traffic grows in
+# proportion to its accepted steps.
 TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "compact"): (4625075712 + 71750656) / (45.15 * 2 ** 20),
                     ("lorenz", "fp64", "record", "compact"): (66017280 + 2269651712) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "reverse", "stages"): (15093851392 + 89244160) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "record", "stages"): (1560973568 + 11288652032) / (45.15 * 2 ** 20)}
+                    ("lorenz", "fp64", "reverse", "stages"): (15051696640 + 89323264) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "record", "stages"): (1714604544 + 11470852352) / (45.15 * 2 ** 20),
+                    ("robertson", "fp64", "reverse", "stages"): (49914448640 + 67795200) / 101243901,
+                    ("robertson", "fp64", "record", "stages"): (3282266112 + 66818809344) / 101243901}
 
 
 def unit_flops(problem, method=None):
