@@ -21,7 +21,7 @@ _SRC = os.path.join(_HERE, "gs_oracle.cpp")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 
 PROBLEMS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5, "nrob": 6}
-METHOD_AUTO, METHOD_TSIT5, METHOD_RODAS5P, METHOD_ROSENBROCK23 = 0, 1, 2, 3
+METHOD_AUTO, METHOD_TSIT5, METHOD_RODAS5P, METHOD_ROSENBROCK23, METHOD_VERNER7 = 0, 1, 2, 3, 4
 TRAJ_OK, TRAJ_MAXSTEPS, TRAJ_DT_UNDERFLOW, TRAJ_NONFINITE, TRAJ_SINGULAR = 0, 1, 2, 3, 4
 
 
@@ -89,10 +89,11 @@ def problem_info(problem):
 
 
 def tableau(method: int):
-    if method == METHOD_TSIT5:
-        A, b, bh, c = np.zeros(49), np.zeros(7), np.zeros(7), np.zeros(7)
+    if method in (METHOD_TSIT5, METHOD_VERNER7):
+        s = 7 if method == METHOD_TSIT5 else 10
+        A, b, bh, c = np.zeros(s * s), np.zeros(s), np.zeros(s), np.zeros(s)
         lib().or_tableau(method, _p(A), _p(b), _p(bh), _p(c))
-        return {"A": A.reshape(7, 7), "b": b, "bhat": bh, "c": c}
+        return {"A": A.reshape(s, s), "b": b, "bhat": bh, "c": c}
     a, m, Cm, g = np.zeros(64), np.zeros(8), np.zeros(64), np.zeros(1)
     lib().or_tableau(method, _p(a), _p(m), _p(Cm), _p(g))
     return {"a": a.reshape(8, 8), "C": Cm.reshape(8, 8), "m": m, "gamma": float(g[0])}

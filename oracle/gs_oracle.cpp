@@ -4,7 +4,9 @@
 // TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or load
 // this file; only the tests, the smoke check and the CPU-baseline leg of the
 // benchmark use it. It shares no code, header, table or constant with the CUDA
-// library: every coefficient below is typed here from the method's publication.
+// library: every coefficient below is typed here from the method's publication
+// (Verner7's, which the paper does not print, from the construction stated
+// beside its table).
 //
 // What it computes (paper, Sec. 3.1 "The construction", Eq. (replay)):
 //   record  R:  an adaptive solve that keeps the accepted step sizes {h_i};
@@ -25,10 +27,11 @@
 // Parity unpinned (no value outside this file fixes them; they only shape the
 // mesh, which the gradient treats as data): the step-size controller constants
 // (safety 0.9, clamp [0.2, 10], exponent 1/(q+1) with q = 4 for Tsit5 and
-// Rodas5P and q = 2 for Rosenbrock23), the starting-step algorithm's order
-// argument, the end-of-span sliver 1e-12 and the quartered step after a
-// singular linear system; and Rodas5P's coefficients beyond what its order
-// conditions and stiff accuracy fix.
+// Rodas5P, q = 2 for Rosenbrock23 and q = 6 for Verner7), the starting-step
+// algorithm's order argument, the end-of-span sliver 1e-12 and the quartered
+// step after a singular linear system; Rodas5P's coefficients beyond what its
+// order conditions and stiff accuracy fix; and Verner7's free parameters
+// beyond its order conditions (the paper prints no table for it).
 
 #include <algorithm>
 #include <cmath>
@@ -446,7 +449,49 @@ struct RodasTab {
 };
 const RodasTab& rodas() { static RodasTab t; return t; }
 
-enum { M_TSIT5 = 1, M_RODAS5P = 2, M_ROS23 = 3 };
+// Verner7: the seventh-order explicit pair with a sixth-order embedded
+// formula (paper Sec. 5, higher-order engines). Its coefficients are not printed
+// in the paper; this table is a 10-stage 7(6) pair of Verner's structure built
+// from the order conditions: c_2 = 1/200, c_3 = 49/450, c_4 = 49/300, the
+// stage-order conditions sum_j a_ij c_j^(k-1) = c_i^k / k (k <= 3) from stage 4
+// on with a_i2 = 0 there, b_2 = b_3 = 0; the 7th-order formula uses stages 1..9
+// (c_9 = 1); stage 10 enters only the 6th-order formula (bhat_10 = 1/20); the
+// remaining free parameters minimise the 8th-order error coefficients with
+// |a_ij| < 10. Zero-based indices below.
+struct Vern7Tab {
+  double c[10], A[10][10], b[10], bhat[10];
+  Vern7Tab() {
+    std::memset(this, 0, sizeof(*this));
+    c[1] = 0.005; c[2] = 0.10888888888888888; c[3] = 0.16333333333333333; c[4] = 0.4412412362945031;
+    c[5] = 0.5125358668205884; c[6] = 0.8153902148736141; c[7] = 0.8320269620357567; c[8] = 1.0;
+    c[9] = 0.6933543729566465;
+    A[1][0] = 0.005;
+    A[2][0] = -1.07679012345679; A[2][1] = 1.1856790123456789;
+    A[3][0] = 0.04083333333333333; A[3][2] = 0.1225;
+    A[4][0] = 0.5613218080778262; A[4][2] = -2.148246263778861; A[4][3] = 2.0281656919955378;
+    A[5][0] = -0.2543252074630068; A[5][2] = 1.1460969356524386; A[5][3] = -0.6256885247646464;
+    A[5][4] = 0.24645266339580296;
+    A[6][0] = -0.39131654768852675; A[6][2] = 1.0869726640940662; A[6][3] = -0.09561592609715297;
+    A[6][4] = -1.6735343341907647; A[6][5] = 1.8888843587559923;
+    A[7][0] = 0.7511017644073372; A[7][2] = -1.7821652979246974; A[7][3] = 0.9581342511515946;
+    A[7][4] = 2.108363229780166; A[7][5] = -1.4351672874423511; A[7][6] = 0.23176030206370712;
+    A[8][0] = -0.06432542550599094; A[8][2] = 0.2780602767716229; A[8][3] = 0.08112820061408241;
+    A[8][4] = 0.5376285679147711; A[8][5] = -0.25166364169525557; A[8][6] = 0.03175435637869014;
+    A[8][7] = 0.38741766552207996;
+    A[9][0] = -3.1187164246988965; A[9][2] = 9.02697407983311; A[9][3] = -4.244000513534974;
+    A[9][4] = -8.655295625316855; A[9][5] = 8.324471440363192; A[9][6] = -2.143779190364296;
+    A[9][7] = 1.5037006066753662;
+    b[0] = 0.04694589982741012; b[3] = 0.25890626416312335; b[4] = 0.12888376947512276;
+    b[5] = 0.23633374752686637; b[6] = 0.15830047862284352; b[7] = 0.11902434451146297;
+    b[8] = 0.051605495873170766;
+    bhat[0] = 0.04776173310604042; bhat[3] = 0.25503657692265447; bhat[4] = 0.17287055313602917;
+    bhat[5] = 0.17283855677828097; bhat[6] = 0.042409513909176653; bhat[7] = 0.20747757027464744;
+    bhat[8] = b[8]; bhat[9] = 0.05;
+  }
+};
+const Vern7Tab& vern7() { static Vern7Tab t; return t; }
+
+enum { M_TSIT5 = 1, M_RODAS5P = 2, M_ROS23 = 3, M_VERN7 = 4 };
 enum { TRAJ_OK = 0, TRAJ_MAXSTEPS = 1, TRAJ_DT_UNDERFLOW = 2, TRAJ_NONFINITE = 3, TRAJ_SINGULAR = 4 };
 
 // ---------------------------------------------------------------- Tsit5 step
@@ -512,6 +557,73 @@ void tsit5_step_vjp(const Prob& pr, const double* y, const double* p, double h, 
   for (int c = 0; c < d; ++c) {
     double s = lam[c];
     for (int j = 0; j < 7; ++j) s += Ybar[j][c];
+    ybar[c] = s;
+  }
+}
+
+// ---------------------------------------------------------------- Verner7 step
+// One explicit step of the 7(6) pair: stage inputs Ys[j] and stages K[j]
+// (j = 0..9), y_new = y + h sum_j b_j k_j over stages 1..9 and the embedded
+// difference e = h sum_j (b_j - bhat_j) k_j, which needs stage 10.
+template <class T>
+void vern7_step(const Prob& pr, const T* y, const T* p, double h, T Ys[10][DMAX], T K[10][DMAX], T* ynew, T* err) {
+  const Vern7Tab& tb = vern7();
+  const int d = pr.d;
+  const int ns = err ? 10 : 9;
+  for (int i = 0; i < ns; ++i) {
+    for (int c = 0; c < d; ++c) {
+      T s = T(0.0);
+      for (int j = 0; j < i; ++j) s = s + tb.A[i][j] * K[j][c];
+      Ys[i][c] = y[c] + h * s;
+    }
+    f_eval(pr, Ys[i], p, K[i]);
+  }
+  for (int c = 0; c < d; ++c) {
+    T s = T(0.0), e = T(0.0);
+    for (int j = 0; j < 9; ++j) s = s + tb.b[j] * K[j][c];
+    ynew[c] = y[c] + h * s;
+    if (err) {
+      for (int j = 0; j < 10; ++j) e = e + (tb.b[j] - tb.bhat[j]) * K[j][c];
+      err[c] = h * e;
+    }
+  }
+}
+
+// Reverse of one Verner7 step, as for Tsit5 over the nine stages that y_new
+// depends on: kbar_j = h (b_j lam + sum_{m>j} a_mj Ybar_m), Ybar_j = J(Y_j)^T kbar_j,
+// pbar += f_theta(Y_j)^T kbar_j, ybar = lam + sum_j Ybar_j.
+void vern7_step_vjp(const Prob& pr, const double* y, const double* p, double h, const double* lam,
+                    double* ybar, double* pbar, double* wbar) {
+  const Vern7Tab& tb = vern7();
+  const int d = pr.d, P = pr.P;
+  double Ys[10][DMAX], K[10][DMAX], yn[DMAX];
+  vern7_step(pr, y, p, h, Ys, K, yn, (double*)nullptr);
+  double Ybar[9][DMAX] = {{0}};
+  for (int j = 8; j >= 0; --j) {
+    double kbar[DMAX];
+    for (int c = 0; c < d; ++c) {
+      double s = tb.b[j] * lam[c];
+      for (int m = j + 1; m < 9; ++m) s += tb.A[m][j] * Ybar[m][c];
+      kbar[c] = h * s;
+    }
+    double J[DMAX][DMAX], Fp[DMAX][PMAX];
+    jac_y(pr, Ys[j], p, J);
+    jac_p(pr, Ys[j], p, Fp);
+    for (int a = 0; a < d; ++a) {
+      double s = 0.0;
+      for (int c = 0; c < d; ++c) s += J[c][a] * kbar[c];
+      Ybar[j][a] = s;
+    }
+    for (int q = 0; q < P; ++q) {
+      double s = 0.0;
+      for (int c = 0; c < d; ++c) s += Fp[c][q] * kbar[c];
+      pbar[q] += s;
+    }
+    if (wbar) w_vjp(pr, Ys[j], kbar, wbar);
+  }
+  for (int c = 0; c < d; ++c) {
+    double s = lam[c];
+    for (int j = 0; j < 9; ++j) s += Ybar[j][c];
     ybar[c] = s;
   }
 }
@@ -773,6 +885,11 @@ bool phi_step(int method, const Prob& pr, const T* y, const T* p, double h, T* y
     int perm[DMAX];
     return ros23_step(pr, y, p, h, ynew, (T*)nullptr, k1, u2, Y1, LU, perm);
   }
+  if (method == M_VERN7) {
+    T Ys[10][DMAX], K[10][DMAX];
+    vern7_step(pr, y, p, h, Ys, K, ynew, (T*)nullptr);
+    return true;
+  }
   T Ys[8][DMAX], U[8][DMAX], LU[DMAX][DMAX];
   int perm[DMAX];
   return rodas_step(pr, y, p, h, Ys, U, ynew, (T*)nullptr, LU, perm);
@@ -781,13 +898,14 @@ bool phi_step_vjp(int method, const Prob& pr, const double* y, const double* p, 
                   double* ybar, double* pbar, double* wbar) {
   if (method == M_TSIT5) { tsit5_step_vjp(pr, y, p, h, lam, ybar, pbar, wbar); return true; }
   if (method == M_ROS23) return ros23_step_vjp(pr, y, p, h, lam, ybar, pbar, wbar);
+  if (method == M_VERN7) { vern7_step_vjp(pr, y, p, h, lam, ybar, pbar, wbar); return true; }
   return rodas_step_vjp(pr, y, p, h, lam, ybar, pbar, wbar);
 }
 // Order of the method's solution (the starting step) and the lower order q of its
 // error estimate (the controller exponent 1/(q+1)): Tsit5 and Rodas5P 5 and 4,
-// Rosenbrock23 2 and 2.
-int method_order(int method) { return method == M_ROS23 ? 2 : 5; }
-int method_err_order(int method) { return method == M_ROS23 ? 2 : 4; }
+// Rosenbrock23 2 and 2, Verner7 7 and 6.
+int method_order(int method) { return method == M_ROS23 ? 2 : (method == M_VERN7 ? 7 : 5); }
+int method_err_order(int method) { return method == M_ROS23 ? 2 : (method == M_VERN7 ? 6 : 4); }
 
 // ---------------------------------------------------------------- record
 // Weighted RMS norm of the paper's Sec. 2.1: sqrt(mean_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2).
@@ -875,6 +993,10 @@ RecordOut record_one(int method, const Prob& pr, const double* y0, const double*
       double k1[DMAX], u2[DMAX], Y1[DMAX], LU[DMAX][DMAX];
       int perm[DMAX];
       ok = ros23_step(pr, y, p, h, yn, e, k1, u2, Y1, LU, perm);
+    } else if (method == M_VERN7) {
+      double Ys[10][DMAX], K[10][DMAX];
+      vern7_step(pr, y, p, h, Ys, K, yn, e);
+      ok = true;
     } else {
       double Ys[8][DMAX], U[8][DMAX], LU[DMAX][DMAX];
       int perm[DMAX];
@@ -1063,12 +1185,23 @@ int or_problem_info(int pid, int* d, int* P, int* stiff, int* n_shared) {
 }
 
 // Coefficients, exported for the order-condition tests.
-// method 1: A[7*7], b[7], bhat[7], c[7]; method 2: a[8*8], C[8*8], m[8], gamma.
+// method 1: A[7*7], b[7], bhat[7], c[7]; method 2: a[8*8], C[8*8], m[8], gamma;
+// method 4: A[10*10], b[10], bhat[10], c[10].
 int or_tableau(int method, double* A, double* b, double* bhat_or_C, double* c_or_gamma) {
   if (method == M_TSIT5) {
     const Tsit5Tab& t = tsit5();
     for (int i = 0; i < 7; ++i) {
       for (int j = 0; j < 7; ++j) A[i * 7 + j] = t.A[i][j];
+      b[i] = t.b[i];
+      bhat_or_C[i] = t.bhat[i];
+      c_or_gamma[i] = t.c[i];
+    }
+    return 0;
+  }
+  if (method == M_VERN7) {
+    const Vern7Tab& t = vern7();
+    for (int i = 0; i < 10; ++i) {
+      for (int j = 0; j < 10; ++j) A[i * 10 + j] = t.A[i][j];
       b[i] = t.b[i];
       bhat_or_C[i] = t.bhat[i];
       c_or_gamma[i] = t.c[i];
@@ -1178,6 +1311,9 @@ int or_step(int pid, int method, int64_t n, const double* params, const double* 
       double k1[DMAX], u2[DMAX], Y1[DMAX], LU[DMAX][DMAX];
       int perm[DMAX];
       if (!ros23_step(pr, yk, pk, h[k], ynew + k * pr.d, err + k * pr.d, k1, u2, Y1, LU, perm)) return 2;
+    } else if (method == M_VERN7) {
+      double Ys[10][DMAX], K[10][DMAX];
+      vern7_step(pr, yk, pk, h[k], Ys, K, ynew + k * pr.d, err + k * pr.d);
     } else {
       double Ys[8][DMAX], U[8][DMAX], LU[DMAX][DMAX];
       int perm[DMAX];

@@ -24,13 +24,15 @@ def _mesh_times(t0, t1, h):
 
 
 def _tsit5_R(tab):
+    """Stability polynomial of an explicit tableau (Tsit5, Verner7)."""
     A, b = tab["A"], tab["b"]
-    beta = [b @ np.linalg.matrix_power(A, q - 1) @ np.ones(7) for q in range(1, 8)]
+    s = A.shape[0]
+    beta = [b @ np.linalg.matrix_power(A, q - 1) @ np.ones(s) for q in range(1, s + 1)]
 
     def R(Z):
         out = np.eye(Z.shape[0], dtype=Z.dtype)
         Zq = np.eye(Z.shape[0], dtype=Z.dtype)
-        for q in range(1, 8):
+        for q in range(1, s + 1):
             Zq = Zq @ Z
             out = out + beta[q - 1] * Zq
         return out
@@ -98,6 +100,8 @@ CASES = [
     (oracle.METHOD_TSIT5, [0.2, 1.5, -1.5, -0.1], 0.15),
     (oracle.METHOD_RODAS5P, [-0.3, 0.8, -0.9, 0.1], 0.07),
     (oracle.METHOD_RODAS5P, [-1000.0, 1.0, 0.5, -1.0], 0.4),
+    (oracle.METHOD_VERNER7, [-0.3, 0.8, -0.9, 0.1], 0.07),
+    (oracle.METHOD_VERNER7, [0.2, 1.5, -1.5, -0.1], 0.3),
 ]
 
 
@@ -116,7 +120,7 @@ def test_replay_and_adjoint_match_closed_form(method, theta, hscale):
     # save times: interior points, one exactly on a mesh point, and t1 itself
     save_t = np.sort(np.concatenate([rng.uniform(t0 + 1e-3, t1 - 1e-3, 6), [ts[9], t1]]))
     tab = oracle.tableau(method)
-    R = _tsit5_R(tab) if method == oracle.METHOD_TSIT5 else _rodas_R(tab)
+    R = _rodas_R(tab) if method == oracle.METHOD_RODAS5P else _tsit5_R(tab)
     L_ref, ysv_ref = closed_form_loss(R, theta, y0, t0, t1, h, save_t)
     gth_ref, gy_ref = complex_step_grad(R, theta, y0, t0, t1, h, save_t)
     off = np.array([0, len(h)])

@@ -72,8 +72,8 @@ def rodas_standard(tab):
 
 
 def test_tree_counts():
-    # 1, 1, 2, 4, 9 rooted trees of orders 1..5 (Butcher).
-    assert [len(_trees(n)) for n in range(1, 6)] == [1, 1, 2, 4, 9]
+    # 1, 1, 2, 4, 9, 20, 48 rooted trees of orders 1..7 (Butcher).
+    assert [len(_trees(n)) for n in range(1, 8)] == [1, 1, 2, 4, 9, 20, 48]
 
 
 def test_tsit5_order_conditions():
@@ -129,6 +129,27 @@ def test_rodas5p_stiffly_accurate():
         assert abs(_rosenbrock_R(alpha, G, b, z)) <= 1.0 + 1e-12
 
 
+def test_verner7_order_conditions():
+    """All 85 trees to order 7 for b, all 37 to order 6 for bhat (to the rounding of
+    the 17-digit table), bhat not of order 7; Verner's structure: explicit, row
+    sums c, c_9 = 1, stages 2 and 3 unweighted and stage 2 used only by stage 3,
+    stage 10 feeding only the embedded formula."""
+    tab = oracle.tableau(oracle.METHOD_VERNER7)
+    A, b, bh, c = tab["A"], tab["b"], tab["bhat"], tab["c"]
+    Z = np.zeros_like(A)
+    r7 = residuals(A, Z, b, 7)
+    r6 = residuals(A, Z, bh, 6)
+    assert len(r7) == 85 and len(r6) == 37
+    assert max(abs(r) for _, r in r7) < 2e-15
+    assert max(abs(r) for _, r in r6) < 2e-15
+    assert max(abs(r) for _, r in residuals(A, Z, bh, 7)) > 1e-5
+    np.testing.assert_allclose(A.sum(1), c, atol=2e-15)
+    assert c[8] == 1.0
+    assert np.allclose(np.tril(A, -1), A)
+    assert b[1] == b[2] == bh[1] == bh[2] == 0.0 and b[9] == 0.0 and bh[9] != 0.0
+    assert (A[3:, 1] == 0.0).all() and (A[:9, 9] == 0.0).all()
+
+
 def test_planted_coefficient_error_is_detected():
     # A perturbation in the 9th digit of one coefficient must break a condition.
     tab = oracle.tableau(oracle.METHOD_TSIT5)
@@ -141,3 +162,7 @@ def test_planted_coefficient_error_is_detected():
     rt["C"][5, 2] *= 1 + 1e-9
     alpha, G, b = rodas_standard(rt)
     assert max(abs(r) for _, r in residuals(alpha, G, b, 5)) > 10 * TOL
+    vt = oracle.tableau(oracle.METHOD_VERNER7)
+    A = vt["A"].copy()
+    A[6, 3] *= 1 + 1e-9
+    assert max(abs(r) for _, r in residuals(A, np.zeros_like(A), vt["b"], 7)) > 1e-12
