@@ -82,6 +82,16 @@ def unit_flops(problem, method=None):
         trial = step + 2 * D * D + 11 * D + norm  # f(y) carried from the last step, f(y_new) added
         rev = 4 * D * D + 2 * v + 8 * D + 2 * c["con"]
         return {"stage_fwd": step, "vjp_unit": step + rev, "trial": trial}
+    if method == "verner7":
+        # Verner7 (10 stages, 37 nonzero a_ij, 30 of them in stages 2..9): the replay
+        # step evaluates 9 slopes, the stage inputs (sum over rows of 2 m + 1 per
+        # component for m coefficients: 68 D) and y_new (7 weights: 15 D). The trial
+        # adds stage 10 (f, 15 D) and the error estimate (7 weights: 14 D). Reverse:
+        # 9 stage VJPs, the a_ij recursions (60 D), kbar and the cotangent sum (34 D).
+        step = 9 * f + 83 * D
+        trial = 10 * f + 112 * D + norm
+        rev = 9 * v + 94 * D
+        return {"stage_fwd": step, "vjp_unit": step + rev, "trial": trial}
     if problem not in STIFF:
         # Tsit5: stage forward (6 slopes + 6 stage inputs) 6 f + 48 D;
         # stage reverse (6 stage VJPs + cotangent recursion) 6 vjp + 54 D
@@ -170,7 +180,8 @@ def dist_env():
 
 def oracle_method(args):
     import oracle
-    return oracle.METHOD_ROSENBROCK23 if args.method == "rosenbrock23" else oracle.METHOD_AUTO
+    return {"rosenbrock23": oracle.METHOD_ROSENBROCK23, "verner7": oracle.METHOD_VERNER7}.get(args.method,
+                                                                                              oracle.METHOD_AUTO)
 
 
 def cpu_baseline(args, budget_s=12.0):
@@ -387,6 +398,8 @@ def forward_mode_measure(args, P, Y, wl, steps=3):
 def method_name(args):
     if args.method == "rosenbrock23":
         return "Rosenbrock23"
+    if args.method == "verner7":
+        return "Verner7"
     return "Rodas5P" if args.problem in STIFF else "Tsit5"
 
 
@@ -419,8 +432,9 @@ def main():
     ap.add_argument("--traj", type=int, default=1 << 24, help="trajectories per GPU")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
-    ap.add_argument("--method", default=None, choices=["rodas5p", "rosenbrock23"],
-                    help="stiff method (default: Rodas5P for the stiff problems, Tsit5 otherwise)")
+    ap.add_argument("--method", default=None, choices=["rodas5p", "rosenbrock23", "verner7"],
+                    help="method (default: Rodas5P for the stiff problems, Tsit5 otherwise; Rosenbrock23 for "
+                         "stiff ones, Verner7 for Lorenz and Van der Pol on request)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1 << 15)
     ap.add_argument("--no-serve", action="store_true")

@@ -77,10 +77,19 @@ enum {
 enum { GS_FP64 = 0, GS_FP32_MIXED = 1 };
 
 /* One-step methods (paper Sec. 3.2): Tsit5 (Tsitouras 2011) for non-stiff
- * problems, Rodas5P (Steinebach 2023) for stiff ones, and the second-order
+ * problems, Rodas5P (Steinebach 2023) for stiff ones, the second-order
  * Rosenbrock23 (Shampine & Reichelt 1997, the ode23s formulas) for stiff
- * ones on request. AUTO picks Tsit5 or Rodas5P by problem. */
-enum { GS_METHOD_AUTO = 0, GS_METHOD_TSIT5 = 1, GS_METHOD_RODAS5P = 2, GS_METHOD_ROSENBROCK23 = 3 };
+ * ones on request, and the seventh-order Verner pair (Sec. 5, higher-order
+ * engines; a 10-stage 7(6) table of Verner's structure, FP64, non-stiff
+ * problems: Lorenz, Van der Pol, the linear test problem) on request. AUTO
+ * picks Tsit5 or Rodas5P by problem. */
+enum {
+  GS_METHOD_AUTO = 0,
+  GS_METHOD_TSIT5 = 1,
+  GS_METHOD_RODAS5P = 2,
+  GS_METHOD_ROSENBROCK23 = 3,
+  GS_METHOD_VERNER7 = 4
+};
 
 typedef struct {
   int precision;        /* GS_FP64 or GS_FP32_MIXED */

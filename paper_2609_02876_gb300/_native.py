@@ -14,7 +14,7 @@ from . import build as _build
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_UNKNOWN_PROBLEM, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TRAJ_FAILED, \
     GS_ERR_TIMEOUT = range(7)
 GS_FP64, GS_FP32_MIXED = 0, 1
-GS_METHOD_AUTO, GS_METHOD_TSIT5, GS_METHOD_RODAS5P, GS_METHOD_ROSENBROCK23 = 0, 1, 2, 3
+GS_METHOD_AUTO, GS_METHOD_TSIT5, GS_METHOD_RODAS5P, GS_METHOD_ROSENBROCK23, GS_METHOD_VERNER7 = 0, 1, 2, 3, 4
 PROBLEMS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5, "nrob": 6}
 TRAJ_STATUS = {0: "ok", 1: "maxsteps", 2: "dt_underflow", 3: "nonfinite", 4: "singular"}
 

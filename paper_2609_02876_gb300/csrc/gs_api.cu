@@ -223,11 +223,13 @@ struct Call {
 cudaError_t launch_forward_m(int method, int problem, int precision, const FwdArgs& a, cudaStream_t s) {
   if (method == GS_METHOD_RODAS5P) return launch_rodas_forward(problem, precision, a, s);
   if (method == GS_METHOD_ROSENBROCK23) return launch_ros23_forward(problem, precision, a, s);
+  if (method == GS_METHOD_VERNER7) return launch_vern7_forward(problem, precision, a, s);
   return launch_tsit5_forward(problem, precision, a, s);
 }
 cudaError_t launch_reverse_m(int method, int problem, int precision, const RevArgs& a, cudaStream_t s) {
   if (method == GS_METHOD_RODAS5P) return launch_rodas_reverse(problem, precision, a, s);
   if (method == GS_METHOD_ROSENBROCK23) return launch_ros23_reverse(problem, precision, a, s);
+  if (method == GS_METHOD_VERNER7) return launch_vern7_reverse(problem, precision, a, s);
   return launch_tsit5_reverse(problem, precision, a, s);
 }
 
@@ -266,7 +268,8 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   if (opt) o = *opt;
   if (o.precision != GS_FP64 && o.precision != GS_FP32_MIXED) return GS_ERR_INVALID_ARG;
   int method = o.method == GS_METHOD_AUTO ? (c->pi.stiff ? GS_METHOD_RODAS5P : GS_METHOD_TSIT5) : o.method;
-  if (method != GS_METHOD_TSIT5 && method != GS_METHOD_RODAS5P && method != GS_METHOD_ROSENBROCK23)
+  if (method != GS_METHOD_TSIT5 && method != GS_METHOD_RODAS5P && method != GS_METHOD_ROSENBROCK23 &&
+      method != GS_METHOD_VERNER7)
     return GS_ERR_INVALID_ARG;
   if (o.ckpt_k < 0 || o.ckpt_k > KMAX_HOST) return GS_ERR_INVALID_ARG;
   if (c->pi.n_shared > 0 && o.ckpt_k > 1) return GS_ERR_INVALID_ARG;  // shared weights: every state stored
@@ -284,6 +287,7 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_RODAS5P && !rodas_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_ROSENBROCK23 && !ros23_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
+  if (method == GS_METHOD_VERNER7 && !vern7_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   return GS_OK;
 }
 
@@ -741,6 +745,8 @@ gs_status gs_record_refresh(gs_record* rec, const double* params, const double* 
           ? launch_rodas_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s)
       : (rec->method == GS_METHOD_ROSENBROCK23)
           ? launch_ros23_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s)
+      : (rec->method == GS_METHOD_VERNER7)
+          ? launch_vern7_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s)
           : launch_tsit5_refresh(rec->problem, rec->precision, a, rec->arena, rec->y_final, y0, s);
   return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

@@ -539,6 +539,173 @@ __device__ __forceinline__ void tsit5_reverse(const R (&Y)[7][Pb::D], const R (&
   }
 }
 
+// ---------------------------------------------------------------------------
+// Verner7: the seventh-order Verner pair (paper Sec. 5, higher-order engines).
+// The paper prints no coefficients; this is a 10-stage 7(6) pair of Verner's
+// structure fixed by its order conditions (c_2 = 1/200, c_3 = 49/450,
+// c_4 = 49/300, stage order 3 from stage 4 on with a_i2 = 0 there,
+// b_2 = b_3 = 0). The 7th-order solution uses stages 1..9; stage 10 feeds only
+// the 6th-order embedded formula. Not FSAL: each step evaluates f(y).
+// ---------------------------------------------------------------------------
+namespace vern7 {
+__host__ __device__ constexpr double A(int i, int j) {
+  // 0-based stage i (1..9), column j < i
+  return (i == 1 && j == 0)   ? 0.005
+         : (i == 2 && j == 0) ? -1.07679012345679
+         : (i == 2 && j == 1) ? 1.1856790123456789
+         : (i == 3 && j == 0) ? 0.04083333333333333
+         : (i == 3 && j == 2) ? 0.1225
+         : (i == 4 && j == 0) ? 0.5613218080778262
+         : (i == 4 && j == 2) ? -2.148246263778861
+         : (i == 4 && j == 3) ? 2.0281656919955378
+         : (i == 5 && j == 0) ? -0.2543252074630068
+         : (i == 5 && j == 2) ? 1.1460969356524386
+         : (i == 5 && j == 3) ? -0.6256885247646464
+         : (i == 5 && j == 4) ? 0.24645266339580296
+         : (i == 6 && j == 0) ? -0.39131654768852675
+         : (i == 6 && j == 2) ? 1.0869726640940662
+         : (i == 6 && j == 3) ? -0.09561592609715297
+         : (i == 6 && j == 4) ? -1.6735343341907647
+         : (i == 6 && j == 5) ? 1.8888843587559923
+         : (i == 7 && j == 0) ? 0.7511017644073372
+         : (i == 7 && j == 2) ? -1.7821652979246974
+         : (i == 7 && j == 3) ? 0.9581342511515946
+         : (i == 7 && j == 4) ? 2.108363229780166
+         : (i == 7 && j == 5) ? -1.4351672874423511
+         : (i == 7 && j == 6) ? 0.23176030206370712
+         : (i == 8 && j == 0) ? -0.06432542550599094
+         : (i == 8 && j == 2) ? 0.2780602767716229
+         : (i == 8 && j == 3) ? 0.08112820061408241
+         : (i == 8 && j == 4) ? 0.5376285679147711
+         : (i == 8 && j == 5) ? -0.25166364169525557
+         : (i == 8 && j == 6) ? 0.03175435637869014
+         : (i == 8 && j == 7) ? 0.38741766552207996
+         : (i == 9 && j == 0) ? -3.1187164246988965
+         : (i == 9 && j == 2) ? 9.02697407983311
+         : (i == 9 && j == 3) ? -4.244000513534974
+         : (i == 9 && j == 4) ? -8.655295625316855
+         : (i == 9 && j == 5) ? 8.324471440363192
+         : (i == 9 && j == 6) ? -2.143779190364296
+         : (i == 9 && j == 7) ? 1.5037006066753662
+                              : 0.0;
+}
+__host__ __device__ constexpr double B(int j) {
+  return j == 0   ? 0.04694589982741012
+         : j == 3 ? 0.25890626416312335
+         : j == 4 ? 0.12888376947512276
+         : j == 5 ? 0.23633374752686637
+         : j == 6 ? 0.15830047862284352
+         : j == 7 ? 0.11902434451146297
+         : j == 8 ? 0.051605495873170766
+                  : 0.0;
+}
+__host__ __device__ constexpr double Bhat(int j) {
+  return j == 0   ? 0.04776173310604042
+         : j == 3 ? 0.25503657692265447
+         : j == 4 ? 0.17287055313602917
+         : j == 5 ? 0.17283855677828097
+         : j == 6 ? 0.042409513909176653
+         : j == 7 ? 0.20747757027464744
+         : j == 8 ? B(8)
+         : j == 9 ? 0.05
+                  : 0.0;
+}
+__host__ __device__ constexpr double Btilde(int j) { return B(j) - Bhat(j); }  // error weights
+}  // namespace vern7
+
+// Stages of one Verner7 step from y with size h: stage inputs Y[0..NS-1]
+// (Y[0] = y) and slopes K[0..NS-1], K[i] = f(Y[i]). NS = 9 gives what y_new
+// needs; NS = 10 adds stage 10 for the error estimate. Zero coefficients are
+// skipped.
+template <class Pb, class R, int NS>
+__device__ __forceinline__ void vern7_stages(const R (&y)[Pb::D], const R (&p)[Pb::NP], R h, R (&Y)[NS][Pb::D],
+                                             R (&K)[NS][Pb::D]) {
+  constexpr int D = Pb::D;
+#pragma unroll
+  for (int c = 0; c < D; ++c) Y[0][c] = y[c];
+  Pb::f(y, p, K[0]);
+#pragma unroll
+  for (int i = 1; i < NS; ++i) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      R s = mul_(R(vern7::A(i, 0)), K[0][c]);
+#pragma unroll
+      for (int j = 1; j < i; ++j)
+        if (vern7::A(i, j) != 0.0) s = fma_(R(vern7::A(i, j)), K[j][c], s);
+      Y[i][c] = fma_(h, s, y[c]);
+    }
+    Pb::f(Y[i], p, K[i]);
+  }
+}
+
+// y_new = y + h sum_{j<9} b_j k_j.
+template <class Pb, class R, int NS>
+__device__ __forceinline__ void vern7_update(const R (&y)[Pb::D], const R (&K)[NS][Pb::D], R h, R (&yn)[Pb::D]) {
+#pragma unroll
+  for (int c = 0; c < Pb::D; ++c) {
+    R s = mul_(R(vern7::B(0)), K[0][c]);
+#pragma unroll
+    for (int j = 1; j < 9; ++j)
+      if (vern7::B(j) != 0.0) s = fma_(R(vern7::B(j)), K[j][c], s);
+    yn[c] = fma_(h, s, y[c]);
+  }
+}
+
+// Embedded error estimate e = h sum_j (b_j - bhat_j) k_j (stage 9's weight is zero).
+template <class Pb, class R>
+__device__ __forceinline__ void vern7_error(const R (&K)[10][Pb::D], R h, R (&e)[Pb::D]) {
+#pragma unroll
+  for (int c = 0; c < Pb::D; ++c) {
+    R s = mul_(R(vern7::Btilde(0)), K[0][c]);
+#pragma unroll
+    for (int j = 1; j < 10; ++j)
+      if (vern7::Btilde(j) != 0.0) s = fma_(R(vern7::Btilde(j)), K[j][c], s);
+    e[c] = mul_(h, s);
+  }
+}
+
+// Reverse of one Verner7 step over its recomputed stage inputs Y[0..8]: given
+// the cotangent c of y_new returns v = dL/dy and accumulates dL/dtheta.
+// kbar_j = h (b_j c + sum_{m>j} a_mj Ybar_m), Ybar_j = J(Y_j)^T kbar_j,
+// theta_bar += f_theta(Y_j)^T kbar_j, v = c + sum_j Ybar_j. acc[l] holds
+// sum over the stages already reversed of a_ml Ybar_m; stage 9 starts it.
+template <class Pb, class R, class RB>
+__device__ __forceinline__ void vern7_reverse(const R (&Y)[9][Pb::D], const R (&p)[Pb::NP], R h, const R (&c)[Pb::D],
+                                              R (&v)[Pb::D], RB& pbacc) {
+  constexpr int D = Pb::D;
+  R acc[8][D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) v[q] = c[q];
+#pragma unroll
+  for (int j = 8; j >= 0; --j) {
+    R kb[D], yb[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      if (j == 8)
+        kb[q] = mul_(h, mul_(R(vern7::B(j)), c[q]));
+      else if (vern7::B(j) == 0.0)
+        kb[q] = mul_(h, acc[j][q]);
+      else
+        kb[q] = mul_(h, fma_(R(vern7::B(j)), c[q], acc[j][q]));
+    }
+    pbacc.template vjp<Pb>(Y[j], p, kb, yb);
+#pragma unroll
+    for (int q = 0; q < D; ++q) v[q] = add_(v[q], yb[q]);
+#pragma unroll
+    for (int l = 0; l < j; ++l) {
+      // column l of row j: the first nonzero entry met (largest j) starts acc[l]
+      if (vern7::A(j, l) == 0.0) continue;
+      bool first = true;
+#pragma unroll
+      for (int m = 8; m > j; --m)
+        if (vern7::A(m, l) != 0.0) first = false;
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        acc[l][q] = first ? mul_(R(vern7::A(j, l)), yb[q]) : fma_(R(vern7::A(j, l)), yb[q], acc[l][q]);
+    }
+  }
+}
+
 // Parameter-gradient accumulators: plain (FP64) and compensated (FP32-mixed,
 // Neumaier's variant of Kahan summation).
 // vjp<Pb>(y, p, v, yb): yb = J(y)^T v and accumulates f_theta(y)^T v.

@@ -134,6 +134,11 @@ cudaError_t launch_ros23_reverse(int problem, int precision, const RevArgs& a, c
 bool ros23_supports(int problem, int precision);
 cudaError_t launch_ros23_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
                                  const double* y0, cudaStream_t s);
+cudaError_t launch_vern7_forward(int problem, int precision, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_vern7_reverse(int problem, int precision, const RevArgs& a, cudaStream_t s);
+bool vern7_supports(int problem, int precision);
+cudaError_t launch_vern7_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,
+                                 const double* y0, cudaStream_t s);
 // Frozen-mesh refresh: re-run each trajectory's state chain over its recorded
 // mesh with a.params and y0, rewriting the record's states and y(t1).
 cudaError_t launch_tsit5_refresh(int problem, int precision, const RevArgs& a, double* arena, double* y_final,

@@ -442,6 +442,66 @@ struct Ros23Method {
   }
 };
 
+struct Verner7Method {  // FP64 only
+  static constexpr int ORDER = 7, ERR_ORDER = 6;
+  static constexpr bool kStages = false;
+  static constexpr double IDLE_H = 0.0;
+  template <class Pb, class R>
+  struct Carry {};  // not FSAL: every step evaluates f(y)
+  template <class Pb, class R>
+  __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>&,
+                                               float (&f0)[Pb::D]) {
+    R f[Pb::D];
+    Pb::f(y, p, f);
+#pragma unroll
+    for (int c = 0; c < Pb::D; ++c) f0[c] = (float)f[c];
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                               const Carry<Pb, R>&, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                               Carry<Pb, R>&) {
+    static_assert(std::is_same<R, double>::value, "Verner7 runs in FP64");
+    constexpr int D = Pb::D;
+    R Y[10][D], K[10][D];
+    vern7_stages<Pb, R, 10>(y, p, h, Y, K);
+    vern7_update<Pb, R, 10>(y, K, h, ynew);
+    vern7_error<Pb, R>(K, h, e);
+    return true;
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool side(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                              const Carry<Pb, R>&, R (&ys)[Pb::D]) {
+    return replay_step<Pb, R>(y, p, h, ys);
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool replay_step(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                     R (&ynew)[Pb::D]) {
+    constexpr int D = Pb::D;
+    R Y[9][D], K[9][D];
+    vern7_stages<Pb, R, 9>(y, p, h, Y, K);
+    vern7_update<Pb, R, 9>(y, K, h, ynew);
+    return true;
+  }
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static bool unit(const RevArgs& a, long long k, int mode, bool active, int us,
+                                              const R (&x)[Pb::D], double h, const R (&p)[Pb::NP], R (&lam)[Pb::D],
+                                              Acc& pacc, double& loss, R (&ynew)[Pb::D]) {
+    static_assert(std::is_same<R, double>::value, "Verner7 runs in FP64");
+    constexpr int D = Pb::D;
+    R Y[9][D], K[9][D];
+    vern7_stages<Pb, R, 9>(x, p, h, Y, K);
+    vern7_update<Pb, R, 9>(x, K, h, ynew);
+    if (mode == U_RECOMP) return true;
+    const bool side = (mode == U_SIDE);
+    R cv[D], v[D];
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
+    vern7_reverse<Pb, R>(Y, p, h, cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
+    return true;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Record kernel
 // ---------------------------------------------------------------------------

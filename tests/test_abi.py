@@ -74,7 +74,9 @@ def _call(lib, **kw):
     (dict(pid=0, opt=dict(method=2)), N.GS_ERR_INVALID_ARG),  # no Rodas5P kernel for Lorenz
     (dict(pid=1, opt=dict(method=3)), N.GS_ERR_INVALID_ARG),  # no Rosenbrock23 kernel for Van der Pol
     (dict(pid=2, opt=dict(method=3, precision=1)), N.GS_ERR_INVALID_ARG),  # Rosenbrock23 runs in FP64
-    (dict(opt=dict(method=4)), N.GS_ERR_INVALID_ARG),
+    (dict(opt=dict(method=5)), N.GS_ERR_INVALID_ARG),
+    (dict(pid=2, opt=dict(method=4)), N.GS_ERR_INVALID_ARG),  # no Verner7 kernel for Robertson
+    (dict(pid=0, opt=dict(method=4, precision=1)), N.GS_ERR_INVALID_ARG),  # Verner7 runs in FP64
     (dict(pid=6), N.GS_ERR_INVALID_ARG),  # the neural Robertson needs shared weights
     (dict(pid=6, w=1, opt=dict(precision=1)), N.GS_ERR_INVALID_ARG),  # stiff: FP64 only
     (dict(pid=6, w=1, opt=dict(method=1)), N.GS_ERR_INVALID_ARG),  # no Tsit5 kernel for it
