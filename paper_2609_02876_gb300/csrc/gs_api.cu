@@ -50,20 +50,33 @@ int step_guess(int pid) {
   }
   return 256;
 }
-// The same for a tolerance rtol: a method of error order q takes ~rtol^(-1/(q+1))
-// steps (q = 4 here for the explicit problems).
-int step_guess(int pid, double rtol) {
-  const double scale = std::pow(1e-6 / (rtol > 0.0 ? rtol : 1e-6), 0.2);
-  const double g = step_guess(pid) * (scale < 1.0 ? 1.0 : scale);
+// The same for a tolerance rtol and a method: a method of error order q takes
+// ~rtol^(-1/(q+1)) steps (q = 4 for Tsit5 and Rodas5P, 6 for Verner7, 2 for
+// Rosenbrock23), Verner7 about 0.65 and Rosenbrock23 about 6 times the steps of
+// Tsit5 / Rodas5P at rtol 1e-6.
+int step_guess(int pid, double rtol, int method) {
+  double base = step_guess(pid), expo = 0.2;
+  if (method == GS_METHOD_VERNER7) {
+    base *= 0.65;
+    expo = 1.0 / 7.0;
+  } else if (method == GS_METHOD_ROSENBROCK23) {
+    base *= 6.0;
+    expo = 1.0 / 3.0;
+  }
+  const double scale = std::pow(1e-6 / (rtol > 0.0 ? rtol : 1e-6), expo);
+  const double g = base * (scale < 1.0 ? 1.0 : scale);
   return (int)std::ceil(g);
 }
 
 // Stored-stage records (k = 1): the doubles a step and a side step store (the
 // kernels' StageData payloads), and the segment [prev, t, y[d], h, step payload]
 // rounded up to a 16-byte multiple. Tsit5: Y_1..Y_5 (a side step also Y_6);
-// Rodas5P: U_0..U_7, the LU factors, pivot reciprocals and pivots (the stage
-// inputs and the save state are rebuilt from them).
-int stage_step_payload(int method, int d) { return method == GS_METHOD_RODAS5P ? 10 * d + d * d : 5 * d; }
+// Verner7: Y_1..Y_8 (a side step also its save state); Rodas5P: U_0..U_7, the
+// LU factors, pivot reciprocals and pivots (the stage inputs and the save state
+// are rebuilt from them).
+int stage_step_payload(int method, int d) {
+  return method == GS_METHOD_RODAS5P ? 10 * d + d * d : (method == GS_METHOD_VERNER7 ? 8 * d : 5 * d);
+}
 int stage_side_payload(int method, int d) {
   return stage_step_payload(method, d) + (method == GS_METHOD_RODAS5P ? 0 : d);
 }
@@ -373,11 +386,12 @@ int auto_ckpt_k(const gs_record* r, int problem, int d, int64_t n) {
 }
 
 // Stored stages when the caller allows them (gs_solve_grad), the method and
-// precision support them (Tsit5, FP64, no shared weights), k is automatic, and
+// precision support them (Tsit5, Rodas5P or Verner7, FP64, no shared weights, a
+// segment within MAX_STAGE_SEGW doubles), k is automatic, and
 // the expected record with its side-step stages takes at most 70% of the free
 // device memory (plus what this workspace already holds).
 bool choose_stages(const gs_record* r, const Call& c, int64_t n, int n_save, double rtol) {
-  if (c.method != GS_METHOD_TSIT5 && c.method != GS_METHOD_RODAS5P) return false;
+  if (c.method != GS_METHOD_TSIT5 && c.method != GS_METHOD_RODAS5P && c.method != GS_METHOD_VERNER7) return false;
   if (c.precision != GS_FP64 || c.pi.n_shared > 0 || c.k > 1) return false;
   if (stage_segw_of(c.method, c.pi.d) > MAX_STAGE_SEGW) return false;
   size_t free_b = 0, total_b = 0;
@@ -385,7 +399,7 @@ bool choose_stages(const gs_record* r, const Call& c, int64_t n, int n_save, dou
   const double held = (double)r->arena_cap * r->segw * sizeof(double) + (double)r->side_cap * sizeof(double);
   const double m = (double)(n > 0 ? n : 1);
   const double want =
-      m * (1.1 * step_guess(c.problem, rtol) + 1.0) * stage_segw_of(c.method, c.pi.d) * sizeof(double) +
+      m * (1.1 * step_guess(c.problem, rtol, c.method) + 1.0) * stage_segw_of(c.method, c.pi.d) * sizeof(double) +
       m * n_save * (double)stage_side_payload(c.method, c.pi.d) * sizeof(double);
   return want <= 0.7 * ((double)free_b + held);
 }
@@ -439,7 +453,7 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
     r->arena_cap = 0;
     r->segw = segw;
   }
-  const long long want = (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol) + r->k - 1) / r->k + 1);
+  const long long want = (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol, c.method) + r->k - 1) / r->k + 1);
   if (r->arena_cap > 0 && r->arena_cap < want / 4) {  // far too small for this ensemble: start over
     cudaFree(r->arena);
     r->arena = nullptr;
@@ -451,7 +465,7 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
       r->stages = 0;
       r->k = c.k > 0 ? c.k : auto_ckpt_k(r, c.problem, c.pi.d, n);
       r->segw = segw_of(r->d, r->k);
-      st = ensure_arena(r, (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol) + r->k - 1) / r->k + 1),
+      st = ensure_arena(r, (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol, c.method) + r->k - 1) / r->k + 1),
                         r->segw);
     }
     if (st != GS_OK) return st;

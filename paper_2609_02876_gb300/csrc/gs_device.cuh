@@ -664,14 +664,15 @@ __device__ __forceinline__ void vern7_error(const R (&K)[10][Pb::D], R h, R (&e)
   }
 }
 
-// Reverse of one Verner7 step over its recomputed stage inputs Y[0..8]: given
+// Reverse of one Verner7 step over its stage inputs Y[0..8]: given
 // the cotangent c of y_new returns v = dL/dy and accumulates dL/dtheta.
 // kbar_j = h (b_j c + sum_{m>j} a_mj Ybar_m), Ybar_j = J(Y_j)^T kbar_j,
 // theta_bar += f_theta(Y_j)^T kbar_j, v = c + sum_j Ybar_j. acc[l] holds
 // sum over the stages already reversed of a_ml Ybar_m; stage 9 starts it.
-template <class Pb, class R, class RB>
-__device__ __forceinline__ void vern7_reverse(const R (&Y)[9][Pb::D], const R (&p)[Pb::NP], R h, const R (&c)[Pb::D],
+template <class Pb, class R, int NY, class RB>
+__device__ __forceinline__ void vern7_reverse(const R (&Y)[NY][Pb::D], const R (&p)[Pb::NP], R h, const R (&c)[Pb::D],
                                               R (&v)[Pb::D], RB& pbacc) {
+  static_assert(NY >= 9, "the reverse reads stage inputs Y[0..8]");
   constexpr int D = Pb::D;
   R acc[8][D];
 #pragma unroll

@@ -444,10 +444,80 @@ struct Ros23Method {
 
 struct Verner7Method {  // FP64 only
   static constexpr int ORDER = 7, ERR_ORDER = 6;
-  static constexpr bool kStages = false;
+  static constexpr bool kStages = true;
   static constexpr double IDLE_H = 0.0;
   template <class Pb, class R>
   struct Carry {};  // not FSAL: every step evaluates f(y)
+  // ---- stored stages: a step stores the stage inputs Y_1..Y_8 (Y_0 is the
+  // segment's state); a side step also its save state.
+  template <class Pb, class R>
+  struct StageData {
+    R Y[10][Pb::D], ynew[Pb::D];
+  };
+  template <int D>
+  static constexpr int step_payload() {
+    return 8 * D;
+  }
+  template <int D>
+  static constexpr int side_payload() {
+    return 9 * D;
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial_s(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                 const Carry<Pb, R>&, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                                 Carry<Pb, R>&, StageData<Pb, R>& sd) {
+    constexpr int D = Pb::D;
+    R K[10][D];
+    vern7_stages<Pb, R, 10>(y, p, h, sd.Y, K);
+    vern7_update<Pb, R, 10>(y, K, h, ynew);
+    vern7_error<Pb, R>(K, h, e);
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.ynew[c] = ynew[c];
+    return true;
+  }
+  template <class Pb, class R, class W>
+  __device__ __forceinline__ static void pack(const StageData<Pb, R>& sd, bool side, W&& write) {
+    constexpr int D = Pb::D;
+#pragma unroll
+    for (int j = 1; j < 9; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c) write((j - 1) * D + c, sd.Y[j][c]);
+    if (side) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) write(8 * D + c, sd.ynew[c]);
+    }
+  }
+  template <class Pb, class R, class Rd>
+  __device__ __forceinline__ static void unpack(bool side, const R (&x)[Pb::D], Rd&& read, StageData<Pb, R>& sd) {
+    constexpr int D = Pb::D;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      sd.Y[0][c] = x[c];
+      sd.ynew[c] = x[c];  // replaced below for a side step; a step unit does not use it
+    }
+#pragma unroll
+    for (int j = 1; j < 9; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c) sd.Y[j][c] = read((j - 1) * D + c);
+    if (side) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) sd.ynew[c] = read(8 * D + c);
+    }
+  }
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static bool unit_stored(const RevArgs& a, long long k, int mode, bool active, int us,
+                                                     const R (&x)[Pb::D], double h, const R (&p)[Pb::NP],
+                                                     const StageData<Pb, R>& sd, R (&lam)[Pb::D], Acc& pacc,
+                                                     double& loss) {
+    constexpr int D = Pb::D;
+    const bool side = (mode == U_SIDE);
+    R cv[D], v[D];
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, sd.ynew, lam, cv, loss);
+    vern7_reverse<Pb, R>(sd.Y, p, h, cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
+    return true;
+  }
   template <class Pb, class R>
   __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>&,
                                                float (&f0)[Pb::D]) {

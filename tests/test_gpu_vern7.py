@@ -100,15 +100,22 @@ def test_vern7_refresh_at_new_parameters():
     assert_close(g1["y0_bar"].cpu().numpy().T, o["y0_bar"], "refreshed y0_bar")
 
 
-def test_vern7_solve_grad_and_forward_only_agree_with_record():
-    wl = W.make("lorenz", 257)
+@pytest.mark.parametrize("name", ["lorenz", "vdp"])
+def test_vern7_solve_grad_and_forward_only_agree_with_record(name):
+    """gs_solve_grad stores the stage inputs (stored-stage layout) and reads
+    them back in the reverse sweep; gs_forward_record keeps the compact record
+    and recomputes them: the gradients agree bit for bit."""
+    wl = W.make(name, 257)
     rec, ysv, st = record(wl, method="verner7", step_counts=True)
     g = reverse(rec, wl)
-    s = api.solve_grad("lorenz", dev(wl["params"].T), dev(wl["y0"].T), wl["t0"], wl["t1"], wl["save_t"],
-                       wl["rtol"], wl["atol"], layout="soa", method="verner7")
+    info = np.zeros(2, np.int32)
+    s = api.solve_grad(name, dev(wl["params"].T), dev(wl["y0"].T), wl["t0"], wl["t1"], wl["save_t"],
+                       wl["rtol"], wl["atol"], layout="soa", method="verner7", record_info=info)
+    assert tuple(info) == (1, 1)
     np.testing.assert_array_equal(s["params_bar"].cpu().numpy(), g["params_bar"])
     np.testing.assert_array_equal(s["y0_bar"].cpu().numpy(), g["y0_bar"])
-    f = api.solve("lorenz", dev(wl["params"].T), dev(wl["y0"].T), wl["t0"], wl["t1"], wl["save_t"], wl["rtol"],
+    np.testing.assert_array_equal(s["loss"].cpu().numpy(), g["loss"])
+    f = api.solve(name, dev(wl["params"].T), dev(wl["y0"].T), wl["t0"], wl["t1"], wl["save_t"], wl["rtol"],
                   wl["atol"], layout="soa", method="verner7", step_counts=True)
     np.testing.assert_array_equal(f["y_save"].cpu().numpy(), ysv.cpu().numpy())
     np.testing.assert_array_equal(f["step_counts"].cpu().numpy(), rec.step_counts.cpu().numpy())
