@@ -192,9 +192,9 @@ gs_status gs_record_refresh(gs_record* rec, const double* params, const double* 
  * may be NULL: a zero tangent). Outputs: loss_dot [n_dir][n] (required),
  * loss_out [n] and y_save_dot [n_dir][n_save][d][n] (either may be NULL).
  * Trajectories whose record is not GS_TRAJ_OK, or whose linear system turns
- * singular, get NaN. Lorenz, Van der Pol and GS_LINEAR (Tsit5), Robertson,
- * HIRES and GS_LINEAR (Rodas5P, Rosenbrock23) records; GS_ERR_INVALID_ARG for
- * others.
+ * singular, get NaN. Lorenz, Van der Pol and GS_LINEAR (Tsit5, Verner7),
+ * Robertson, HIRES and GS_LINEAR (Rodas5P, Rosenbrock23) records;
+ * GS_ERR_INVALID_ARG for others.
  * FP64 whatever the record's precision. The first forward-mode call on a
  * record allocates and fills an index of its segments in forward order (8
  * bytes per segment and per trajectory, then included in gs_record_bytes).

@@ -664,6 +664,57 @@ __device__ __forceinline__ void vern7_error(const R (&K)[10][Pb::D], R h, R (&e)
   }
 }
 
+// Forward mode of one Verner7 step with h held as data: y_new (the arithmetic
+// of vern7_stages + vern7_update over nine stages) and, for each of ND tangent
+// directions (yd, pd), yd_new from the stage tangents
+// Yd_i = yd + h sum_j a_ij Kd_j, Kd_i = J(Y_i) Yd_i + f_theta(Y_i) pd.
+template <class Pb, int ND>
+__device__ __forceinline__ void vern7_tangent(const double (&y)[Pb::D], const double (&yd)[ND][Pb::D],
+                                              const double (&p)[Pb::NP], const double (&pd)[ND][Pb::NP], double h,
+                                              double (&yn)[Pb::D], double (&ydn)[ND][Pb::D]) {
+  constexpr int D = Pb::D;
+  double K[9][D], Kd[9][ND][D];
+  Pb::f(y, p, K[0]);
+#pragma unroll
+  for (int q = 0; q < ND; ++q) Pb::jvp(y, p, yd[q], pd[q], Kd[0][q]);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    double Y[D], Yd[ND][D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double s = mul_(vern7::A(i, 0), K[0][c]);
+#pragma unroll
+      for (int j = 1; j < i; ++j)
+        if (vern7::A(i, j) != 0.0) s = fma_(vern7::A(i, j), K[j][c], s);
+      Y[c] = fma_(h, s, y[c]);
+    }
+#pragma unroll
+    for (int q = 0; q < ND; ++q)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        double s = mul_(vern7::A(i, 0), Kd[0][q][c]);
+#pragma unroll
+        for (int j = 1; j < i; ++j)
+          if (vern7::A(i, j) != 0.0) s = fma_(vern7::A(i, j), Kd[j][q][c], s);
+        Yd[q][c] = fma_(h, s, yd[q][c]);
+      }
+    Pb::f(Y, p, K[i]);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) Pb::jvp(Y, p, Yd[q], pd[q], Kd[i][q]);
+  }
+  vern7_update<Pb, double, 9>(y, K, h, yn);
+#pragma unroll
+  for (int q = 0; q < ND; ++q)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double s = mul_(vern7::B(0), Kd[0][q][c]);
+#pragma unroll
+      for (int j = 1; j < 9; ++j)
+        if (vern7::B(j) != 0.0) s = fma_(vern7::B(j), Kd[j][q][c], s);
+      ydn[q][c] = fma_(h, s, yd[q][c]);
+    }
+}
+
 // Reverse of one Verner7 step over its stage inputs Y[0..8]: given
 // the cotangent c of y_new returns v = dL/dy and accumulates dL/dtheta.
 // kbar_j = h (b_j c + sum_{m>j} a_mj Ybar_m), Ybar_j = J(Y_j)^T kbar_j,

@@ -111,7 +111,8 @@ cudaError_t launch_fwd_index(int64_t n, const long long* head, const int32_t* S,
                              const double* arena, long long arena_cap, int k, int segw, unsigned long long* top,
                              long long* fwd_base, long long* fwd_seg, long long cap, cudaStream_t s);
 
-// Forward-mode replay: method GS_METHOD_TSIT5 (1), GS_METHOD_RODAS5P (2) or GS_METHOD_ROSENBROCK23 (3).
+// Forward-mode replay: method GS_METHOD_TSIT5 (1), GS_METHOD_RODAS5P (2), GS_METHOD_ROSENBROCK23 (3) or
+// GS_METHOD_VERNER7 (4).
 bool jvp_supports(int method, int problem);
 cudaError_t launch_jvp(int method, int problem, const JvpArgs& a, cudaStream_t s);
 

@@ -79,6 +79,16 @@ struct Ros23Tangent {
   }
 };
 
+struct Vern7Tangent {
+  template <class Pb, int ND>
+  __device__ __forceinline__ static bool step(const double (&y)[Pb::D], const double (&yd)[ND][Pb::D],
+                                              const double (&p)[Pb::NP], const double (&pd)[ND][Pb::NP], double h,
+                                              double (&yn)[Pb::D], double (&ydn)[ND][Pb::D]) {
+    vern7_tangent<Pb, ND>(y, yd, p, pd, h, yn, ydn);
+    return true;
+  }
+};
+
 // Outputs of trajectory k: the loss and, per direction, its derivative (into
 // loss_dot, or in basis mode into the gradient row of that input).
 template <int NP, int ND>
@@ -290,7 +300,7 @@ cudaError_t launch_fwd_index(int64_t n, const long long* head, const int32_t* S,
 }
 
 bool jvp_supports(int method, int problem) {
-  if (method == 1) return problem == 0 || problem == 1 || problem == 4;  // Lorenz, Van der Pol, linear
+  if (method == 1 || method == 4) return problem == 0 || problem == 1 || problem == 4;  // Lorenz, VdP, linear
   if (method == 2 || method == 3) return problem == 2 || problem == 3 || problem == 4;  // Robertson, HIRES, linear
   return false;
 }
@@ -313,6 +323,12 @@ cudaError_t launch_jvp(int method, int problem, const JvpArgs& a, cudaStream_t s
       case 2: return jvp_dispatch<Ros23Tangent, Robertson>(a, s);
       case 3: return jvp_dispatch<Ros23Tangent, Hires>(a, s);
       case 4: return jvp_dispatch<Ros23Tangent, Linear2>(a, s);
+    }
+  } else if (method == 4) {
+    switch (problem) {
+      case 0: return jvp_dispatch<Vern7Tangent, Lorenz>(a, s);
+      case 1: return jvp_dispatch<Vern7Tangent, VanDerPol>(a, s);
+      case 4: return jvp_dispatch<Vern7Tangent, Linear2>(a, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -86,6 +86,29 @@ def test_vern7_checkpoint_interval_and_user_cotangent(k):
     assert_close(g["y0_bar"].cpu().numpy().T, o["y0_bar"], "y0_bar")
 
 
+def test_vern7_forward_mode_matches_oracle_and_reverse():
+    """Forward mode over a Verner7 record: the directional derivatives equal the
+    oracle's dual-number replay on the same mesh, and the forward-mode gradient
+    equals the reverse sweep's (both to 1e-11 normwise)."""
+    wl = W.make("lorenz", 400)
+    rec, _, _ = record(wl, method="verner7", want_saves=False)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    rng = np.random.default_rng(21)
+    pd = rng.standard_normal(wl["params"].shape) * wl["params"]
+    yd = rng.standard_normal(wl["y0"].shape)
+    j = api.replay_jvp(rec, P, Y, params_dot=dev(pd.T)[None], y0_dot=dev(yd.T)[None], layout="soa")
+    off, h = rec.export_mesh()
+    o = oracle.replay_jvp("lorenz", wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h, pd, yd,
+                          method=V7)
+    ld = j["loss_dot"].cpu().numpy()[0]
+    scale = np.abs(o["loss_dot"]).max()
+    assert np.abs(ld - o["loss_dot"]).max() <= 1e-11 * scale
+    fw = api.forward_grad(rec, P, Y, layout="soa")
+    rv = api.reverse(rec, P, Y, layout="soa")
+    assert_close(fw["params_bar"].cpu().numpy().T, rv["params_bar"].cpu().numpy().T, "forward vs reverse")
+    assert_close(fw["y0_bar"].cpu().numpy().T, rv["y0_bar"].cpu().numpy().T, "forward vs reverse y0")
+
+
 def test_vern7_refresh_at_new_parameters():
     wl = W.make("lorenz", 300)
     rec, _, _ = record(wl, method="verner7", want_saves=False)
