@@ -227,6 +227,29 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
                         double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status);
 
 /*
+ * gs_solve_grad from HOST memory, end to end: params [P][n] and y0 [d][n] are
+ * read from, and loss_out [n], params_bar [P][n], y0_bar [d][n] and
+ * traj_status [n] written to, HOST arrays (page-locked memory lets the copies
+ * run asynchronously; pageable memory works, slower). loss_out, params_bar and
+ * y0_bar may be NULL (not written); traj_status is required. shared_w and
+ * shared_w_bar stay DEVICE pointers (shared-weight problems).
+ * The ensemble is solved in chunks of `chunk` trajectories (0: 2^21) on the
+ * library's own streams, with the copy of chunk c + 1 to the device and of
+ * chunk c - 1 back to the host overlapping the solve of chunk c. Trajectories
+ * are independent, so every per-trajectory result equals gs_solve_grad's on
+ * the whole ensemble bit for bit. Shared-weight problems run as one chunk
+ * (their weight gradient sums the whole ensemble). opt->step_counts must be
+ * NULL; opt->kernel_ms and opt->record_info describe the last chunk.
+ * Device memory: the gs_solve_grad workspace (sized for one chunk) plus four
+ * chunk staging buffers, kept per device for later calls. Synchronous: returns
+ * when every output is in host memory; GS_ERR_TRAJ_FAILED as gs_solve_grad.
+ */
+gs_status gs_solve_grad_host(int problem_id, int64_t n, const double* params, const double* y0,
+                             const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                             double rtol, double atol, const gs_options* opt, int64_t chunk, double* loss_out,
+                             double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status);
+
+/*
  * Forward-only solve (paper Sec. 2.1, the adaptive solve of map R without a
  * record): the same accepted mesh, save states and statuses as
  * gs_forward_record, bit for bit, but nothing is stored for a reverse sweep.

@@ -60,6 +60,8 @@ def lib():
                                     C.POINTER(GsOptions), vp, vp, vp, vp, vp, vp]
         L.gs_solve.argtypes = [i32, i64, vp, vp, vp, d, d, C.POINTER(C.c_double), i32, d, d,
                                C.POINTER(GsOptions), vp, vp, vp, vp]
+        L.gs_solve_grad_host.argtypes = [i32, i64, vp, vp, vp, d, d, C.POINTER(C.c_double), i32, d, d,
+                                         C.POINTER(GsOptions), i64, vp, vp, vp, vp, vp]
         L.gs_record_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.gs_record_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.gs_record_export_mesh.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
@@ -73,7 +75,7 @@ def lib():
         L.gs_context_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.gs_solve_grad_ctx.argtypes = [vp] + list(L.gs_solve_grad.argtypes)
         for name in ("gs_default_options", "gs_problem_info", "gs_forward_record", "gs_reverse", "gs_solve_grad",
-                     "gs_solve", "gs_replay_jvp", "gs_forward_grad",
+                     "gs_solve", "gs_solve_grad_host", "gs_replay_jvp", "gs_forward_grad",
                      "gs_record_bytes", "gs_record_stats", "gs_record_export_mesh", "gs_record_free",
                      "gs_context_create", "gs_context_destroy", "gs_context_bytes", "gs_solve_grad_ctx"):
             getattr(L, name).restype = C.c_int

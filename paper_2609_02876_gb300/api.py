@@ -373,6 +373,45 @@ def solve_grad(problem, params, y0, t0, t1, save_t, rtol, atol, *, shared_w=None
     return res
 
 
+def solve_grad_host(problem, params, y0, t0, t1, save_t, rtol, atol, *, shared_w=None, chunk=0, check=True,
+                    out=None, **opts):
+    """gs_solve_grad_host: host (CPU) SoA tensors in and out, params [P][n], y0 [d][n]
+    (pin them for overlapped copies); the library pipelines the copies with the
+    solve in chunks. Returns dict(loss, params_bar [P][n], y0_bar [d][n], status) on
+    the host (plus shared_w_bar on the device for shared-weight problems)."""
+    pid = _pid(problem)
+    d, P, _, nw = problem_info(pid)
+    p = torch.as_tensor(params, dtype=torch.float64)
+    y = torch.as_tensor(y0, dtype=torch.float64)
+    if p.is_cuda or y.is_cuda or p.dim() != 2 or y.dim() != 2 or p.shape[0] != P or y.shape[0] != d:
+        raise ValueError(f"params and y0 must be host tensors of shapes ({P}, n) and ({d}, n)")
+    p, y = p.contiguous(), y.contiguous()
+    n = p.shape[1]
+    if y.shape[1] != n:
+        raise ValueError("params and y0 hold different ensemble sizes")
+    st, stp = _save_t(save_t)
+    pin = p.is_pinned()
+    if out is None:
+        out = {"loss": torch.empty(n, dtype=torch.float64, pin_memory=pin),
+               "params_bar": torch.empty((P, n), dtype=torch.float64, pin_memory=pin),
+               "y0_bar": torch.empty((d, n), dtype=torch.float64, pin_memory=pin),
+               "status": torch.empty(n, dtype=torch.int32, pin_memory=pin)}
+    w = _dev(shared_w, "shared_w", torch.float32) if nw else None
+    wb = torch.zeros(nw, dtype=torch.float32, device="cuda") if nw else None
+    o = _opts(**opts)
+    rc = N.lib().gs_solve_grad_host(pid, n, p.data_ptr(), y.data_ptr(), _ptr(w), float(t0), float(t1), stp, st.size,
+                                    float(rtol), float(atol), C.byref(o), int(chunk), out["loss"].data_ptr(),
+                                    out["params_bar"].data_ptr(), out["y0_bar"].data_ptr(), _ptr(wb),
+                                    out["status"].data_ptr())
+    if rc not in (N.GS_OK, N.GS_ERR_TRAJ_FAILED) or (check and rc != N.GS_OK):
+        raise N.GsError(rc, "gs_solve_grad_host")
+    res = dict(out)
+    res["rc"] = rc
+    if nw:
+        res["shared_w_bar"] = wb
+    return res
+
+
 class GsFunction(torch.autograd.Function):
     """y_save = ODE ensemble solve at the save times; backward = the discrete adjoint
     on the recorded mesh (record in forward, replay sweep in backward)."""

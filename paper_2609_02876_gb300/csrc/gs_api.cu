@@ -1,6 +1,7 @@
 // C-ABI of gradsolve-gb300 (declared in include/gs.h): argument checking, the
 // device-resident record, the reusable workspace of gs_solve_grad, and the
 // kernel launches. No exception or abort crosses this boundary.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -618,6 +619,63 @@ gs_record* workspace(int dev) {
   return g_ws[dev];
 }
 
+// gs_solve_grad_host's device staging, one per device (guarded by g_ws_mu):
+// two input and two output chunk slots, a copy stream per direction, a
+// compute stream and the events that order them.
+struct HostPipe {
+  cudaStream_t comp = nullptr, h2d = nullptr, d2h = nullptr;
+  cudaEvent_t in_ready[2] = {nullptr, nullptr}, out_ready[2] = {nullptr, nullptr},
+              out_free[2] = {nullptr, nullptr};
+  double* in[2] = {nullptr, nullptr};   // [P + d][chunk]
+  double* out[2] = {nullptr, nullptr};  // [1 + P + d][chunk] doubles, then [chunk] int32 status
+  size_t in_bytes = 0, out_bytes = 0;
+};
+std::vector<HostPipe*> g_pipe;
+
+gs_status host_pipe(int dev, size_t in_bytes, size_t out_bytes, HostPipe** out) {
+  if ((int)g_pipe.size() <= dev) g_pipe.resize(dev + 1, nullptr);
+  if (!g_pipe[dev]) {
+    HostPipe* hp = new (std::nothrow) HostPipe();
+    if (!hp) return GS_ERR_OOM;
+    if (cudaStreamCreateWithFlags(&hp->comp, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&hp->h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&hp->d2h, cudaStreamNonBlocking) != cudaSuccess)
+      return GS_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&hp->in_ready[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&hp->out_ready[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&hp->out_free[i], cudaEventDisableTiming) != cudaSuccess)
+        return GS_ERR_CUDA;
+    g_pipe[dev] = hp;
+  }
+  HostPipe* hp = g_pipe[dev];
+  if (hp->in_bytes < in_bytes || hp->out_bytes < out_bytes) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(hp->in[i]);
+      cudaFree(hp->out[i]);
+      hp->in[i] = hp->out[i] = nullptr;
+    }
+    hp->in_bytes = hp->out_bytes = 0;
+    for (int i = 0; i < 2; ++i)
+      if (cudaMalloc(&hp->in[i], in_bytes) != cudaSuccess || cudaMalloc(&hp->out[i], out_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_OOM;
+      }
+    hp->in_bytes = in_bytes;
+    hp->out_bytes = out_bytes;
+  }
+  *out = hp;
+  return GS_OK;
+}
+
+// Rows [rows][n] of a host SoA array, trajectories [k0, k0 + nc), to or from a
+// device [rows][nc] block: one strided copy.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, int rows,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+  if (rows <= 0 || width == 0) return cudaSuccess;
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, (size_t)rows, kind, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -781,6 +839,90 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
   if (!r) return GS_ERR_OOM;
   return solve_grad_in(r, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
                        loss_out, params_bar, y0_bar, shared_w_bar, traj_status, true);
+}
+
+gs_status gs_solve_grad_host(int problem_id, int64_t n, const double* params, const double* y0,
+                             const float* shared_w, double t0, double t1, const double* save_t, int n_save,
+                             double rtol, double atol, const gs_options* opt, int64_t chunk, double* loss_out,
+                             double* params_bar, double* y0_bar, float* shared_w_bar, int32_t* traj_status) {
+  Call c;
+  gs_status st = check_common(problem_id, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, opt, &c);
+  if (st != GS_OK) return st;
+  if (chunk < 0 || (opt && opt->step_counts)) return GS_ERR_INVALID_ARG;
+  if (n == 0) return GS_OK;
+  if (!traj_status) return GS_ERR_INVALID_ARG;
+  const int P = c.pi.P, d = c.pi.d;
+  int64_t ch = chunk > 0 ? chunk : ((int64_t)1 << 21);
+  if (c.pi.n_shared > 0 || ch > n) ch = n;  // a shared-weight gradient sums the whole ensemble: one chunk
+  const int64_t nchunks = (n + ch - 1) / ch;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  gs_record* r = workspace(dev);
+  if (!r) return GS_ERR_OOM;
+  HostPipe* hp = nullptr;
+  const size_t in_bytes = (size_t)(P + d) * ch * sizeof(double);
+  const size_t out_bytes = (size_t)(1 + P + d) * ch * sizeof(double) + (size_t)ch * sizeof(int32_t);
+  if ((st = host_pipe(dev, in_bytes, out_bytes, &hp)) != GS_OK) return st;
+  const size_t hp_row = (size_t)n * sizeof(double), hs_row = (size_t)n * sizeof(int32_t);
+
+  auto upload = [&](int64_t ci) -> cudaError_t {
+    const int64_t k0 = ci * ch, nc = std::min(ch, n - k0);
+    const int slot = (int)(ci & 1);
+    double* din = hp->in[slot];
+    const size_t w = (size_t)nc * sizeof(double);
+    cudaError_t e = copy_rows(din, w, params + k0, hp_row, w, P, cudaMemcpyHostToDevice, hp->h2d);
+    if (e == cudaSuccess) e = copy_rows(din + (size_t)P * nc, w, y0 + k0, hp_row, w, d, cudaMemcpyHostToDevice, hp->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(hp->in_ready[slot], hp->h2d);
+    return e;
+  };
+  auto download = [&](int64_t ci) -> cudaError_t {
+    const int64_t k0 = ci * ch, nc = std::min(ch, n - k0);
+    const int slot = (int)(ci & 1);
+    const double* dout = hp->out[slot];
+    const size_t w = (size_t)nc * sizeof(double);
+    cudaError_t e = cudaStreamWaitEvent(hp->d2h, hp->out_ready[slot], 0);
+    if (e == cudaSuccess && loss_out) e = copy_rows(loss_out + k0, hp_row, dout, w, w, 1, cudaMemcpyDeviceToHost, hp->d2h);
+    if (e == cudaSuccess && params_bar)
+      e = copy_rows(params_bar + k0, hp_row, dout + nc, w, w, P, cudaMemcpyDeviceToHost, hp->d2h);
+    if (e == cudaSuccess && y0_bar)
+      e = copy_rows(y0_bar + k0, hp_row, dout + (size_t)(1 + P) * nc, w, w, d, cudaMemcpyDeviceToHost, hp->d2h);
+    if (e == cudaSuccess)
+      e = copy_rows(traj_status + k0, hs_row, dout + (size_t)(1 + P + d) * nc, (size_t)nc * sizeof(int32_t),
+                    (size_t)nc * sizeof(int32_t), 1, cudaMemcpyDeviceToHost, hp->d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(hp->out_free[slot], hp->d2h);
+    return e;
+  };
+
+  gs_status result = GS_OK;
+  cudaError_t e = upload(0);
+  for (int64_t ci = 0; ci < nchunks && e == cudaSuccess; ++ci) {
+    const int64_t nc = std::min(ch, n - ci * ch);
+    const int slot = (int)(ci & 1);
+    // the next chunk's inputs go to the other slot, whose previous solve has returned
+    if (ci + 1 < nchunks && (e = upload(ci + 1)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(hp->comp, hp->in_ready[slot], 0)) != cudaSuccess) break;
+    if (ci >= 2 && (e = cudaStreamWaitEvent(hp->comp, hp->out_free[slot], 0)) != cudaSuccess) break;
+    double* din = hp->in[slot];
+    double* dout = hp->out[slot];
+    const gs_status cs = solve_grad_in(r, c, nc, din, din + (size_t)P * nc, shared_w, t0, t1, save_t, n_save, rtol,
+                                       atol, hp->comp, dout, dout + nc, dout + (size_t)(1 + P) * nc, shared_w_bar,
+                                       reinterpret_cast<int32_t*>(dout + (size_t)(1 + P + d) * nc), true);
+    if (cs == GS_ERR_TRAJ_FAILED) {
+      result = GS_ERR_TRAJ_FAILED;
+    } else if (cs != GS_OK) {
+      result = cs;
+      break;
+    }
+    if ((e = cudaEventRecord(hp->out_ready[slot], hp->comp)) != cudaSuccess) break;
+    if ((e = download(ci)) != cudaSuccess) break;
+  }
+  const cudaError_t e1 = cudaStreamSynchronize(hp->h2d);
+  const cudaError_t e2 = cudaStreamSynchronize(hp->d2h);
+  const cudaError_t e3 = cudaStreamSynchronize(hp->comp);
+  if (result != GS_OK && result != GS_ERR_TRAJ_FAILED) return result;
+  if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return GS_ERR_CUDA;
+  return result;
 }
 
 gs_status gs_solve(int problem_id, int64_t n, const double* params, const double* y0, const float* shared_w,

@@ -124,3 +124,40 @@ def test_forward_only_solve_of_an_empty_ensemble_is_a_no_op(lib):
 def test_forward_mode_entry_points_reject_invalid_arguments(lib):
     assert lib.gs_replay_jvp(None, 1, 1, 1, None, None, None, 1, None, None) == N.GS_ERR_INVALID_ARG
     assert lib.gs_forward_grad(None, 1, 1, None, 1, None, None) == N.GS_ERR_INVALID_ARG
+
+
+def _call_host(lib, **kw):
+    a = dict(pid=0, n=4, params=1, y0=1, w=None, t0=0.0, t1=1.0, save=[0.5, 1.0], rtol=1e-6, atol=1e-8, opt=None,
+             chunk=0, status=1)
+    a.update(kw)
+    st = np.asarray(a["save"], dtype=np.float64)
+    return lib.gs_solve_grad_host(a["pid"], a["n"], a["params"], a["y0"], a["w"], a["t0"], a["t1"],
+                                  st.ctypes.data_as(C.POINTER(C.c_double)), st.size, a["rtol"], a["atol"], a["opt"],
+                                  a["chunk"], None, None, None, None, a["status"])
+
+
+def _opts_with_counts():
+    o = N.GsOptions()
+    lib_ = N.lib()
+    lib_.gs_default_options(C.byref(o))
+    o.step_counts = 1
+    _opts_with_counts.keep = o
+    return C.byref(o)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(pid=42), N.GS_ERR_UNKNOWN_PROBLEM),
+    (dict(n=-1), N.GS_ERR_INVALID_ARG),
+    (dict(params=None), N.GS_ERR_INVALID_ARG),
+    (dict(save=[1.5]), N.GS_ERR_INVALID_ARG),
+    (dict(chunk=-2), N.GS_ERR_INVALID_ARG),
+    (dict(status=None), N.GS_ERR_INVALID_ARG),
+    (dict(pid=6), N.GS_ERR_INVALID_ARG),  # the neural Robertson needs its shared weights
+])
+def test_host_buffer_entry_rejects_invalid_arguments(lib, kw, code):
+    assert _call_host(lib, **kw) == code
+
+
+def test_host_buffer_entry_rejects_device_step_counts_and_empty_is_a_no_op(lib):
+    assert _call_host(lib, opt=_opts_with_counts()) == N.GS_ERR_INVALID_ARG
+    assert _call_host(lib, n=0, params=None, y0=None, status=None) == N.GS_OK
