@@ -916,6 +916,10 @@ struct WeightAcc<LvUde> {
   using type = UdeAcc;
 };
 template <>
+struct WeightAcc<LvUdeWarp> {
+  using type = UdeAcc;
+};
+template <>
 struct WeightAcc<NeuralRobertson> {
   using type = NrAcc;
 };

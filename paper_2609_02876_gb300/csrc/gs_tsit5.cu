@@ -30,7 +30,7 @@ cudaError_t launch_tsit5_reverse(int problem, int precision, const RevArgs& a, c
     case 3: return rev_dispatch<Tsit5Method, VanDerPol, float>(a, s);
     case 8: return rev_dispatch<Tsit5Method, Linear2, double>(a, s);
     case 9: return rev_dispatch<Tsit5Method, Linear2, float>(a, s);
-    case 11: return rev_dispatch<Tsit5Method, LvUde, float>(a, s);
+    case 11: return rev_dispatch<Tsit5Method, LvUdeWarp, float>(a, s);  // warp-collective tensor-core network
   }
   return cudaErrorInvalidValue;
 }

@@ -168,6 +168,176 @@ __device__ __forceinline__ float* ude_stage() {
   return s[threadIdx.x >> 5];
 }
 
+// ---------------------------------------------------------------------------
+// Warp-collective form of the network for the reverse sweep, where every lane
+// of a warp evaluates the network together (lanes without work pass zeros).
+// The 16 x 16 hidden layer, forward (Z2 = H1 W2^T) and backward
+// (GH1 = GZ2 W2), runs on the tensor cores as [32 lanes x 16] x [16 x 16]
+// products (mma.sync m16n8k8, 3xTF32: activations split hi + lo per call, W2
+// split once per CTA into fragment tables); the 2-wide input and output layers
+// and the elementwise work stay per lane. The lanes exchange their vectors
+// through the warp's staging rows (the same rows the weight-gradient MMAs read:
+// after a VJP they already hold gz2, h1, gz1, h2, x, y, go).
+// ---------------------------------------------------------------------------
+struct LvUdeWarp : LvUde {
+  // B fragments of the two hidden-layer products, per lane, pre-split:
+  // [q][kk][nt][lane] = {b0.hi, b0.lo, b1.hi, b1.lo} with q = 0: B[k][n] = W2[n][k]
+  // (forward), q = 1: B[k][n] = W2[k][n] (backward); k = 8 kk + t (+4), n = 8 nt + g.
+  __device__ __forceinline__ static uint4* frags() {
+    __shared__ uint4 f[2 * 2 * 2 * 32];
+    return f;
+  }
+  __device__ static void block_setup(const float* shared_w) {
+    LvUde::block_setup(shared_w);
+    uint4* f = frags();
+    for (int i = threadIdx.x; i < 2 * 2 * 2 * 32; i += blockDim.x) {
+      const int lane = i & 31, nt = (i >> 5) & 1, kk = (i >> 6) & 1, q = i >> 7;
+      const int g = lane >> 2, t = lane & 3, n = 8 * nt + g, k0 = 8 * kk + t, k1 = k0 + 4;
+      const float b0 = q == 0 ? shared_w[UDE_W2 + UDE_H * n + k0] : shared_w[UDE_W2 + UDE_H * k0 + n];
+      const float b1 = q == 0 ? shared_w[UDE_W2 + UDE_H * n + k1] : shared_w[UDE_W2 + UDE_H * k1 + n];
+      const Tf32x2 s0 = split_tf32(b0), s1 = split_tf32(b1);
+      f[i] = make_uint4(s0.hi, s0.lo, s1.hi, s1.lo);
+    }
+  }
+  // c[mt][nt] = rows' [32 x 16] block at column offset `off` times B of product q.
+  __device__ __forceinline__ static void hidden_mma(float (&c)[2][2][4], const float* st, int off, int q) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint4* f = frags() + q * 128;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[mt][nt][e] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint4 bf[2];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) bf[nt] = f[(kk * 2 + nt) * 32 + lane];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const float* r0 = st + (16 * mt + g) * UDE_ROW + off + 8 * kk + t;
+        const float* r1 = r0 + 8 * UDE_ROW;
+        const Tf32x2 a[4] = {split_tf32(r0[0]), split_tf32(r1[0]), split_tf32(r0[4]), split_tf32(r1[4])};
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const Tf32x2 b[2] = {{bf[nt].x, bf[nt].y}, {bf[nt].z, bf[nt].w}};
+          mma_3xtf32(c[mt][nt], a, b);
+        }
+      }
+    }
+  }
+  // Forward pass of all lanes: leaves h1 and h2 in the staging rows and
+  // returns this lane's network output and h2.
+  __device__ __forceinline__ static void forward_warp(float x, float y, float (&h2)[UDE_H], float (&nn)[2]) {
+    float* st = ude_stage();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float* row = st + lane * UDE_ROW;
+    __syncwarp();
+    asm volatile("" ::: "memory");
+    const float* w = weights();
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4) {
+      float h[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        h[u] = tanh_f32(fmaf(w[UDE_W1 + 2 * (j + u) + 1], y, fmaf(w[UDE_W1 + 2 * (j + u)], x, w[UDE_B1 + j + u])));
+      *reinterpret_cast<float4*>(row + 16 + j) = make_float4(h[0], h[1], h[2], h[3]);
+    }
+    __syncwarp();
+    float c[2][2][4];
+    hidden_mma(c, st, 16, 0);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {  // rows g and g + 8 of the tile
+          const int r = 16 * mt + g + 8 * hf, col = 8 * nt + 2 * t;
+          const float v0 = tanh_f32(c[mt][nt][2 * hf] + w[UDE_B2 + col]);
+          const float v1 = tanh_f32(c[mt][nt][2 * hf + 1] + w[UDE_B2 + col + 1]);
+          *reinterpret_cast<float2*>(st + r * UDE_ROW + 48 + col) = make_float2(v0, v1);
+        }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(row + 48 + j);
+      h2[j] = v.x;
+      h2[j + 1] = v.y;
+      h2[j + 2] = v.z;
+      h2[j + 3] = v.w;
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      float s = w[UDE_B3 + o];
+#pragma unroll
+      for (int j = 0; j < UDE_H; ++j) s = fmaf(w[UDE_W3 + UDE_H * o + j], h2[j], s);
+      nn[o] = s;
+    }
+  }
+  __device__ __forceinline__ static void f(const float (&y)[D], const float (&p)[NP], float (&o)[D]) {
+    float h2[UDE_H], nn[2];
+    forward_warp(y[0], y[1], h2, nn);
+    o[0] = fmaf(p[0], y[0], -nn[0]);
+    o[1] = fmaf(-p[1], y[1], nn[1]);
+  }
+  // VJP of all lanes (as LvUde::backprop): yb = J^T v, pb += f_theta^T v, and the
+  // staging rows left holding [gz2 | h1 | gz1 | h2 | x, y, go] for the
+  // weight-gradient MMAs.
+  __device__ __forceinline__ static void backprop_warp(const float (&y)[D], const float (&p)[NP],
+                                                       const float (&v)[D], float (&yb)[D], float (&pb)[NP]) {
+    float* st = ude_stage();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float* row = st + lane * UDE_ROW;
+    float h2[UDE_H], nn[2];
+    forward_warp(y[0], y[1], h2, nn);
+    const float* w = weights();
+    const float go0 = -v[0], go1 = v[1];  // f0 = a x - nn0, f1 = -d y + nn1
+    *reinterpret_cast<float4*>(row + 64) = make_float4(y[0], y[1], go0, go1);
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4) {
+      float z[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float gh = fmaf(w[UDE_W3 + j + u], go0, w[UDE_W3 + UDE_H + j + u] * go1);
+        z[u] = gh * fmaf(-h2[j + u], h2[j + u], 1.0f);
+      }
+      *reinterpret_cast<float4*>(row + j) = make_float4(z[0], z[1], z[2], z[3]);
+    }
+    __syncwarp();
+    float c[2][2][4];
+    hidden_mma(c, st, 0, 1);  // GH1 = GZ2 W2
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int r = 16 * mt + g + 8 * hf, col = 8 * nt + 2 * t;
+          const float2 h1 = *reinterpret_cast<const float2*>(st + r * UDE_ROW + 16 + col);
+          const float z0 = c[mt][nt][2 * hf] * fmaf(-h1.x, h1.x, 1.0f);
+          const float z1 = c[mt][nt][2 * hf + 1] * fmaf(-h1.y, h1.y, 1.0f);
+          *reinterpret_cast<float2*>(st + r * UDE_ROW + 32 + col) = make_float2(z0, z1);
+        }
+    __syncwarp();
+    float gx = 0.0f, gy = 0.0f;
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4) {
+      const float4 z = *reinterpret_cast<const float4*>(row + 32 + j);
+      const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        gx = fmaf(w[UDE_W1 + 2 * (j + u)], zz[u], gx);
+        gy = fmaf(w[UDE_W1 + 2 * (j + u) + 1], zz[u], gy);
+      }
+    }
+    yb[0] = fmaf(p[0], v[0], gx);
+    yb[1] = fmaf(-p[1], v[1], gy);
+    pb[0] = fmaf(y[0], v[0], pb[0]);
+    pb[1] = fmaf(-y[1], v[1], pb[1]);
+  }
+};
+
 // Accumulator of the UDE reverse sweep: the per-trajectory (a, d) gradient
 // (compensated FP32, per lane) and the warp's shared-weight gradient in MMA
 // accumulator fragments:
@@ -195,9 +365,14 @@ struct UdeAcc {
   template <class Pb>
   __device__ __forceinline__ void vjp(const float (&y)[2], const float (&p)[2], const float (&v)[2],
                                       float (&yb)[2]) {
-    LvUde::Factors fa;
     float x[2] = {0.0f, 0.0f};
-    LvUde::backprop(y, p, v, yb, x, fa);
+    if constexpr (std::is_same<Pb, LvUdeWarp>::value) {
+      LvUdeWarp::backprop_warp(y, p, v, yb, x);  // leaves the factor rows staged
+    } else {
+      LvUde::Factors fa;
+      LvUde::backprop(y, p, v, yb, x, fa);
+      stage(fa);
+    }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float t = add_(th.s[q], x[q]);
@@ -205,13 +380,12 @@ struct UdeAcc {
                                                                     : add_(sub_(x[q], t), th.s[q]));
       th.s[q] = t;
     }
-    accumulate(fa);
+    accumulate();
   }
 
-  __device__ __forceinline__ void accumulate(const LvUde::Factors& fa) {
-    float* st = ude_stage();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float* row = st + lane * UDE_ROW;
+  // Writes this lane's factor row from a per-lane VJP.
+  __device__ __forceinline__ void stage(const LvUde::Factors& fa) {
+    float* row = ude_stage() + (threadIdx.x & 31) * UDE_ROW;
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < UDE_H; j += 4) {
@@ -221,6 +395,11 @@ struct UdeAcc {
       *reinterpret_cast<float4*>(row + 48 + j) = make_float4(fa.h2[j], fa.h2[j + 1], fa.h2[j + 2], fa.h2[j + 3]);
     }
     *reinterpret_cast<float4*>(row + 64) = make_float4(fa.x, fa.y, fa.go[0], fa.go[1]);
+  }
+  // The weight-gradient MMAs over the warp's staged factor rows.
+  __device__ __forceinline__ void accumulate() {
+    const float* st = ude_stage();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     __syncwarp();
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks) {  // contraction over lanes, 8 at a time
