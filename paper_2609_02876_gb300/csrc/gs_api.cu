@@ -872,7 +872,8 @@ gs_status gs_solve_grad_host(int problem_id, int64_t n, const double* params, co
     double* din = hp->in[slot];
     const size_t w = (size_t)nc * sizeof(double);
     cudaError_t e = copy_rows(din, w, params + k0, hp_row, w, P, cudaMemcpyHostToDevice, hp->h2d);
-    if (e == cudaSuccess) e = copy_rows(din + (size_t)P * nc, w, y0 + k0, hp_row, w, d, cudaMemcpyHostToDevice, hp->h2d);
+    if (e == cudaSuccess)
+      e = copy_rows(din + (size_t)P * nc, w, y0 + k0, hp_row, w, d, cudaMemcpyHostToDevice, hp->h2d);
     if (e == cudaSuccess) e = cudaEventRecord(hp->in_ready[slot], hp->h2d);
     return e;
   };
@@ -882,7 +883,8 @@ gs_status gs_solve_grad_host(int problem_id, int64_t n, const double* params, co
     const double* dout = hp->out[slot];
     const size_t w = (size_t)nc * sizeof(double);
     cudaError_t e = cudaStreamWaitEvent(hp->d2h, hp->out_ready[slot], 0);
-    if (e == cudaSuccess && loss_out) e = copy_rows(loss_out + k0, hp_row, dout, w, w, 1, cudaMemcpyDeviceToHost, hp->d2h);
+    if (e == cudaSuccess && loss_out)
+      e = copy_rows(loss_out + k0, hp_row, dout, w, w, 1, cudaMemcpyDeviceToHost, hp->d2h);
     if (e == cudaSuccess && params_bar)
       e = copy_rows(params_bar + k0, hp_row, dout + nc, w, w, P, cudaMemcpyDeviceToHost, hp->d2h);
     if (e == cudaSuccess && y0_bar)

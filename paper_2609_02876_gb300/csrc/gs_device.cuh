@@ -81,7 +81,9 @@ __device__ __forceinline__ long long dkey(double x) {
   const long long b = __double_as_longlong(x);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
-__device__ __forceinline__ bool same_time(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+__device__ __forceinline__ bool same_time(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
 constexpr unsigned long long DBITS_ONE = 0x3ff0000000000000ull;  // 1.0
 constexpr unsigned long long DBITS_INF = 0x7ff0000000000000ull;  // +inf
 __device__ __forceinline__ bool le_one(double q) { return dbits(q) <= DBITS_ONE; }      // q >= 0: q <= 1, NaN false
@@ -914,7 +916,8 @@ __device__ __forceinline__ double initial_step_f32(const float (&y0)[Pb::D], con
   }
   d2 = sqrtf(d2 / D) / h0;
   const float dm = fmaxf(d1, d2);
-  const float h1 = (dm <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : ex2_approx(lg2_approx(0.01f / dm) * (1.0f / (ORDER + 1)));
+  const float h1 =
+      (dm <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : ex2_approx(lg2_approx(0.01f / dm) * (1.0f / (ORDER + 1)));
   return (double)fminf(fminf(100.0f * h0, h1), span);
 }
 

@@ -157,10 +157,14 @@ __device__ __forceinline__ void mma_3xtf32(float (&c)[4], const Tf32x2 (&a)[4], 
 }
 
 // Per-warp staging of the lanes' factor vectors for the weight-gradient MMAs.
-// Row per lane, 72 floats (stride 72: the fragment reads of rows t, t+4 and
-// columns g hit 32 distinct banks): [gz2 0..15 | h1 16..31 | gz1 32..47 |
-// h2 48..63 | x 64, y 65, go0 66, go1 67].
+// Row per lane, 72 floats: [gz2 0..15 | h1 16..31 | gz1 32..47 | h2 48..63 |
+// x 64, y 65, go0 66, go1 67], with column c of row r stored at
+// c ^ ude_sw(r) (rows with bit 2 set swap their 4-column groups pairwise). With
+// the stride of 72 the weight-gradient fragment reads (rows t, t + 4, columns
+// g) and the hidden-layer fragment reads (rows g, g + 8, columns t, t + 4)
+// each hit 32 distinct banks, and so do the per-lane 16-byte row accesses.
 constexpr int UDE_ROW = 72;
+__device__ __forceinline__ int ude_sw(int row) { return row & 4; }
 constexpr int UDE_WARPS_PER_CTA = 4;
 
 __device__ __forceinline__ float* ude_stage() {
@@ -216,9 +220,10 @@ struct LvUdeWarp : LvUde {
       for (int nt = 0; nt < 2; ++nt) bf[nt] = f[(kk * 2 + nt) * 32 + lane];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
-        const float* r0 = st + (16 * mt + g) * UDE_ROW + off + 8 * kk + t;
+        const float* r0 = st + (16 * mt + g) * UDE_ROW;
         const float* r1 = r0 + 8 * UDE_ROW;
-        const Tf32x2 a[4] = {split_tf32(r0[0]), split_tf32(r1[0]), split_tf32(r0[4]), split_tf32(r1[4])};
+        const int sw = ude_sw(g), c0 = (off + 8 * kk + t) ^ sw, c1 = (off + 8 * kk + t + 4) ^ sw;
+        const Tf32x2 a[4] = {split_tf32(r0[c0]), split_tf32(r1[c0]), split_tf32(r0[c1]), split_tf32(r1[c1])};
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
           const Tf32x2 b[2] = {{bf[nt].x, bf[nt].y}, {bf[nt].z, bf[nt].w}};
@@ -231,7 +236,7 @@ struct LvUdeWarp : LvUde {
   // returns this lane's network output and h2.
   __device__ __forceinline__ static void forward_warp(float x, float y, float (&h2)[UDE_H], float (&nn)[2]) {
     float* st = ude_stage();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, swl = ude_sw(lane), swg = ude_sw(g);
     float* row = st + lane * UDE_ROW;
     __syncwarp();
     asm volatile("" ::: "memory");
@@ -242,7 +247,7 @@ struct LvUdeWarp : LvUde {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         h[u] = tanh_f32(fmaf(w[UDE_W1 + 2 * (j + u) + 1], y, fmaf(w[UDE_W1 + 2 * (j + u)], x, w[UDE_B1 + j + u])));
-      *reinterpret_cast<float4*>(row + 16 + j) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(row + ((16 + j) ^ swl)) = make_float4(h[0], h[1], h[2], h[3]);
     }
     __syncwarp();
     float c[2][2][4];
@@ -256,12 +261,12 @@ struct LvUdeWarp : LvUde {
           const int r = 16 * mt + g + 8 * hf, col = 8 * nt + 2 * t;
           const float v0 = tanh_f32(c[mt][nt][2 * hf] + w[UDE_B2 + col]);
           const float v1 = tanh_f32(c[mt][nt][2 * hf + 1] + w[UDE_B2 + col + 1]);
-          *reinterpret_cast<float2*>(st + r * UDE_ROW + 48 + col) = make_float2(v0, v1);
+          *reinterpret_cast<float2*>(st + r * UDE_ROW + ((48 + col) ^ swg)) = make_float2(v0, v1);
         }
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < UDE_H; j += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(row + 48 + j);
+      const float4 v = *reinterpret_cast<const float4*>(row + ((48 + j) ^ swl));
       h2[j] = v.x;
       h2[j + 1] = v.y;
       h2[j + 2] = v.z;
@@ -287,13 +292,13 @@ struct LvUdeWarp : LvUde {
   __device__ __forceinline__ static void backprop_warp(const float (&y)[D], const float (&p)[NP],
                                                        const float (&v)[D], float (&yb)[D], float (&pb)[NP]) {
     float* st = ude_stage();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, swl = ude_sw(lane), swg = ude_sw(g);
     float* row = st + lane * UDE_ROW;
     float h2[UDE_H], nn[2];
     forward_warp(y[0], y[1], h2, nn);
     const float* w = weights();
     const float go0 = -v[0], go1 = v[1];  // f0 = a x - nn0, f1 = -d y + nn1
-    *reinterpret_cast<float4*>(row + 64) = make_float4(y[0], y[1], go0, go1);
+    *reinterpret_cast<float4*>(row + (64 ^ swl)) = make_float4(y[0], y[1], go0, go1);
 #pragma unroll
     for (int j = 0; j < UDE_H; j += 4) {
       float z[4];
@@ -302,7 +307,7 @@ struct LvUdeWarp : LvUde {
         const float gh = fmaf(w[UDE_W3 + j + u], go0, w[UDE_W3 + UDE_H + j + u] * go1);
         z[u] = gh * fmaf(-h2[j + u], h2[j + u], 1.0f);
       }
-      *reinterpret_cast<float4*>(row + j) = make_float4(z[0], z[1], z[2], z[3]);
+      *reinterpret_cast<float4*>(row + (j ^ swl)) = make_float4(z[0], z[1], z[2], z[3]);
     }
     __syncwarp();
     float c[2][2][4];
@@ -314,16 +319,16 @@ struct LvUdeWarp : LvUde {
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf) {
           const int r = 16 * mt + g + 8 * hf, col = 8 * nt + 2 * t;
-          const float2 h1 = *reinterpret_cast<const float2*>(st + r * UDE_ROW + 16 + col);
+          const float2 h1 = *reinterpret_cast<const float2*>(st + r * UDE_ROW + ((16 + col) ^ swg));
           const float z0 = c[mt][nt][2 * hf] * fmaf(-h1.x, h1.x, 1.0f);
           const float z1 = c[mt][nt][2 * hf + 1] * fmaf(-h1.y, h1.y, 1.0f);
-          *reinterpret_cast<float2*>(st + r * UDE_ROW + 32 + col) = make_float2(z0, z1);
+          *reinterpret_cast<float2*>(st + r * UDE_ROW + ((32 + col) ^ swg)) = make_float2(z0, z1);
         }
     __syncwarp();
     float gx = 0.0f, gy = 0.0f;
 #pragma unroll
     for (int j = 0; j < UDE_H; j += 4) {
-      const float4 z = *reinterpret_cast<const float4*>(row + 32 + j);
+      const float4 z = *reinterpret_cast<const float4*>(row + ((32 + j) ^ swl));
       const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -385,16 +390,21 @@ struct UdeAcc {
 
   // Writes this lane's factor row from a per-lane VJP.
   __device__ __forceinline__ void stage(const LvUde::Factors& fa) {
-    float* row = ude_stage() + (threadIdx.x & 31) * UDE_ROW;
+    const int lane = threadIdx.x & 31, sw = ude_sw(lane);
+    float* row = ude_stage() + lane * UDE_ROW;
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < UDE_H; j += 4) {
-      *reinterpret_cast<float4*>(row + j) = make_float4(fa.gz2[j], fa.gz2[j + 1], fa.gz2[j + 2], fa.gz2[j + 3]);
-      *reinterpret_cast<float4*>(row + 16 + j) = make_float4(fa.h1[j], fa.h1[j + 1], fa.h1[j + 2], fa.h1[j + 3]);
-      *reinterpret_cast<float4*>(row + 32 + j) = make_float4(fa.gz1[j], fa.gz1[j + 1], fa.gz1[j + 2], fa.gz1[j + 3]);
-      *reinterpret_cast<float4*>(row + 48 + j) = make_float4(fa.h2[j], fa.h2[j + 1], fa.h2[j + 2], fa.h2[j + 3]);
+      *reinterpret_cast<float4*>(row + (j ^ sw)) =
+          make_float4(fa.gz2[j], fa.gz2[j + 1], fa.gz2[j + 2], fa.gz2[j + 3]);
+      *reinterpret_cast<float4*>(row + ((16 + j) ^ sw)) =
+          make_float4(fa.h1[j], fa.h1[j + 1], fa.h1[j + 2], fa.h1[j + 3]);
+      *reinterpret_cast<float4*>(row + ((32 + j) ^ sw)) =
+          make_float4(fa.gz1[j], fa.gz1[j + 1], fa.gz1[j + 2], fa.gz1[j + 3]);
+      *reinterpret_cast<float4*>(row + ((48 + j) ^ sw)) =
+          make_float4(fa.h2[j], fa.h2[j + 1], fa.h2[j + 2], fa.h2[j + 3]);
     }
-    *reinterpret_cast<float4*>(row + 64) = make_float4(fa.x, fa.y, fa.go[0], fa.go[1]);
+    *reinterpret_cast<float4*>(row + (64 ^ sw)) = make_float4(fa.x, fa.y, fa.go[0], fa.go[1]);
   }
   // The weight-gradient MMAs over the warp's staged factor rows.
   __device__ __forceinline__ void accumulate() {
@@ -403,36 +413,37 @@ struct UdeAcc {
     __syncwarp();
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks) {  // contraction over lanes, 8 at a time
-      const float* r0 = st + (ks * 8 + t) * UDE_ROW;
-      const float* r1 = st + (ks * 8 + t + 4) * UDE_ROW;
+      const float* r0 = st + (ks * 8 + t) * UDE_ROW;      // rows with bit 2 clear: columns as stored
+      const float* r1 = st + (ks * 8 + t + 4) * UDE_ROW;  // rows with bit 2 set: column c at c ^ 4
       // GA: A[i][k] = gz2_k[i], B[k][j] = (h1_k, 1, 0...)[j]
       {
-        const Tf32x2 a[4] = {split_tf32(r0[g]), split_tf32(r0[g + 8]), split_tf32(r1[g]), split_tf32(r1[g + 8])};
+        const Tf32x2 a[4] = {split_tf32(r0[g]), split_tf32(r0[g + 8]), split_tf32(r1[g ^ 4]),
+                             split_tf32(r1[(g + 8) ^ 4])};
 #pragma unroll
         for (int nt = 0; nt < 3; ++nt) {
           const int j = nt * 8 + g;
           const float b0 = j < 16 ? r0[16 + j] : (j == 16 ? 1.0f : 0.0f);
-          const float b1 = j < 16 ? r1[16 + j] : (j == 16 ? 1.0f : 0.0f);
+          const float b1 = j < 16 ? r1[(16 + j) ^ 4] : (j == 16 ? 1.0f : 0.0f);
           const Tf32x2 b[2] = {split_tf32(b0), split_tf32(b1)};
           mma_3xtf32(ga[nt], a, b);
         }
       }
       // GB: A[i][k] = gz1_k[i], B[k][j] = (x_k, y_k, 1, 0...)[j]
       {
-        const Tf32x2 a[4] = {split_tf32(r0[32 + g]), split_tf32(r0[40 + g]), split_tf32(r1[32 + g]),
-                             split_tf32(r1[40 + g])};
+        const Tf32x2 a[4] = {split_tf32(r0[32 + g]), split_tf32(r0[40 + g]), split_tf32(r1[(32 + g) ^ 4]),
+                             split_tf32(r1[(40 + g) ^ 4])};
         const float b0 = g < 2 ? r0[64 + g] : (g == 2 ? 1.0f : 0.0f);
-        const float b1 = g < 2 ? r1[64 + g] : (g == 2 ? 1.0f : 0.0f);
+        const float b1 = g < 2 ? r1[(64 + g) ^ 4] : (g == 2 ? 1.0f : 0.0f);
         const Tf32x2 b[2] = {split_tf32(b0), split_tf32(b1)};
         mma_3xtf32(gb, a, b);
       }
       // GC: A[i][k] = (h2_k, 1, 0...)[i] over two row tiles, B[k][o] = go_k[o]
       {
         const float b0 = g < 2 ? r0[66 + g] : 0.0f;
-        const float b1 = g < 2 ? r1[66 + g] : 0.0f;
+        const float b1 = g < 2 ? r1[(66 + g) ^ 4] : 0.0f;
         const Tf32x2 b[2] = {split_tf32(b0), split_tf32(b1)};
-        const Tf32x2 a0[4] = {split_tf32(r0[48 + g]), split_tf32(r0[56 + g]), split_tf32(r1[48 + g]),
-                              split_tf32(r1[56 + g])};
+        const Tf32x2 a0[4] = {split_tf32(r0[48 + g]), split_tf32(r0[56 + g]), split_tf32(r1[(48 + g) ^ 4]),
+                              split_tf32(r1[(56 + g) ^ 4])};
         mma_3xtf32(gc[0], a0, b);
         const float one = (g == 0) ? 1.0f : 0.0f;  // row 16 of GC: the bias db3
         const Tf32x2 a1[4] = {split_tf32(one), split_tf32(0.0f), split_tf32(one), split_tf32(0.0f)};
