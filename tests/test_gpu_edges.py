@@ -25,7 +25,8 @@ def check(wl, method=None, **opts):
     assert (st.cpu().numpy() == 0).all()
     g = api.reverse(rec, P, Y, layout="soa")
     off, h = rec.export_mesh()
-    om = {None: oracle.METHOD_AUTO, "rosenbrock23": oracle.METHOD_ROSENBROCK23}[method]
+    om = {None: oracle.METHOD_AUTO, "rosenbrock23": oracle.METHOD_ROSENBROCK23,
+          "verner7": oracle.METHOD_VERNER7}[method]
     o = oracle.replay_grad(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h,
                            method=om)
     assert_close(ysv.permute(2, 0, 1).cpu().numpy(), o["y_save"], "y_save")
@@ -62,7 +63,8 @@ def test_user_first_step_and_loose_tolerance():
     assert np.all(first <= 1e-3)  # the given step is the first trial (accepted or shrunk)
 
 
-@pytest.mark.parametrize("name,method", [("lorenz", None), ("robertson", None), ("robertson", "rosenbrock23")])
+@pytest.mark.parametrize("name,method", [("lorenz", None), ("robertson", None), ("robertson", "rosenbrock23"),
+                                         ("vdp", "verner7")])
 def test_single_trajectory_through_every_entry_point(name, method):
     wl = W.make(name, 1)
     check(wl, method=method)
@@ -76,6 +78,10 @@ def test_single_trajectory_through_every_entry_point(name, method):
     np.testing.assert_array_equal(f["y_save"].cpu().numpy(), ysv.cpu().numpy())
     fg = api.forward_grad(rec, P, Y, layout="soa")
     assert_close(fg["params_bar"].cpu().numpy().T, s["params_bar"].cpu().numpy().T, "forward vs reverse")
+    hs = api.solve_grad_host(name, torch.from_numpy(np.ascontiguousarray(wl["params"].T)),
+                             torch.from_numpy(np.ascontiguousarray(wl["y0"].T)), wl["t0"], wl["t1"], wl["save_t"],
+                             wl["rtol"], wl["atol"], method=method)
+    np.testing.assert_array_equal(hs["params_bar"].numpy(), s["params_bar"].cpu().numpy())
 
 
 def test_empty_ensembles_are_no_ops():
@@ -85,3 +91,6 @@ def test_empty_ensembles_are_no_ops():
     assert s["params_bar"].shape == (3, 0)
     f = api.solve("lorenz", z, z, 0.0, 1.0, wl["save_t"], 1e-6, 1e-8, layout="soa")
     assert f["y_final"].shape == (3, 0)
+    e = torch.empty((3, 0), dtype=torch.float64)
+    h = api.solve_grad_host("lorenz", e, e, 0.0, 1.0, wl["save_t"], 1e-6, 1e-8)
+    assert h["params_bar"].shape == (3, 0)
