@@ -63,8 +63,8 @@ STIFF = {"robertson", "hires", "nrob"}
 # proportion to its accepted steps.
 TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "compact"): (4625075712 + 71750656) / (45.15 * 2 ** 20),
                     ("lorenz", "fp64", "record", "compact"): (66017280 + 2269651712) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "reverse", "stages"): (15051696640 + 89323264) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "record", "stages"): (1714604544 + 11470852352) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "reverse", "stages"): (15005185536 + 89034752) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "record", "stages"): (1782274816 + 11522356736) / (45.15 * 2 ** 20),
                     ("robertson", "fp64", "reverse", "stages"): (49914448640 + 67795200) / 101243901,
                     ("robertson", "fp64", "record", "stages"): (3282266112 + 66818809344) / 101243901}
 
