@@ -852,21 +852,24 @@ __device__ __forceinline__ double err_meansq(const double (&e)[D], const double 
   }
   return mul_(q, 1.0 / D);
 }
-// FP32-mixed form: the error, y and y_new are FP32 stage values, so each ratio
-// e_c / sc_c is formed in FP32 (scale with an IEEE reciprocal); the squares are
-// summed in FP64 and the mean taken in FP32 (relative error 2^-23, below the
-// 1e-6 the ratios already carry), which keeps the FP64 pipe for the sum alone.
+// FP32-mixed form: the error, y and y_new are FP32 stage values, so the whole
+// norm is formed in FP32: each ratio e_c / sc_c (scale with an IEEE
+// reciprocal), the sum of squares and the mean (relative error ~1e-7, below
+// the 1e-6 the ratios already carry). A ratio beyond 1e18 is clamped there so
+// that the square stays finite (any error that large gives the controller's
+// minimum factor either way); a NaN passes through. No FP64 instruction.
 template <int D>
 __device__ __forceinline__ double err_meansq(const float (&e)[D], const float (&y)[D], const float (&yn)[D],
                                              double, double, float rt, float at) {
-  double q = 0.0;
+  float q = 0.0f;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const float sc = fmaf(rt, fmaxf(fabsf(y[c]), fabsf(yn[c])), at);
-    const double r = to_d(__fmul_rn(e[c], __frcp_rn(sc)));
-    q = fma_(r, r, q);
+    float r = __fmul_rn(e[c], __frcp_rn(sc));
+    r = (fabsf(r) > 1e18f) ? 1e18f : r;
+    q = __fmaf_rn(r, r, q);
   }
-  return to_d(__fmul_rn(to_f(q), 1.0f / D));
+  return to_d(__fmul_rn(q, 1.0f / D));
 }
 
 // Integral-controller factor from the mean-square error q = err^2, for an
