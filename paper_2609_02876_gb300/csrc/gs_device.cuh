@@ -539,6 +539,7 @@ __device__ __forceinline__ void tsit5_reverse(const R (&Y)[7][Pb::D], const R (&
       for (int q = 0; q < D; ++q)
         acc[l][q] = (j == 5) ? mul_(R(tsit5::A(j, l)), yb[q]) : fma_(R(tsit5::A(j, l)), yb[q], acc[l][q]);
   }
+  pbacc.flush();
 }
 
 // ---------------------------------------------------------------------------
@@ -758,11 +759,15 @@ __device__ __forceinline__ void vern7_reverse(const R (&Y)[NY][Pb::D], const R (
         acc[l][q] = first ? mul_(R(vern7::A(j, l)), yb[q]) : fma_(R(vern7::A(j, l)), yb[q], acc[l][q]);
     }
   }
+  pbacc.flush();
 }
 
 // Parameter-gradient accumulators: plain (FP64) and compensated (FP32-mixed,
 // Neumaier's variant of Kahan summation).
-// vjp<Pb>(y, p, v, yb): yb = J(y)^T v and accumulates f_theta(y)^T v.
+// vjp<Pb>(y, p, v, yb): yb = J(y)^T v and accumulates f_theta(y)^T v;
+// flush(): called once at the end of each unit's reverse (the compensated form
+// sums a unit's stage contributions plainly and adds the unit's total to the
+// running sum with compensation).
 template <int NP>
 struct PlainAcc {
   double s[NP];
@@ -782,30 +787,31 @@ struct PlainAcc {
                                                double (&gy)[Pb::D]) {
     Pb::jac_contract(y, p, r, u, gy, s);
   }
+  __device__ __forceinline__ void flush() {}
   __device__ double get(int q) const { return s[q]; }
 };
 template <int NP>
 struct CompensatedAcc {
-  float s[NP], comp[NP];
+  float s[NP], comp[NP], u[NP];  // running sum, its compensation, this unit's partial
   __device__ void zero() {
 #pragma unroll
-    for (int q = 0; q < NP; ++q) s[q] = comp[q] = 0.0f;
+    for (int q = 0; q < NP; ++q) s[q] = comp[q] = u[q] = 0.0f;
   }
   template <class Pb>
   __device__ __forceinline__ void vjp(const float (&y)[Pb::D], const float (&p)[NP], const float (&v)[Pb::D],
                                       float (&yb)[Pb::D]) {
-    float x[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) x[q] = 0.0f;
-    Pb::vjp(y, p, v, yb, x);
+    Pb::vjp(y, p, v, yb, u);
+  }
+  __device__ __forceinline__ void flush() {
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-      const float t = add_(s[q], x[q]);
-      comp[q] = add_(comp[q], (fabsf(s[q]) >= fabsf(x[q])) ? add_(sub_(s[q], t), x[q]) : add_(sub_(x[q], t), s[q]));
+      const float x = u[q], t = add_(s[q], x);
+      comp[q] = add_(comp[q], (fabsf(s[q]) >= fabsf(x)) ? add_(sub_(s[q], t), x) : add_(sub_(x, t), s[q]));
       s[q] = t;
+      u[q] = 0.0f;
     }
   }
-  __device__ double get(int q) const { return (double)s[q] + (double)comp[q]; }
+  __device__ double get(int q) const { return (double)s[q] + (double)comp[q] + (double)u[q]; }
 };
 
 // ---------------------------------------------------------------------------

@@ -238,6 +238,7 @@ struct NrAcc {
     for (int o = 0; o < NR_OWN; ++o) wacc[o] = 0.0;
   }
   __device__ void zero() { th.zero(); }
+  __device__ __forceinline__ void flush() {}
   __device__ double get(int q) const { return th.get(q); }
 
   // (a, b) row offsets of flat weight q.

@@ -379,14 +379,10 @@ struct UdeAcc {
       stage(fa);
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float t = add_(th.s[q], x[q]);
-      th.comp[q] = add_(th.comp[q], (fabsf(th.s[q]) >= fabsf(x[q])) ? add_(sub_(th.s[q], t), x[q])
-                                                                    : add_(sub_(x[q], t), th.s[q]));
-      th.s[q] = t;
-    }
+    for (int q = 0; q < 2; ++q) th.u[q] = add_(th.u[q], x[q]);
     accumulate();
   }
+  __device__ __forceinline__ void flush() { th.flush(); }
 
   // Writes this lane's factor row from a per-lane VJP.
   __device__ __forceinline__ void stage(const LvUde::Factors& fa) {
