@@ -99,6 +99,7 @@ struct gs_record {
   int device = 0;
   int problem = 0, method = GS_METHOD_TSIT5, precision = GS_FP64;
   int d = 0, P = 0, k = 0, segw = 0;
+  int arena_block = 32;  // arena slots the record kernel reserves per warp at a time
   int64_t n = 0;
   double t0 = 0, t1 = 0, rtol = 0, atol = 0;
   int n_save = 0;
@@ -327,6 +328,7 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
   for (int attempt = 0; attempt < 3; ++attempt) {
     a.k = r->k;
     a.segw = r->segw;
+    a.arena_block = r->arena_block;
     a.stages = r->stages;
     a.side_stg = r->stages ? r->side_stg : nullptr;
     cudaError_t e = cudaMemsetAsync(r->ctr, 0, sizeof(Counters), s);
@@ -454,7 +456,17 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
     r->arena_cap = 0;
     r->segw = segw;
   }
-  const long long want = (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol, c.method) + r->k - 1) / r->k + 1);
+  // Expected segments, plus the unused tails of the record kernel's per-warp slot
+  // blocks: a warp reserves about an eighth of its expected segments at a time
+  // (32 to ARENA_BLOCK_HOST slots), and leaves less than one block unused.
+  const long long m = n > 0 ? n : 1;
+  const long long per_traj = (step_guess(c.problem, rtol, c.method) + r->k - 1) / r->k + 1;
+  const long long warps = std::min<long long>((m + 31) / 32, 4096 * 4);
+  long long blk = 32;
+  while (blk < ARENA_BLOCK_HOST && 8 * 2 * blk <= m * per_traj / warps) blk *= 2;
+  r->arena_block = (int)blk;
+  const long long slack = warps * blk;
+  const long long want = m * per_traj + slack;
   if (r->arena_cap > 0 && r->arena_cap < want / 4) {  // far too small for this ensemble: start over
     cudaFree(r->arena);
     r->arena = nullptr;
@@ -466,8 +478,8 @@ gs_status setup_record(gs_record* r, const Call& c, int64_t n, double t0, double
       r->stages = 0;
       r->k = c.k > 0 ? c.k : auto_ckpt_k(r, c.problem, c.pi.d, n);
       r->segw = segw_of(r->d, r->k);
-      st = ensure_arena(r, (long long)(n > 0 ? n : 1) * ((step_guess(c.problem, rtol, c.method) + r->k - 1) / r->k + 1),
-                        r->segw);
+      st = ensure_arena(r, m * ((step_guess(c.problem, rtol, c.method) + r->k - 1) / r->k + 1) + slack, r->segw);
+      // (the block size chosen above stays: it depends on the ensemble, not the layout)
     }
     if (st != GS_OK) return st;
   }

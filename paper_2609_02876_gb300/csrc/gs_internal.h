@@ -12,6 +12,10 @@ constexpr int KMAX_HOST = 32;  // largest checkpoint interval accepted by the AB
 // Largest stored-stage segment in doubles: the record kernel stages one segment
 // per lane in shared memory (128 lanes).
 constexpr int MAX_STAGE_SEGW = 72;
+// Arena slots the record kernel reserves per warp at a time (FwdArgs::arena_block):
+// one atomic per block instead of one per flush; at most arena_block - 1 slots
+// per warp stay unused at the end.
+constexpr int ARENA_BLOCK_HOST = 256;
 
 // Arguments of the record (forward) kernels. Passed by value.
 struct FwdArgs {
@@ -38,6 +42,7 @@ struct FwdArgs {
   int* any_failed;                // set when a trajectory ends with a non-OK status
   int k;                          // accepted steps per segment
   int segw;                       // doubles per segment
+  int arena_block;                // slots a warp reserves at a time (>= 32; 0 means ARENA_BLOCK_HOST)
   // Stored stages (k = 1, FP64): each segment also holds its step's stage
   // data after h (Tsit5: Y_1..Y_5; Rodas5P: Y_1..Y_7, U_0..U_7, the LU of W,
   // pivot reciprocals and pivots), and side_stg [n_save][payload][n] receives

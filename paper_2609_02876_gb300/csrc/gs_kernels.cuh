@@ -49,6 +49,7 @@ struct HasWeights<Pb, std::void_t<decltype(Pb::kWeights)>> : std::integral_const
 constexpr int TPB_FWD = 128;
 constexpr int TPB_REV = 128;
 
+
 enum : int { U_NONE = 0, U_RECOMP = 1, U_STEP = 2, U_SIDE = 3, U_DONE = 4, U_FAIL = 5 };
 
 __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -636,6 +637,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
   Carry cyp;
   double tp = 0.0;
   int jp = 0, je = 0;
+  long long res_next = 0, res_end = 0;  // this warp's reserved arena slots [res_next, res_end) (warp-uniform)
 
   for (;;) {
     // ---- refill: lanes without a trajectory take the next ticket
@@ -820,7 +822,26 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
 
     // ---- segment write-out: one arena slot per flushing lane, one atomic per warp
     if (__any_sync(FULL_MASK, flush)) {
-      const long long idx = warp_ticket(a.arena_top, flush);
+      // arena slots are reserved per warp in blocks (one atomic per block, not
+      // per flush); the unused tail of a warp's last block stays empty, since
+      // segments are linked, not indexed
+      const unsigned fm = __ballot_sync(FULL_MASK, flush);
+      const int cnt = __popc(fm), rem = (int)(res_end - res_next);
+      const int blk = a.arena_block >= 32 ? a.arena_block : ARENA_BLOCK_HOST;
+      long long nb = 0;
+      if (cnt > rem) {  // warp-uniform: a new block continues where the reserved one ends
+        unsigned long long base = 0;
+        if (lane_id() == 0) base = atomicAdd(a.arena_top, (unsigned long long)blk);
+        nb = (long long)__shfl_sync(FULL_MASK, base, 0);
+      }
+      const int rank = __popc(fm & ((1u << lane_id()) - 1u));
+      const long long idx = rank < rem ? res_next + rank : nb + (rank - rem);
+      if (cnt > rem) {
+        res_next = nb + (cnt - rem);
+        res_end = nb + blk;
+      } else {
+        res_next += cnt;
+      }
       if (flush) {
         stg[0] = __longlong_as_double(prev);
         if (idx < a.arena_cap) {

@@ -138,6 +138,7 @@ extern "C" gs_status gs_solve_grad_noalloc(int problem_id, int64_t n, const doub
   a.work = &ctr->work_fwd;
   a.k = k;
   a.segw = segw;
+  a.arena_block = 32;  // the fixed array: reserve one flush's worth at a time, wasting at most 31 slots a warp
   if (launch_tsit5_forward(problem_id, o.precision, a, s) != cudaSuccess) return GS_ERR_CUDA;
 
   RevArgs r;
