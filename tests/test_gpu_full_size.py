@@ -56,6 +56,33 @@ def test_full_size_results_equal_their_sample_and_the_oracle(name, n, m, rtol):
     assert_close(full["y0_bar"].T, o["y0_bar"], "y0_bar", rtol)
 
 
+def test_full_size_fp32_mixed_sample_and_oracle():
+    """Lorenz at 2^24 in the FP32-mixed form (the bench's second line): a sample
+    re-solved alone reproduces the full-size gradients bit for bit, and its error
+    against the FP64 oracle on its mesh stays at the FP32 level of the mixed
+    parity test (median 1e-4, max 1e-2 of the vector's scale)."""
+    n, m = 1 << 24, 1024
+    wl = W.make("lorenz", n)
+    s = api.solve_grad("lorenz", dev(wl["params"].T), dev(wl["y0"].T), wl["t0"], wl["t1"], wl["save_t"], wl["rtol"],
+                       wl["atol"], layout="soa", precision="fp32_mixed")
+    assert (s["status"] == 0).all().item()
+    idx = np.sort(np.random.default_rng(5).choice(n, m, replace=False))
+    full = {k: s[k].cpu().numpy()[..., idx] for k in ("params_bar", "y0_bar")}
+    del s
+    torch.cuda.empty_cache()
+    ws = sub(wl, idx)
+    P, Y = dev(ws["params"].T), dev(ws["y0"].T)
+    rec, _, _ = api.forward_record("lorenz", P, Y, ws["t0"], ws["t1"], ws["save_t"], ws["rtol"], ws["atol"],
+                                   layout="soa", want_saves=False, precision="fp32_mixed")
+    g = api.reverse(rec, P, Y, layout="soa")
+    np.testing.assert_array_equal(g["params_bar"].cpu().numpy(), full["params_bar"])
+    np.testing.assert_array_equal(g["y0_bar"].cpu().numpy(), full["y0_bar"])
+    off, h = rec.export_mesh()
+    o = oracle.replay_grad("lorenz", ws["params"], ws["y0"], ws["t0"], ws["t1"], ws["save_t"], off, h)
+    e = np.abs(full["params_bar"].T - o["params_bar"]) / np.abs(o["params_bar"]).max(1, keepdims=True)
+    assert np.median(e) < 1e-4 and e.max() < 1e-2, (np.median(e), e.max())
+
+
 def test_full_size_ude_sample_and_oracle():
     """LV UDE at 2^18 (FP32 network): per-trajectory results of a sample equal the
     full run bit for bit and match the FP64 oracle within the FP32 bound 1e-4."""
