@@ -74,12 +74,19 @@ int step_guess(int pid, double rtol, int method) {
 // rounded up to a 16-byte multiple. Tsit5: Y_1..Y_5 (a side step also Y_6);
 // Verner7: Y_1..Y_8 (a side step also its save state); Rodas5P: U_0..U_7, the
 // LU factors, pivot reciprocals and pivots (the stage inputs and the save state
-// are rebuilt from them).
+// are rebuilt from them); Rosenbrock23: k1, u2 and the LU of W (Y1 and the save
+// state rebuilt).
 int stage_step_payload(int method, int d) {
-  return method == GS_METHOD_RODAS5P ? 10 * d + d * d : (method == GS_METHOD_VERNER7 ? 8 * d : 5 * d);
+  switch (method) {
+    case GS_METHOD_RODAS5P: return 10 * d + d * d;
+    case GS_METHOD_ROSENBROCK23: return 4 * d + d * d;
+    case GS_METHOD_VERNER7: return 8 * d;
+  }
+  return 5 * d;  // Tsit5
 }
 int stage_side_payload(int method, int d) {
-  return stage_step_payload(method, d) + (method == GS_METHOD_RODAS5P ? 0 : d);
+  const bool rebuilt = method == GS_METHOD_RODAS5P || method == GS_METHOD_ROSENBROCK23;  // save state rebuilt
+  return stage_step_payload(method, d) + (rebuilt ? 0 : d);
 }
 int stage_segw_of(int method, int d) { return ((3 + d + stage_step_payload(method, d)) + 1) & ~1; }
 
@@ -389,12 +396,14 @@ int auto_ckpt_k(const gs_record* r, int problem, int d, int64_t n) {
 }
 
 // Stored stages when the caller allows them (gs_solve_grad), the method and
-// precision support them (Tsit5, Rodas5P or Verner7, FP64, no shared weights, a
-// segment within MAX_STAGE_SEGW doubles), k is automatic, and
+// precision support them (Tsit5, Rodas5P, Rosenbrock23 or Verner7, FP64, no
+// shared weights, a segment within MAX_STAGE_SEGW doubles), k is automatic, and
 // the expected record with its side-step stages takes at most 70% of the free
 // device memory (plus what this workspace already holds).
 bool choose_stages(const gs_record* r, const Call& c, int64_t n, int n_save, double rtol) {
-  if (c.method != GS_METHOD_TSIT5 && c.method != GS_METHOD_RODAS5P && c.method != GS_METHOD_VERNER7) return false;
+  if (c.method != GS_METHOD_TSIT5 && c.method != GS_METHOD_RODAS5P && c.method != GS_METHOD_VERNER7 &&
+      c.method != GS_METHOD_ROSENBROCK23)
+    return false;
   if (c.precision != GS_FP64 || c.pi.n_shared > 0 || c.k > 1) return false;
   if (stage_segw_of(c.method, c.pi.d) > MAX_STAGE_SEGW) return false;
   size_t free_b = 0, total_b = 0;

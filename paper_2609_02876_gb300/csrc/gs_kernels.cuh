@@ -380,12 +380,88 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
 // controller), f at the accepted state carried to the next step.
 struct Ros23Method {
   static constexpr int ORDER = 2, ERR_ORDER = 2;
-  static constexpr bool kStages = false;
+  static constexpr bool kStages = true;
   static constexpr double IDLE_H = 1.0;
   template <class Pb, class R>
   struct Carry {
     R F0[Pb::D];  // f(y) of the current accepted state
   };
+  // ---- stored stages: a step stores k1, u2 and the LU of W (factors, pivot
+  // reciprocals, pivots); Y1 = y + h/2 k1 and a side step's save state
+  // y + h (u2 + k1) are rebuilt from them by the step's own operations.
+  template <class Pb, class R>
+  struct StageData {
+    double k1[Pb::D], u2[Pb::D], LU[Pb::D][Pb::D], rinv[Pb::D];
+    int piv[Pb::D];
+  };
+  template <int D>
+  static constexpr int step_payload() {
+    return 4 * D + D * D;
+  }
+  template <int D>
+  static constexpr int side_payload() {
+    return step_payload<D>();
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static bool trial_s(const R (&y)[Pb::D], const R (&p)[Pb::NP], double h,
+                                                 const Carry<Pb, R>& cy, R (&ynew)[Pb::D], R (&e)[Pb::D],
+                                                 Carry<Pb, R>& next, StageData<Pb, R>& sd) {
+    return ros23_trial<Pb>(y, p, h, cy.F0, ynew, e, next.F0, sd.LU, sd.piv, sd.rinv, sd.k1, sd.u2);
+  }
+  template <class Pb, class R, class W>
+  __device__ __forceinline__ static void pack(const StageData<Pb, R>& sd, bool, W&& write) {
+    constexpr int D = Pb::D;
+    int i = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) write(i++, sd.k1[c]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) write(i++, sd.u2[c]);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) write(i++, sd.LU[r][c]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) write(i++, sd.rinv[c]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) write(i++, (double)sd.piv[c]);
+  }
+  template <class Pb, class R, class Rd>
+  __device__ __forceinline__ static void unpack(bool, const R (&)[Pb::D], Rd&& read, StageData<Pb, R>& sd) {
+    constexpr int D = Pb::D;
+    int i = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.k1[c] = read(i++);
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.u2[c] = read(i++);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) sd.LU[r][c] = read(i++);
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.rinv[c] = read(i++);
+#pragma unroll
+    for (int c = 0; c < D; ++c) sd.piv[c] = (int)read(i++);
+  }
+  template <class Pb, class R, bool USER_COT, class Acc>
+  __device__ __forceinline__ static bool unit_stored(const RevArgs& a, long long k, int mode, bool active, int us,
+                                                     const R (&x)[Pb::D], double h, const R (&p)[Pb::NP],
+                                                     const StageData<Pb, R>& sd, R (&lam)[Pb::D], Acc& pacc,
+                                                     double& loss) {
+    constexpr int D = Pb::D;
+    const bool side = (mode == U_SIDE);
+    const double hh = mul_(0.5, h);
+    double Y1[D], ynew[D], cv[D], v[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      Y1[c] = fma_(hh, sd.k1[c], x[c]);
+      ynew[c] = fma_(h, add_(sd.u2[c], sd.k1[c]), x[c]);
+    }
+    unit_cotangent<Pb, R, USER_COT>(a, k, active, side, us, ynew, lam, cv, loss);
+    ros23_reverse<Pb>(x, p, h, sd.k1, sd.u2, Y1, sd.LU, sd.piv, sd.rinv, cv, v, pacc);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lam[c] = !active ? lam[c] : (side ? add_(lam[c], v[c]) : v[c]);
+    return true;
+  }
   template <class Pb, class R>
   __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>& cy,
                                                float (&f0)[Pb::D]) {

@@ -418,14 +418,16 @@ __device__ __forceinline__ void ros23_stages(const double (&y)[Pb::D], const dou
   for (int c = 0; c < D; ++c) ynew[c] = fma_(h, add_(u2[c], k1[c]), y[c]);
 }
 
-// Trial step of the record: y_new, the error estimate e and F2 = f(y_new).
+// Trial step of the record: y_new, the error estimate e and F2 = f(y_new), and
+// the step's factored W and stage solutions k1, u2 (what a stored-stage record
+// keeps).
 template <class Pb>
 __device__ __forceinline__ bool ros23_trial(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
                                             const double (&F0)[Pb::D], double (&ynew)[Pb::D], double (&e)[Pb::D],
-                                            double (&F2)[Pb::D]) {
+                                            double (&F2)[Pb::D], double (&LU)[Pb::D][Pb::D], int (&piv)[Pb::D],
+                                            double (&rinv)[Pb::D], double (&k1)[Pb::D], double (&u2)[Pb::D]) {
   constexpr int D = Pb::D;
-  double LU[D][D], rinv[D], k1[D], u2[D], Y1[D], F1[D], r[D], k3[D];
-  int piv[D];
+  double Y1[D], F1[D], r[D], k3[D];
   const bool ok = ros23_factor<Pb>(y, p, h, LU, piv, rinv);
   ros23_stages<Pb>(y, p, h, F0, LU, piv, rinv, k1, u2, Y1, F1, ynew);
   Pb::f(ynew, p, F2);
@@ -439,6 +441,15 @@ __device__ __forceinline__ bool ros23_trial(const double (&y)[Pb::D], const doub
 #pragma unroll
   for (int c = 0; c < D; ++c) e[c] = mul_(h6, add_(fma_(-2.0, add_(u2[c], k1[c]), k1[c]), k3[c]));
   return ok;
+}
+template <class Pb>
+__device__ __forceinline__ bool ros23_trial(const double (&y)[Pb::D], const double (&p)[Pb::NP], double h,
+                                            const double (&F0)[Pb::D], double (&ynew)[Pb::D], double (&e)[Pb::D],
+                                            double (&F2)[Pb::D]) {
+  constexpr int D = Pb::D;
+  double LU[D][D], rinv[D], k1[D], u2[D];
+  int piv[D];
+  return ros23_trial<Pb>(y, p, h, F0, ynew, e, F2, LU, piv, rinv, k1, u2);
 }
 
 // Reverse of one Rosenbrock23 step (h held as data): given lam = dL/dy_new,

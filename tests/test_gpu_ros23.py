@@ -102,3 +102,21 @@ def test_ros23_solve_grad_and_forward_only_agree_with_record():
                   wl["atol"], layout="soa", method="rosenbrock23", step_counts=True)
     np.testing.assert_array_equal(f["y_save"].cpu().numpy(), ysv.cpu().numpy())
     np.testing.assert_array_equal(f["step_counts"].cpu().numpy(), rec.step_counts.cpu().numpy())
+
+
+@pytest.mark.parametrize("name,n,stages", [("robertson", 700, 1), ("hires", 120, 0)])
+def test_ros23_stored_stage_layout_is_bit_identical(name, n, stages):
+    """gs_solve_grad keeps each Rosenbrock23 step's k1, u2 and LU of W when the
+    segment fits (Robertson; not HIRES, d = 8) and rebuilds Y1 and the save
+    states from them; its gradients equal the compact record's bit for bit."""
+    wl = W.make(name, n)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    info = np.zeros(2, np.int32)
+    s = api.solve_grad(name, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                       method="rosenbrock23", record_info=info)
+    assert tuple(info) == (1, stages)
+    rec, _, _ = record(wl, method="rosenbrock23", want_saves=False)
+    g = api.reverse(rec, P, Y, layout="soa")
+    np.testing.assert_array_equal(s["loss"].cpu().numpy(), g["loss"].cpu().numpy())
+    np.testing.assert_array_equal(s["params_bar"].cpu().numpy(), g["params_bar"].cpu().numpy())
+    np.testing.assert_array_equal(s["y0_bar"].cpu().numpy(), g["y0_bar"].cpu().numpy())
