@@ -108,10 +108,12 @@ typedef struct {
                            before using the outputs or calling the library again */
   int32_t* record_info; /* optional HOST [2] output of gs_forward_record / gs_solve_grad /
                            gs_solve_grad_ctx: the record's checkpoint interval k, and 1 if
-                           the record also stored every step's stage inputs (gs_solve_grad
-                           chooses that layout for Tsit5 in FP64 when the device memory
-                           allows; the reverse sweep then reads the stages instead of
-                           recomputing them, with identical results), else 0 */
+                           the record also stored every step's stage data (gs_solve_grad
+                           chooses that layout in FP64 for Tsit5, Verner7, Rodas5P and
+                           Rosenbrock23 when the segment is small enough (not HIRES) and
+                           the device memory allows; the reverse sweep then reads the
+                           stages instead of recomputing them, with identical results),
+                           else 0 */
 } gs_options;
 
 /* A readable name for a status code (static storage, never NULL). */

@@ -44,9 +44,10 @@ struct FwdArgs {
   int segw;                       // doubles per segment
   int arena_block;                // slots a warp reserves at a time (>= 32; 0 means ARENA_BLOCK_HOST)
   // Stored stages (k = 1, FP64): each segment also holds its step's stage
-  // data after h (Tsit5: Y_1..Y_5; Rodas5P: Y_1..Y_7, U_0..U_7, the LU of W,
-  // pivot reciprocals and pivots), and side_stg [n_save][payload][n] receives
-  // the same for every save-time side step plus its save state.
+  // data after h (Tsit5: Y_1..Y_5; Verner7: Y_1..Y_8; Rodas5P: U_0..U_7 and
+  // the LU of W with pivot reciprocals and pivots; Rosenbrock23: k1, u2 and the
+  // LU of W), and side_stg [n_save][payload][n] receives the same for every
+  // save-time side step (plus its save state for the explicit methods).
   int stages;
   double* side_stg;
   double save_t[MAX_SAVE_HOST];
