@@ -94,3 +94,19 @@ def test_empty_ensembles_are_no_ops():
     e = torch.empty((3, 0), dtype=torch.float64)
     h = api.solve_grad_host("lorenz", e, e, 0.0, 1.0, wl["save_t"], 1e-6, 1e-8)
     assert h["params_bar"].shape == (3, 0)
+
+
+def test_record_outgrowing_the_first_arena_guess():
+    """t1 = 8 instead of 1: about eight times the steps the first arena size
+    assumes, so the record kernel overflows its arena, the host regrows it to the
+    measured demand and reruns; the results still match the oracle, and the
+    stored-stage workspace (gs_solve_grad) agrees with the compact record."""
+    wl = dict(W.make("lorenz", 3000), t1=8.0, save_t=np.linspace(0.8, 8.0, 10))
+    off, h = check(wl)
+    assert np.diff(off).mean() > 5 * 48
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    s = api.solve_grad("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa")
+    rec, _, _ = api.forward_record("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                   layout="soa", want_saves=False)
+    g = api.reverse(rec, P, Y, layout="soa")
+    np.testing.assert_array_equal(s["params_bar"].cpu().numpy(), g["params_bar"].cpu().numpy())
