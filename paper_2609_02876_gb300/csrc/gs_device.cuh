@@ -429,6 +429,12 @@ __host__ __device__ constexpr double Bhat(int j) {
 __host__ __device__ constexpr double Btilde(int j) { return B(j) - Bhat(j); }  // error weights
 }  // namespace tsit5
 
+// Problems with a shared network (they declare kWeights).
+template <class Pb, class = void>
+struct HasNet : std::false_type {};
+template <class Pb>
+struct HasNet<Pb, std::void_t<decltype(Pb::kWeights)>> : std::true_type {};
+
 // Stage inputs Y[0..6] of one Tsit5 step from y with size h (Y[0] = y,
 // Y[6] = y_new by FSAL) and stage slopes K[0..KN-1]. K[0] must hold f(y).
 // KN = 7 also evaluates k7 = f(y_new) for the error estimate and FSAL.
@@ -440,8 +446,20 @@ __device__ __forceinline__ void tsit5_stages(const R (&y)[Pb::D], const R (&p)[P
   for (int c = 0; c < D; ++c) Y[0][c] = y[c];
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
+    // FP32 (not the network problems, whose register budget it upsets): components 0, 1 as FP32x2
+    constexpr bool PACK = std::is_same<R, float>::value && D >= 2 && !HasNet<Pb>::value;
+    if constexpr (PACK) {
+      // the same per-component IEEE operations, two components per instruction
+      float2 s = __fmul2_rn(make_float2(tsit5::A(i, 0), tsit5::A(i, 0)), make_float2(K[0][0], K[0][1]));
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
+      for (int j = 1; j < i; ++j)
+        s = __ffma2_rn(make_float2(tsit5::A(i, j), tsit5::A(i, j)), make_float2(K[j][0], K[j][1]), s);
+      const float2 yy = __ffma2_rn(make_float2(h, h), s, make_float2(y[0], y[1]));
+      Y[i][0] = yy.x;
+      Y[i][1] = yy.y;
+    }
+#pragma unroll
+    for (int c = PACK ? 2 : 0; c < D; ++c) {
       R s = mul_(R(tsit5::A(i, 0)), K[0][c]);
 #pragma unroll
       for (int j = 1; j < i; ++j) s = fma_(R(tsit5::A(i, j)), K[j][c], s);
