@@ -139,3 +139,20 @@ def test_gradient_accuracy_against_an_independent_sensitivity():
     ferr = np.abs(fwd - tight).max(1) / np.abs(tight).max(1)
     assert 4.6e-8 < np.median(rel) < 4.6e-4, np.median(rel)
     assert np.median(rel) < 30 * np.median(ferr) + 1e-12, (np.median(rel), np.median(ferr))
+
+
+def test_hires_rodas5p_gradient_accuracy_is_the_papers_order():
+    """Sec. 5 reports the Rodas5P replay reaching an achieved error of 1.3e-7 on
+    HIRES (tolerance not stated). At rtol 1e-6, atol 1e-10 the oracle's gradient
+    with respect to y0 sits at or below that level against a converged solve
+    (rtol 1e-11), and is not exact (a loose check on the Rodas5P table and the
+    step control together)."""
+    wl = W.make("hires", 4)
+
+    def grad(rtol, atol):
+        return oracle.solve_grad("hires", wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], rtol, atol,
+                                 method=oracle.METHOD_RODAS5P)
+
+    g, ref = grad(1e-6, 1e-10), grad(1e-11, 1e-15)
+    e = np.abs(g["y0_bar"] - ref["y0_bar"]).max(1) / np.abs(ref["y0_bar"]).max(1)
+    assert e.max() < 2 * 1.3e-7 and e.min() > 1e-11, e
