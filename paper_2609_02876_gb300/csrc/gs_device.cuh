@@ -542,20 +542,43 @@ __device__ __forceinline__ void tsit5_reverse(const R (&Y)[7][Pb::D], const R (&
   R acc[6][D];
 #pragma unroll
   for (int q = 0; q < D; ++q) v[q] = c[q];
+  // FP32 (not the network problems): components 0, 1 as FP32x2, the same
+  // per-component IEEE operations
+  constexpr bool PACK = std::is_same<R, float>::value && D >= 2 && !HasNet<Pb>::value;
+  constexpr int Q0 = PACK ? 2 : 0;  // first component done one at a time
 #pragma unroll
   for (int j = 5; j >= 0; --j) {
     R kb[D], yb[D];
+    if constexpr (PACK) {
+      const float2 bb = make_float2(tsit5::B(j), tsit5::B(j)), hh = make_float2(h, h), cc = make_float2(c[0], c[1]);
+      const float2 k2 = (j == 5) ? __fmul2_rn(hh, __fmul2_rn(bb, cc))
+                                 : __fmul2_rn(hh, __ffma2_rn(bb, cc, make_float2(acc[j][0], acc[j][1])));
+      kb[0] = k2.x;
+      kb[1] = k2.y;
+    }
 #pragma unroll
-    for (int q = 0; q < D; ++q)
+    for (int q = Q0; q < D; ++q)
       kb[q] = (j == 5) ? mul_(h, mul_(R(tsit5::B(j)), c[q])) : mul_(h, fma_(R(tsit5::B(j)), c[q], acc[j][q]));
     pbacc.template vjp<Pb>(Y[j], p, kb, yb);
+    if constexpr (PACK) {
+      const float2 v2 = __fadd2_rn(make_float2(v[0], v[1]), make_float2(yb[0], yb[1]));
+      v[0] = v2.x;
+      v[1] = v2.y;
+    }
 #pragma unroll
-    for (int q = 0; q < D; ++q) v[q] = add_(v[q], yb[q]);
+    for (int q = Q0; q < D; ++q) v[q] = add_(v[q], yb[q]);
 #pragma unroll
-    for (int l = 0; l < j; ++l)
+    for (int l = 0; l < j; ++l) {
+      if constexpr (PACK) {
+        const float2 aa = make_float2(tsit5::A(j, l), tsit5::A(j, l)), y2 = make_float2(yb[0], yb[1]);
+        const float2 a2 = (j == 5) ? __fmul2_rn(aa, y2) : __ffma2_rn(aa, y2, make_float2(acc[l][0], acc[l][1]));
+        acc[l][0] = a2.x;
+        acc[l][1] = a2.y;
+      }
 #pragma unroll
-      for (int q = 0; q < D; ++q)
+      for (int q = Q0; q < D; ++q)
         acc[l][q] = (j == 5) ? mul_(R(tsit5::A(j, l)), yb[q]) : fma_(R(tsit5::A(j, l)), yb[q], acc[l][q]);
+    }
   }
   pbacc.flush();
 }
