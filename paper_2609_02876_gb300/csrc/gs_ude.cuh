@@ -1,8 +1,10 @@
 // The LV UDE problem: dx/dt = a x - NN(x, y)_1, dy/dt = -d y + NN(x, y)_2 with a
 // shared-weight MLP 2-16-16-2 (tanh hidden layers, linear output), FP32.
 //
-// Per lane the network is evaluated and differentiated on the FP32 CUDA cores
-// (weights in shared memory, broadcast reads). The gradient with respect to the
+// The record kernel evaluates the network per lane on the FP32 CUDA cores
+// (weights in shared memory, broadcast reads); the reverse sweep evaluates and
+// differentiates it warp-collectively, its 16 x 16 hidden layer on the tensor
+// cores (LvUdeWarp below). The gradient with respect to the
 // 354 shared weights is a sum over every lane, stage and step of rank-1
 // products, i.e. a dense contraction over the lanes; each warp accumulates it
 // with tensor-core MMAs (mma.sync m16n8k8, TF32 inputs split hi + lo so that
@@ -71,51 +73,6 @@ struct LvUde {
     forward(y[0], y[1], h1, h2, nn);
     o[0] = fmaf(p[0], y[0], -nn[0]);
     o[1] = fmaf(-p[1], y[1], nn[1]);
-  }
-  // Per-lane backpropagation of the output cotangent v through f at y:
-  // yb = J^T v, pb += f_theta^T v, and the per-layer factors whose outer
-  // products over the lanes form the weight gradient.
-  struct Factors {
-    float x, y, h1[UDE_H], h2[UDE_H], gz1[UDE_H], gz2[UDE_H], go[2];
-  };
-  __device__ __forceinline__ static void backprop(const float (&y)[D], const float (&p)[NP], const float (&v)[D],
-                                                  float (&yb)[D], float (&pb)[NP], Factors& fa) {
-    asm volatile("" ::: "memory");
-    const float* w = weights();
-    float nn[2], gh2[UDE_H];
-    forward(y[0], y[1], fa.h1, fa.h2, nn);
-    fa.x = y[0];
-    fa.y = y[1];
-    fa.go[0] = -v[0];  // f0 = a x - nn0
-    fa.go[1] = v[1];   // f1 = -d y + nn1
-#pragma unroll
-    for (int j = 0; j < UDE_H; ++j) {
-      gh2[j] = fmaf(w[UDE_W3 + j], fa.go[0], w[UDE_W3 + UDE_H + j] * fa.go[1]);
-      fa.gz2[j] = gh2[j] * fmaf(-fa.h2[j], fa.h2[j], 1.0f);
-    }
-#pragma unroll
-    for (int j = 0; j < UDE_H; ++j) {
-      float s = 0.0f;
-#pragma unroll
-      for (int i = 0; i < UDE_H; ++i) s = fmaf(w[UDE_W2 + UDE_H * i + j], fa.gz2[i], s);
-      fa.gz1[j] = s * fmaf(-fa.h1[j], fa.h1[j], 1.0f);
-    }
-    float gx = 0.0f, gy = 0.0f;
-#pragma unroll
-    for (int j = 0; j < UDE_H; ++j) {
-      gx = fmaf(w[UDE_W1 + 2 * j], fa.gz1[j], gx);
-      gy = fmaf(w[UDE_W1 + 2 * j + 1], fa.gz1[j], gy);
-    }
-    yb[0] = fmaf(p[0], v[0], gx);
-    yb[1] = fmaf(-p[1], v[1], gy);
-    pb[0] = fmaf(y[0], v[0], pb[0]);
-    pb[1] = fmaf(-y[1], v[1], pb[1]);
-  }
-  // Plain per-lane VJP (no weight gradient): used where only J^T v and f_theta^T v are needed.
-  __device__ __forceinline__ static void vjp(const float (&y)[D], const float (&p)[NP], const float (&v)[D],
-                                             float (&yb)[D], float (&pb)[NP]) {
-    Factors fa;
-    backprop(y, p, v, yb, pb, fa);
   }
 };
 
@@ -370,38 +327,15 @@ struct UdeAcc {
   template <class Pb>
   __device__ __forceinline__ void vjp(const float (&y)[2], const float (&p)[2], const float (&v)[2],
                                       float (&yb)[2]) {
+    static_assert(std::is_same<Pb, LvUdeWarp>::value, "the UDE reverse sweep uses the warp-collective network");
     float x[2] = {0.0f, 0.0f};
-    if constexpr (std::is_same<Pb, LvUdeWarp>::value) {
-      LvUdeWarp::backprop_warp(y, p, v, yb, x);  // leaves the factor rows staged
-    } else {
-      LvUde::Factors fa;
-      LvUde::backprop(y, p, v, yb, x, fa);
-      stage(fa);
-    }
+    LvUdeWarp::backprop_warp(y, p, v, yb, x);  // leaves the factor rows staged
 #pragma unroll
     for (int q = 0; q < 2; ++q) th.u[q] = add_(th.u[q], x[q]);
     accumulate();
   }
   __device__ __forceinline__ void flush() { th.flush(); }
 
-  // Writes this lane's factor row from a per-lane VJP.
-  __device__ __forceinline__ void stage(const LvUde::Factors& fa) {
-    const int lane = threadIdx.x & 31, sw = ude_sw(lane);
-    float* row = ude_stage() + lane * UDE_ROW;
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < UDE_H; j += 4) {
-      *reinterpret_cast<float4*>(row + (j ^ sw)) =
-          make_float4(fa.gz2[j], fa.gz2[j + 1], fa.gz2[j + 2], fa.gz2[j + 3]);
-      *reinterpret_cast<float4*>(row + ((16 + j) ^ sw)) =
-          make_float4(fa.h1[j], fa.h1[j + 1], fa.h1[j + 2], fa.h1[j + 3]);
-      *reinterpret_cast<float4*>(row + ((32 + j) ^ sw)) =
-          make_float4(fa.gz1[j], fa.gz1[j + 1], fa.gz1[j + 2], fa.gz1[j + 3]);
-      *reinterpret_cast<float4*>(row + ((48 + j) ^ sw)) =
-          make_float4(fa.h2[j], fa.h2[j + 1], fa.h2[j + 2], fa.h2[j + 3]);
-    }
-    *reinterpret_cast<float4*>(row + (64 ^ sw)) = make_float4(fa.x, fa.y, fa.go[0], fa.go[1]);
-  }
   // The weight-gradient MMAs over the warp's staged factor rows.
   __device__ __forceinline__ void accumulate() {
     const float* st = ude_stage();
