@@ -1,6 +1,7 @@
 """Run one named workload once, for profiling a single kernel under ncu.
 
     python -m paper_2609_02876_gb300.cases <case> [--traj N] [--problem P] [--precision fp64|fp32_mixed]
+                                                  [--method tsit5|rodas5p|rosenbrock23|verner7]
 
 Cases (each on the seeded synthetic workload of `workloads.make`):
   solve_grad    record + reverse sweep (gs_solve_grad), 3 warm-up calls then one
@@ -27,6 +28,8 @@ def main(argv=None) -> int:
     ap.add_argument("--traj", type=int, default=1 << 20)
     ap.add_argument("--problem", default="lorenz")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
+    ap.add_argument("--method", default=None, choices=["tsit5", "rodas5p", "rosenbrock23", "verner7"],
+                    help="default: Tsit5 for the non-stiff problems, Rodas5P for the stiff ones")
     args = ap.parse_args(argv)
     build.build()
     wl = W.make(args.problem, args.traj)
@@ -36,11 +39,13 @@ def main(argv=None) -> int:
     common = (wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"])
     if args.case == "solve_grad":
         run = lambda: api.solve_grad(args.problem, P, Y, *common, layout="soa", precision=args.precision,
-                                     shared_w=SW)
+                                     shared_w=SW, method=args.method)
     elif args.case == "forward_only":
-        run = lambda: api.solve(args.problem, P, Y, *common, layout="soa", precision=args.precision, shared_w=SW)
+        run = lambda: api.solve(args.problem, P, Y, *common, layout="soa", precision=args.precision, shared_w=SW,
+                                method=args.method)
     else:
-        rec, _, _ = api.forward_record(args.problem, P, Y, *common, layout="soa", want_saves=False)
+        rec, _, _ = api.forward_record(args.problem, P, Y, *common, layout="soa", want_saves=False,
+                                       method=args.method)
         run = lambda: api.forward_grad(rec, P, Y, wrt=("params",), layout="soa")
     for _ in range(4):
         run()
