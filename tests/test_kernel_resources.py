@@ -65,3 +65,11 @@ def test_ude_reverse_fits_three_ctas(tsit5):
     # 3 CTAs of 128 threads per SM need at most 170 registers
     regs, _ = find(tsit5, "reverse_k1_kernel", "Tsit5Method", "LvUdeWarp", "EfLb0ELb0E")
     assert regs <= 170
+
+
+def test_verner7_stored_stage_kernels():
+    res = resources("gs_vern7.cu")
+    regs, spill = find(res, "record_kernel", "Verner7Method", "Lorenz", "EdLb1ELb1E")
+    assert regs <= 128 and spill == 0  # 4 CTAs per SM
+    regs, spill = find(res, "reverse_k1_kernel", "Verner7Method", "Lorenz", "EdLb0ELb1E")
+    assert regs <= 170 and spill == 0  # 3 CTAs per SM
