@@ -1,5 +1,6 @@
 // The persistent record and reverse-sweep kernels, generic over the one-step
-// method (Tsit5 for non-stiff problems, Rodas5P for stiff ones).
+// method (Tsit5 and Verner7 for non-stiff problems, Rodas5P and Rosenbrock23
+// for stiff ones).
 //
 // Both kernels are persistent: a grid of resident CTAs whose lanes each own one
 // trajectory at a time and take the next one from a global ticket counter
@@ -14,7 +15,8 @@
 // weighted RMS error test and an integral controller. Accepted step sizes are
 // staged per lane in shared memory and written out as fixed-size record
 // segments [prev, t_start, y_start[d], h[k]] (one vector-stored segment per k
-// accepted steps) allocated from a device arena.
+// accepted steps; with stored stages, k = 1 and the step's stage data follow
+// h) allocated from a device arena in per-warp blocks of slots.
 //
 // Reverse (paper Sec. 3.1, discrete adjoint of Eq. (replay)): each lane walks
 // its trajectory's segments last to first and runs one unit per iteration: a
@@ -25,7 +27,9 @@
 // A Method provides Carry (state carried between accepted steps), start (the
 // carry and f(y0) for the starting step), trial (one trial step: y_new and the
 // error estimate; false if the step's linear system is singular), side (one
-// step of a given size from an accepted state) and unit (the reverse unit).
+// step of a given size from an accepted state) and unit (the reverse unit);
+// with kStages also StageData, its payload sizes, trial_s, pack, unpack and
+// unit_stored (the stored-stage record and reverse unit).
 #pragma once
 
 #include <type_traits>
@@ -896,7 +900,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
     // (a.k == 0: forward-only solve, nothing is recorded)
     const bool flush = (a.k > 0) && (k >= 0) && ((slot == a.k) || (done && slot > 0));
 
-    // ---- segment write-out: one arena slot per flushing lane, one atomic per warp
+    // ---- segment write-out: one arena slot per flushing lane, from the warp's reserved block
     if (__any_sync(FULL_MASK, flush)) {
       // arena slots are reserved per warp in blocks (one atomic per block, not
       // per flush); the unused tail of a warp's last block stays empty, since
