@@ -147,3 +147,25 @@ def test_adjoint_matches_central_fd_on_same_mesh(name):
     fd = (lp - lm) / 2.0
     ad = (np.concatenate([g["params_bar"], g["y0_bar"]], 1) * dx).sum(1)
     assert (np.abs(fd - ad) / np.abs(ad)).max() < 1e-5
+
+
+@pytest.mark.parametrize("name,med_bound,max_bound", [("robertson", 2e-6, 1e-2), ("hires", 2e-7, 1e-4)])
+def test_record_accuracy_against_radau(name, med_bound, max_bound):
+    """The adaptive Rosenbrock23 solve at the workload's tolerance against scipy's
+    Radau at rtol 1e-10: the save states match to the accuracy a second-order
+    method reaches there (Robertson median 2.9e-7, HIRES 3.0e-8 measured)."""
+    from scipy.integrate import solve_ivp
+    from tests.test_oracle_record import _scipy_rhs
+    wl = W.make(name, 4)
+    rec = oracle.record(wl["problem"], wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], wl["rtol"],
+                        wl["atol"], method=R23)
+    assert (rec["status"] == 0).all()
+    errs = []
+    for k in range(4):
+        sol = solve_ivp(_scipy_rhs(name, wl["params"][k]), (wl["t0"], wl["t1"]), wl["y0"][k], method="Radau",
+                        t_eval=wl["save_t"], rtol=1e-10, atol=1e-14)
+        assert sol.success
+        big = np.abs(sol.y.T) > 1e3 * wl["atol"]
+        errs.append((np.abs(rec["y_save"][k] - sol.y.T) / np.abs(sol.y.T))[big])
+    e = np.concatenate(errs)
+    assert np.median(e) < med_bound and e.max() < max_bound, (np.median(e), e.max())
