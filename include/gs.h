@@ -152,7 +152,9 @@ gs_status gs_forward_record(int problem_id, int64_t n, const double* params, con
  * the recorded mesh with h held as data. For each trajectory, segments are
  * visited last to first; states inside a segment are recomputed from its
  * checkpoint, stages are recomputed per step, and the stage cotangents are
- * propagated back (for Rodas5P with one transposed LU solve per stage).
+ * propagated back (for the Rosenbrock methods with one transposed LU solve per
+ * stage). (gs_solve_grad's own record may instead hold the stage data, which
+ * its reverse sweep reads rather than recomputes; see record_info.)
  *
  * params (and shared_w) must be the values the record's states were computed
  * with: those of gs_forward_record, or those of the last gs_record_refresh.
