@@ -290,7 +290,9 @@ gs_status gs_solve(int problem_id, int64_t n, const double* params, const double
  * stream capture. Every call shares the one array and overwrites what the
  * previous call left in it: calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.
- * Synchronises `stream`. Only Tsit5 problems; shared_w_bar is not written.
+ * Synchronises `stream`. Only Tsit5 problems without shared weights: a
+ * shared-weight problem (n_shared > 0, the LV UDE) returns GS_ERR_INVALID_ARG
+ * before any work; shared_w and shared_w_bar are not used.
  */
 #define GS_NOALLOC_MAX_TRAJ 16384
 #define GS_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -63,7 +63,9 @@ extern "C" gs_status gs_solve_grad_noalloc(int problem_id, int64_t n, const doub
   if (n < 0 || n > GS_NOALLOC_MAX_TRAJ) return GS_ERR_INVALID_ARG;
   if (n == 0) return GS_OK;
   if (!params || !y0 || !traj_status) return GS_ERR_INVALID_ARG;
-  if (n_shared > 0 && !shared_w) return GS_ERR_INVALID_ARG;
+  // Shared-weight problems need the reverse sweep's per-warp weight partials,
+  // which live outside the fixed array, and a k = 1 record: not offered here.
+  if (n_shared > 0) return GS_ERR_INVALID_ARG;
   if (!std::isfinite(t0) || !std::isfinite(t1) || !(t1 > t0)) return GS_ERR_INVALID_ARG;
   if (n_save < 0 || n_save > MAX_SAVE_HOST || (n_save > 0 && !save_t)) return GS_ERR_INVALID_ARG;
   for (int s = 0; s < n_save; ++s) {

@@ -1,0 +1,198 @@
+"""Pins of the oracle's record map R (the adaptive loop of the paper's Sec. 2.1:
+weighted RMS error norm, accept when it is at most one, an integral
+controller, the controller's own starting step) against scipy, an
+implementation that shares nothing with the oracle.
+
+- The starting step equals scipy's `select_initial_step` (Hairer, Norsett &
+  Wanner I, Sec. II.4: the same RMS norm and Euler probe) called with the
+  method's order, to 1e-12 relative (the probe's difference f(y0 + h0 f0) - f0
+  cancels, which raises the two codes' rounding differences to ~1e-14).
+- The accepted mesh equals that of scipy's explicit Runge-Kutta driver
+  (`RungeKutta._step_impl`: safety 0.9, factor clamped to [0.2, 10], exponent
+  -1/(q+1) for an error estimate of order q, factor capped at 1 after a
+  rejection, scale atol + rtol max(|y|, |y_new|)) run with the oracle's Tsit5
+  table (itself pinned by the order conditions) and the same starting step:
+  the same number of accepted and attempted steps and the same h to 1e-6
+  relative. The two codes round the stage sums differently (~1e-16 of |K|);
+  the error estimate cancels down to ~1e-9 of |K| on smooth stretches, so err
+  differs by up to ~1e-7 and each controller factor by ~1e-8 (measured:
+  7e-8 on Van der Pol), and the differences compound over ~200 steps to
+  ~5e-8 in h. A changed control constant moves h by 1e-3 or more.
+
+A plausible mistake in the oracle's control constants must fail these pins;
+the last test plants several, one at a time, in a copy of the oracle compiled
+here, and checks that each one is caught.
+"""
+import contextlib
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+from scipy.integrate._ivp.common import select_initial_step
+from scipy.integrate._ivp.rk import RungeKutta
+
+import oracle
+from paper_2609_02876_gb300 import workloads as W
+
+TSIT5 = oracle.METHOD_TSIT5
+H0_RTOL = 1e-12
+H_RTOL = 1e-6  # h agreement (see the module docstring)
+
+
+def _rhs(name, p):
+    if name == "lorenz":
+        return lambda t, y: np.array([p[0] * (y[1] - y[0]), y[0] * (p[1] - y[2]) - y[1], y[0] * y[1] - p[2] * y[2]])
+    if name == "vdp":
+        return lambda t, y: np.array([y[1], p[0] * ((1 - y[0] ** 2) * y[1] - y[0])])
+    raise KeyError(name)
+
+
+def _tsit5_driver(order_for_first_step):
+    tab = oracle.tableau(TSIT5)
+
+    class Tsit5Scipy(RungeKutta):
+        """scipy's RK driver with the Tsit5 table: six stages before y_new, the
+        seventh (FSAL) stage is f(y_new), which scipy appends as K[-1]."""
+        C = tab["c"][:6]
+        A = tab["A"][:6, :6]
+        B = tab["b"][:6]
+        E = tab["b"] - tab["bhat"]
+        P = np.zeros((7, 1))
+        order = 5
+        error_estimator_order = 4
+        n_stages = 6
+
+        def __init__(self, fun, t0, y0, t_bound, **kw):
+            super().__init__(fun, t0, y0, t_bound, **kw)
+            self.h_abs = select_initial_step(self.fun, self.t, self.y, t_bound, np.inf, self.f, self.direction,
+                                             order_for_first_step, self.rtol, self.atol)
+
+    return Tsit5Scipy
+
+
+def _scipy_mesh(name, p, y0, t0, t1, rtol, atol):
+    sol = solve_ivp(_rhs(name, p), (t0, t1), np.array(y0, dtype=np.float64), method=_tsit5_driver(5),
+                    rtol=rtol, atol=atol)
+    assert sol.status == 0
+    # nfev: f(y0), the starting-step probe (twice: scipy's own and the one above),
+    # then 6 evaluations per attempted step
+    return np.diff(sol.t), (sol.nfev - 3) // 6
+
+
+def _cases():
+    out = []
+    for name, rtol in (("lorenz", 1e-6), ("lorenz", 1e-4), ("vdp", 1e-6), ("vdp", 1e-3)):
+        wl = W.make(name, 24, rtol=rtol, seed=3)
+        out.append((name, wl))
+    return out
+
+
+def _compare_meshes(cases):
+    """Per trajectory: (equal accepted count, equal attempted count, max rel h diff
+    over all steps but the last). Also returns the number of rejected trials seen."""
+    res, rejected = [], 0
+    for name, wl in cases:
+        rec = oracle.record(name, wl["params"], wl["y0"], wl["t0"], wl["t1"], [], wl["rtol"], wl["atol"],
+                            method=TSIT5, want_saves=False)
+        for k in range(wl["params"].shape[0]):
+            h_o = rec["h"][rec["offsets"][k]:rec["offsets"][k + 1]]
+            h_s, att_s = _scipy_mesh(name, wl["params"][k], wl["y0"][k], wl["t0"], wl["t1"], wl["rtol"],
+                                     wl["atol"])
+            rejected += int(rec["n_att"][k] - rec["S"][k])
+            if h_o.size != h_s.size:
+                res.append((False, False, np.inf))
+                continue
+            dh = np.abs(h_o[:-1] - h_s[:-1]) / h_s[:-1] if h_o.size > 1 else np.zeros(1)
+            res.append((True, int(rec["n_att"][k]) == int(att_s), float(dh.max())))
+    return res, rejected
+
+
+def test_initial_step_equals_scipy_select_initial_step():
+    for name in ("lorenz", "vdp"):
+        for rtol in (1e-3, 1e-6, 1e-9):
+            wl = W.make(name, 16, rtol=rtol, seed=5)
+            for k in range(16):
+                p, y0 = wl["params"][k], wl["y0"][k]
+                f = _rhs(name, p)
+                for order in (2, 5, 7):
+                    ref = select_initial_step(f, wl["t0"], y0, wl["t1"], np.inf, f(wl["t0"], y0), 1.0, order,
+                                              wl["rtol"], wl["atol"])
+                    got = oracle.initial_step(name, p, y0, wl["t0"], wl["t1"], wl["rtol"], wl["atol"], order=order)
+                    assert abs(got - ref) <= H0_RTOL * ref, (name, rtol, k, order, got, ref)
+
+
+def test_initial_step_special_cases_equal_scipy():
+    # y0 = 0 (d0 < 1e-5: the 1e-6 first guess) and a short span (the interval clamp)
+    p = np.array([10.0, 28.0, 8.0 / 3.0])
+    f = _rhs("lorenz", p)
+    for y0, t1 in ((np.zeros(3), 1.0), (np.array([1.0, 1.0, 1.0]), 1e-7), (np.array([1e-7, 0.0, 0.0]), 1.0)):
+        ref = select_initial_step(f, 0.0, y0, t1, np.inf, f(0.0, y0), 1.0, 5, 1e-6, 1e-8)
+        got = oracle.initial_step("lorenz", p, y0, 0.0, t1, 1e-6, 1e-8, order=5)
+        assert abs(got - ref) <= H0_RTOL * ref, (y0, t1, got, ref)
+
+
+def test_accepted_mesh_equals_scipy_rk_driver_with_tsit5_table():
+    res, rejected = _compare_meshes(_cases())
+    same_s = np.mean([r[0] for r in res])
+    same_att = np.mean([r[1] for r in res])
+    worst = max(r[2] for r in res)
+    assert rejected >= 20, rejected  # the cases exercise the rejection path and its cap
+    assert same_s == 1.0 and same_att == 1.0, (same_s, same_att)
+    assert worst <= H_RTOL, worst
+
+
+# ----------------------------------------------------------------------------- planted mistakes
+
+@contextlib.contextmanager
+def _mutant_oracle(old, new):
+    """The oracle with one source substitution, compiled like the real one and
+    swapped in for the duration of the block."""
+    src = open(oracle._SRC).read()
+    assert src.count(old) >= 1, old
+    d = tempfile.mkdtemp(prefix="oracle_mutant_")
+    cpp, so = os.path.join(d, "m.cpp"), os.path.join(d, "m.so")
+    with open(cpp, "w") as fh:
+        fh.write(src.replace(old, new))
+    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared", "-o", so, cpp,
+                    "-lpthread"], check=True)
+    saved = (oracle._lib, oracle._LIB_PATH)
+    oracle._lib, oracle._LIB_PATH = None, so
+    try:
+        yield
+    finally:
+        oracle._lib, oracle._LIB_PATH = saved
+
+
+MUTANTS = [
+    # starting step: exponent 1/p instead of 1/(p+1)
+    ("std::pow(0.01 / dm, 1.0 / (order + 1))", "std::pow(0.01 / dm, 1.0 / order)"),
+    # controller exponent -1/q instead of -1/(q+1)
+    ("std::pow(err, -1.0 / (q + 1))", "std::pow(err, -1.0 / q)"),
+    # safety factor
+    ("double f = 0.9 * std::pow", "double f = 0.95 * std::pow"),
+    # growth clamp
+    ("return std::min(10.0, std::max(0.2, f));", "return std::min(5.0, std::max(0.2, f));"),
+    # no cap after a rejection
+    ("if (reject_prev) fac = std::min(fac, 1.0);", "(void)reject_prev;"),
+    # error scale from |y| only
+    ("std::max(std::fabs(y[c]), std::fabs(yn[c]))", "std::fabs(y[c])"),
+]
+
+
+@pytest.mark.parametrize("old,new", MUTANTS)
+def test_planted_control_mistake_fails_the_scipy_pins(old, new):
+    cases = _cases()[:3]
+    with _mutant_oracle(old, new):
+        res, _ = _compare_meshes(cases)
+        worst = max(r[2] for r in res)
+        mesh_ok = all(r[0] and r[1] for r in res) and worst <= H_RTOL
+        wl = W.make("lorenz", 4, seed=5)
+        f = _rhs("lorenz", wl["params"][0])
+        ref = select_initial_step(f, 0.0, wl["y0"][0], 1.0, np.inf, f(0.0, wl["y0"][0]), 1.0, 5, wl["rtol"],
+                                  wl["atol"])
+        h0 = oracle.initial_step("lorenz", wl["params"][0], wl["y0"][0], 0.0, 1.0, wl["rtol"], wl["atol"], order=5)
+        h0_ok = abs(h0 - ref) <= H0_RTOL * ref
+    assert not (mesh_ok and h0_ok), f"planted mistake not detected: {new}"
