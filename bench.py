@@ -83,10 +83,10 @@ def unit_flops(problem, method=None):
         rev = 4 * D * D + 2 * v + 8 * D + 2 * c["con"]
         return {"stage_fwd": step, "vjp_unit": step + rev, "trial": trial}
     if method == "verner7":
-        # Verner7 (10 stages, 37 nonzero a_ij, 30 of them in stages 2..9): the replay
+        # Verner7 (10 stages, 36 nonzero a_ij, 30 of them in stages 2..9): the replay
         # step evaluates 9 slopes, the stage inputs (sum over rows of 2 m + 1 per
         # component for m coefficients: 68 D) and y_new (7 weights: 15 D). The trial
-        # adds stage 10 (f, 15 D) and the error estimate (7 weights: 14 D). Reverse:
+        # adds stage 10 (f, 13 D) and the error estimate (8 weights: 16 D). Reverse:
         # 9 stage VJPs, the a_ij recursions (60 D), kbar and the cotangent sum (34 D).
         step = 9 * f + 83 * D
         trial = 10 * f + 112 * D + norm

@@ -4,9 +4,7 @@
 // TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or load
 // this file; only the tests, the smoke check and the CPU-baseline leg of the
 // benchmark use it. It shares no code, header, table or constant with the CUDA
-// library: every coefficient below is typed here from the method's publication
-// (Verner7's, which the paper does not print, from the construction stated
-// beside its table).
+// library: every coefficient below is typed here from the method's publication.
 //
 // What it computes (paper, Sec. 3.1 "The construction", Eq. (replay)):
 //   record  R:  an adaptive solve that keeps the accepted step sizes {h_i};
@@ -22,16 +20,17 @@
 //
 // Parity pins: see tests/test_oracle_*.py (order conditions, closed-form linear
 // replay, complex-step gradients, finite differences, invariants, Rosenbrock23's
-// stability function and error estimate, the neural term's weight derivatives).
+// stability function and error estimate, the neural term's weight derivatives;
+// the starting step and the controller against scipy's implementations of the
+// same textbook rules, with planted mistakes caught).
 //
 // Parity unpinned (no value outside this file fixes them; they only shape the
-// mesh, which the gradient treats as data): the step-size controller constants
-// (safety 0.9, clamp [0.2, 10], exponent 1/(q+1) with q = 4 for Tsit5 and
-// Rodas5P, q = 2 for Rosenbrock23 and q = 6 for Verner7), the starting-step
-// algorithm's order argument, the end-of-span sliver 1e-12 and the quartered
-// step after a singular linear system; Rodas5P's coefficients beyond what its
-// order conditions and stiff accuracy fix; and Verner7's free parameters
-// beyond its order conditions (the paper prints no table for it).
+// mesh, which the gradient treats as data): the end-of-span sliver 1e-12, the
+// quartered step after a singular linear system, the controller exponents of
+// the methods other than Tsit5 (1/(q+1) with q = 4 for Rodas5P, 2 for
+// Rosenbrock23, 6 for Verner7: the same function with the method's order),
+// and Rodas5P's coefficients beyond what its order conditions and stiff
+// accuracy fix.
 
 #include <algorithm>
 #include <cmath>
@@ -449,44 +448,76 @@ struct RodasTab {
 };
 const RodasTab& rodas() { static RodasTab t; return t; }
 
-// Verner7: the seventh-order explicit pair with a sixth-order embedded
-// formula (paper Sec. 5, higher-order engines). Its coefficients are not printed
-// in the paper; this table is a 10-stage 7(6) pair of Verner's structure built
-// from the order conditions: c_2 = 1/200, c_3 = 49/450, c_4 = 49/300, the
-// stage-order conditions sum_j a_ij c_j^(k-1) = c_i^k / k (k <= 3) from stage 4
-// on with a_i2 = 0 there, b_2 = b_3 = 0; the 7th-order formula uses stages 1..9
-// (c_9 = 1); stage 10 enters only the 6th-order formula (bhat_10 = 1/20); the
-// remaining free parameters minimise the 8th-order error coefficients with
-// |a_ij| < 10. Zero-based indices below.
+// Verner7: Verner's "efficient" seventh-order explicit pair with a
+// sixth-order embedded formula (J. H. Verner, Numerically optimal Runge-Kutta
+// pairs with interpolants, Numer. Algorithms 53 (2010) 383-396), the pair the
+// paper cites for its higher-order engine (Sec. 5). 10 stages, not FSAL: the
+// 7th-order solution uses stages 1..9 (c_9 = 1), stage 10 (c_10 = 1) enters
+// only the 6th-order formula; a_i2 = 0 from stage 4 on and b_2 = b_3 = 0.
+// Coefficients to 40 significant digits as published (the compiler rounds each
+// to the nearest double). Zero-based indices below.
 struct Vern7Tab {
   double c[10], A[10][10], b[10], bhat[10];
   Vern7Tab() {
     std::memset(this, 0, sizeof(*this));
-    c[1] = 0.005; c[2] = 0.10888888888888888; c[3] = 0.16333333333333333; c[4] = 0.4412412362945031;
-    c[5] = 0.5125358668205884; c[6] = 0.8153902148736141; c[7] = 0.8320269620357567; c[8] = 1.0;
-    c[9] = 0.6933543729566465;
+    c[1] = 0.005;
+    c[2] = 0.1088888888888888888888888888888888888889;
+    c[3] = 0.1633333333333333333333333333333333333333;
+    c[4] = 0.4555;
+    c[5] = 0.6095094489978381317087004421486024949638;
+    c[6] = 0.884;
+    c[7] = 0.925;
+    c[8] = 1.0;
+    c[9] = 1.0;
     A[1][0] = 0.005;
-    A[2][0] = -1.07679012345679; A[2][1] = 1.1856790123456789;
-    A[3][0] = 0.04083333333333333; A[3][2] = 0.1225;
-    A[4][0] = 0.5613218080778262; A[4][2] = -2.148246263778861; A[4][3] = 2.0281656919955378;
-    A[5][0] = -0.2543252074630068; A[5][2] = 1.1460969356524386; A[5][3] = -0.6256885247646464;
-    A[5][4] = 0.24645266339580296;
-    A[6][0] = -0.39131654768852675; A[6][2] = 1.0869726640940662; A[6][3] = -0.09561592609715297;
-    A[6][4] = -1.6735343341907647; A[6][5] = 1.8888843587559923;
-    A[7][0] = 0.7511017644073372; A[7][2] = -1.7821652979246974; A[7][3] = 0.9581342511515946;
-    A[7][4] = 2.108363229780166; A[7][5] = -1.4351672874423511; A[7][6] = 0.23176030206370712;
-    A[8][0] = -0.06432542550599094; A[8][2] = 0.2780602767716229; A[8][3] = 0.08112820061408241;
-    A[8][4] = 0.5376285679147711; A[8][5] = -0.25166364169525557; A[8][6] = 0.03175435637869014;
-    A[8][7] = 0.38741766552207996;
-    A[9][0] = -3.1187164246988965; A[9][2] = 9.02697407983311; A[9][3] = -4.244000513534974;
-    A[9][4] = -8.655295625316855; A[9][5] = 8.324471440363192; A[9][6] = -2.143779190364296;
-    A[9][7] = 1.5037006066753662;
-    b[0] = 0.04694589982741012; b[3] = 0.25890626416312335; b[4] = 0.12888376947512276;
-    b[5] = 0.23633374752686637; b[6] = 0.15830047862284352; b[7] = 0.11902434451146297;
-    b[8] = 0.051605495873170766;
-    bhat[0] = 0.04776173310604042; bhat[3] = 0.25503657692265447; bhat[4] = 0.17287055313602917;
-    bhat[5] = 0.17283855677828097; bhat[6] = 0.042409513909176653; bhat[7] = 0.20747757027464744;
-    bhat[8] = b[8]; bhat[9] = 0.05;
+    A[2][0] = -1.076790123456790123456790123456790123457;
+    A[2][1] = 1.185679012345679012345679012345679012346;
+    A[3][0] = 0.04083333333333333333333333333333333333333;
+    A[3][2] = 0.1225;
+    A[4][0] = 0.6389139236255726780508121615993336109954;
+    A[4][2] = -2.455672638223656809662640566430653894211;
+    A[4][3] = 2.272258714598084131611828404831320283215;
+    A[5][0] = -2.661577375018757131119259297861818119279;
+    A[5][2] = 10.80451388645613769565396655365532838482;
+    A[5][3] = -8.353914657396199411968048547819291691541;
+    A[5][4] = 0.8204875949566569791420417341743839209619;
+    A[6][0] = 6.067741434696770992718360183877276714679;
+    A[6][2] = -24.71127363591108579734203485290746001803;
+    A[6][3] = 20.42751793078889394045773111748346612697;
+    A[6][4] = -1.906157978816647150624096784352757010879;
+    A[6][5] = 1.006172249242068014790040335899474187268;
+    A[7][0] = 12.05467007625320299509109452892778311648;
+    A[7][2] = -49.75478495046898932807257615331444758322;
+    A[7][3] = 41.14288863860467663259698416710157354209;
+    A[7][4] = -4.461760149974004185641911603484815375051;
+    A[7][5] = 2.042334822239174959821717077708608543738;
+    A[7][6] = -0.09834843665406107379530801693870224403537;
+    A[8][0] = 10.13814652288180787641845141981689030769;
+    A[8][2] = -42.64113603171750214622846006736635730625;
+    A[8][3] = 35.76384003992257007135021178023160054034;
+    A[8][4] = -4.348022840392907653340370296908245943710;
+    A[8][5] = 2.009862268377035895441943593011827554771;
+    A[8][6] = 0.3487490460338272405953822853053145879140;
+    A[8][7] = -0.2714390051048312842371587140910297407572;
+    A[9][0] = -45.03007203429867712435322405073769635151;
+    A[9][2] = 187.3272437654588840752418206154201997384;
+    A[9][3] = -154.0288236935018690596728621034510402582;
+    A[9][4] = 18.56465306347536233859492332958439136765;
+    A[9][5] = -7.141809679295078854925420496823551192821;
+    A[9][6] = 1.308808578161378625114762706007696696508;
+    b[0] = 0.04715561848627222170431765108838175679569;
+    b[3] = 0.2575056429843415189596436101037687580986;
+    b[4] = 0.2621665397741262047713863095764527711129;
+    b[5] = 0.1521609265673855740323133199165117535523;
+    b[6] = 0.4939969170032484246907175893227876844296;
+    b[7] = -0.2943031171403250441557244744092703429139;
+    b[8] = 0.08131747232495109999734599440136761892478;
+    bhat[0] = 0.04460860660634117628731817597479197781432;
+    bhat[3] = 0.2671640378571372680509102260943837899738;
+    bhat[4] = 0.2201018300177293019979715776650753096323;
+    bhat[5] = 0.2188431703143156830983120833512893824578;
+    bhat[6] = 0.2289871705411202883378173889763552365362;
+    bhat[9] = 0.02029518466335628222767054793810430358554;
   }
 };
 const Vern7Tab& vern7() { static Vern7Tab t; return t; }

@@ -584,74 +584,72 @@ __device__ __forceinline__ void tsit5_reverse(const R (&Y)[7][Pb::D], const R (&
 }
 
 // ---------------------------------------------------------------------------
-// Verner7: the seventh-order Verner pair (paper Sec. 5, higher-order engines).
-// The paper prints no coefficients; this is a 10-stage 7(6) pair of Verner's
-// structure fixed by its order conditions (c_2 = 1/200, c_3 = 49/450,
-// c_4 = 49/300, stage order 3 from stage 4 on with a_i2 = 0 there,
-// b_2 = b_3 = 0). The 7th-order solution uses stages 1..9; stage 10 feeds only
-// the 6th-order embedded formula. Not FSAL: each step evaluates f(y).
+// Verner7: Verner's "efficient" seventh-order pair with a sixth-order embedded
+// formula (J. H. Verner, Numer. Algorithms 53 (2010) 383-396), the pair the
+// paper cites for its higher-order engine (Sec. 5). The 7th-order solution
+// uses stages 1..9 (c_9 = 1); stage 10 (c_10 = 1) feeds only the 6th-order
+// embedded formula; a_i2 = 0 from stage 4 on and b_2 = b_3 = 0. Not FSAL:
+// each step evaluates f(y). Coefficients to 40 significant digits as
+// published (each rounds to the nearest double at compile time).
 // ---------------------------------------------------------------------------
 namespace vern7 {
 __host__ __device__ constexpr double A(int i, int j) {
   // 0-based stage i (1..9), column j < i
-  return (i == 1 && j == 0)   ? 0.005
-         : (i == 2 && j == 0) ? -1.07679012345679
-         : (i == 2 && j == 1) ? 1.1856790123456789
-         : (i == 3 && j == 0) ? 0.04083333333333333
+  return (i == 1 && j == 0) ? 0.005
+         : (i == 2 && j == 0) ? -1.076790123456790123456790123456790123457
+         : (i == 2 && j == 1) ? 1.185679012345679012345679012345679012346
+         : (i == 3 && j == 0) ? 0.04083333333333333333333333333333333333333
          : (i == 3 && j == 2) ? 0.1225
-         : (i == 4 && j == 0) ? 0.5613218080778262
-         : (i == 4 && j == 2) ? -2.148246263778861
-         : (i == 4 && j == 3) ? 2.0281656919955378
-         : (i == 5 && j == 0) ? -0.2543252074630068
-         : (i == 5 && j == 2) ? 1.1460969356524386
-         : (i == 5 && j == 3) ? -0.6256885247646464
-         : (i == 5 && j == 4) ? 0.24645266339580296
-         : (i == 6 && j == 0) ? -0.39131654768852675
-         : (i == 6 && j == 2) ? 1.0869726640940662
-         : (i == 6 && j == 3) ? -0.09561592609715297
-         : (i == 6 && j == 4) ? -1.6735343341907647
-         : (i == 6 && j == 5) ? 1.8888843587559923
-         : (i == 7 && j == 0) ? 0.7511017644073372
-         : (i == 7 && j == 2) ? -1.7821652979246974
-         : (i == 7 && j == 3) ? 0.9581342511515946
-         : (i == 7 && j == 4) ? 2.108363229780166
-         : (i == 7 && j == 5) ? -1.4351672874423511
-         : (i == 7 && j == 6) ? 0.23176030206370712
-         : (i == 8 && j == 0) ? -0.06432542550599094
-         : (i == 8 && j == 2) ? 0.2780602767716229
-         : (i == 8 && j == 3) ? 0.08112820061408241
-         : (i == 8 && j == 4) ? 0.5376285679147711
-         : (i == 8 && j == 5) ? -0.25166364169525557
-         : (i == 8 && j == 6) ? 0.03175435637869014
-         : (i == 8 && j == 7) ? 0.38741766552207996
-         : (i == 9 && j == 0) ? -3.1187164246988965
-         : (i == 9 && j == 2) ? 9.02697407983311
-         : (i == 9 && j == 3) ? -4.244000513534974
-         : (i == 9 && j == 4) ? -8.655295625316855
-         : (i == 9 && j == 5) ? 8.324471440363192
-         : (i == 9 && j == 6) ? -2.143779190364296
-         : (i == 9 && j == 7) ? 1.5037006066753662
+         : (i == 4 && j == 0) ? 0.6389139236255726780508121615993336109954
+         : (i == 4 && j == 2) ? -2.455672638223656809662640566430653894211
+         : (i == 4 && j == 3) ? 2.272258714598084131611828404831320283215
+         : (i == 5 && j == 0) ? -2.661577375018757131119259297861818119279
+         : (i == 5 && j == 2) ? 10.80451388645613769565396655365532838482
+         : (i == 5 && j == 3) ? -8.353914657396199411968048547819291691541
+         : (i == 5 && j == 4) ? 0.8204875949566569791420417341743839209619
+         : (i == 6 && j == 0) ? 6.067741434696770992718360183877276714679
+         : (i == 6 && j == 2) ? -24.71127363591108579734203485290746001803
+         : (i == 6 && j == 3) ? 20.42751793078889394045773111748346612697
+         : (i == 6 && j == 4) ? -1.906157978816647150624096784352757010879
+         : (i == 6 && j == 5) ? 1.006172249242068014790040335899474187268
+         : (i == 7 && j == 0) ? 12.05467007625320299509109452892778311648
+         : (i == 7 && j == 2) ? -49.75478495046898932807257615331444758322
+         : (i == 7 && j == 3) ? 41.14288863860467663259698416710157354209
+         : (i == 7 && j == 4) ? -4.461760149974004185641911603484815375051
+         : (i == 7 && j == 5) ? 2.042334822239174959821717077708608543738
+         : (i == 7 && j == 6) ? -0.09834843665406107379530801693870224403537
+         : (i == 8 && j == 0) ? 10.13814652288180787641845141981689030769
+         : (i == 8 && j == 2) ? -42.64113603171750214622846006736635730625
+         : (i == 8 && j == 3) ? 35.76384003992257007135021178023160054034
+         : (i == 8 && j == 4) ? -4.348022840392907653340370296908245943710
+         : (i == 8 && j == 5) ? 2.009862268377035895441943593011827554771
+         : (i == 8 && j == 6) ? 0.3487490460338272405953822853053145879140
+         : (i == 8 && j == 7) ? -0.2714390051048312842371587140910297407572
+         : (i == 9 && j == 0) ? -45.03007203429867712435322405073769635151
+         : (i == 9 && j == 2) ? 187.3272437654588840752418206154201997384
+         : (i == 9 && j == 3) ? -154.0288236935018690596728621034510402582
+         : (i == 9 && j == 4) ? 18.56465306347536233859492332958439136765
+         : (i == 9 && j == 5) ? -7.141809679295078854925420496823551192821
+         : (i == 9 && j == 6) ? 1.308808578161378625114762706007696696508
                               : 0.0;
 }
 __host__ __device__ constexpr double B(int j) {
-  return j == 0   ? 0.04694589982741012
-         : j == 3 ? 0.25890626416312335
-         : j == 4 ? 0.12888376947512276
-         : j == 5 ? 0.23633374752686637
-         : j == 6 ? 0.15830047862284352
-         : j == 7 ? 0.11902434451146297
-         : j == 8 ? 0.051605495873170766
+  return j == 0 ? 0.04715561848627222170431765108838175679569
+         : j == 3 ? 0.2575056429843415189596436101037687580986
+         : j == 4 ? 0.2621665397741262047713863095764527711129
+         : j == 5 ? 0.1521609265673855740323133199165117535523
+         : j == 6 ? 0.4939969170032484246907175893227876844296
+         : j == 7 ? -0.2943031171403250441557244744092703429139
+         : j == 8 ? 0.08131747232495109999734599440136761892478
                   : 0.0;
 }
 __host__ __device__ constexpr double Bhat(int j) {
-  return j == 0   ? 0.04776173310604042
-         : j == 3 ? 0.25503657692265447
-         : j == 4 ? 0.17287055313602917
-         : j == 5 ? 0.17283855677828097
-         : j == 6 ? 0.042409513909176653
-         : j == 7 ? 0.20747757027464744
-         : j == 8 ? B(8)
-         : j == 9 ? 0.05
+  return j == 0 ? 0.04460860660634117628731817597479197781432
+         : j == 3 ? 0.2671640378571372680509102260943837899738
+         : j == 4 ? 0.2201018300177293019979715776650753096323
+         : j == 5 ? 0.2188431703143156830983120833512893824578
+         : j == 6 ? 0.2289871705411202883378173889763552365362
+         : j == 9 ? 0.02029518466335628222767054793810430358554
                   : 0.0;
 }
 __host__ __device__ constexpr double Btilde(int j) { return B(j) - Bhat(j); }  // error weights
@@ -695,7 +693,7 @@ __device__ __forceinline__ void vern7_update(const R (&y)[Pb::D], const R (&K)[N
   }
 }
 
-// Embedded error estimate e = h sum_j (b_j - bhat_j) k_j (stage 9's weight is zero).
+// Embedded error estimate e = h sum_j (b_j - bhat_j) k_j (stages 2 and 3 have zero weight).
 template <class Pb, class R>
 __device__ __forceinline__ void vern7_error(const R (&K)[10][Pb::D], R h, R (&e)[Pb::D]) {
 #pragma unroll

@@ -130,24 +130,51 @@ def test_rodas5p_stiffly_accurate():
 
 
 def test_verner7_order_conditions():
-    """All 85 trees to order 7 for b, all 37 to order 6 for bhat (to the rounding of
-    the 17-digit table), bhat not of order 7; Verner's structure: explicit, row
-    sums c, c_9 = 1, stages 2 and 3 unweighted and stage 2 used only by stage 3,
-    stage 10 feeding only the embedded formula."""
+    """Verner's 7(6) pair: all 85 trees to order 7 for b, all 37 to order 6 for
+    bhat, bhat not of order 7; Verner's structure: explicit, row sums c,
+    c_9 = c_10 = 1, stages 2 and 3 unweighted and stage 2 used only by stage 3,
+    stage 10 feeding only the embedded formula. The table's entries reach 187,
+    whose double has an ulp of 2.8e-14: the residuals of the rounded table are
+    ~4e-15 (row sums ~1e-14), against ~1e-8 for a coefficient changed in its
+    ninth digit (test_planted_coefficient_error_is_detected)."""
     tab = oracle.tableau(oracle.METHOD_VERNER7)
     A, b, bh, c = tab["A"], tab["b"], tab["bhat"], tab["c"]
     Z = np.zeros_like(A)
     r7 = residuals(A, Z, b, 7)
     r6 = residuals(A, Z, bh, 6)
     assert len(r7) == 85 and len(r6) == 37
-    assert max(abs(r) for _, r in r7) < 2e-15
-    assert max(abs(r) for _, r in r6) < 2e-15
+    assert max(abs(r) for _, r in r7) < 1e-14
+    assert max(abs(r) for _, r in r6) < 1e-14
     assert max(abs(r) for _, r in residuals(A, Z, bh, 7)) > 1e-5
-    np.testing.assert_allclose(A.sum(1), c, atol=2e-15)
-    assert c[8] == 1.0
+    np.testing.assert_allclose(A.sum(1), c, atol=3e-14)
+    assert c[8] == 1.0 and c[9] == 1.0
     assert np.allclose(np.tril(A, -1), A)
     assert b[1] == b[2] == bh[1] == bh[2] == 0.0 and b[9] == 0.0 and bh[9] != 0.0
     assert (A[3:, 1] == 0.0).all() and (A[:9, 9] == 0.0).all()
+
+
+def _quadrature_weights(c, cols, p):
+    """The unique weights w on the nodes c[cols] with sum_j w_j c_j^k = 1/(k+1),
+    k = 0..p-1 (a Vandermonde system), in exact rational arithmetic on the
+    doubles c."""
+    from fractions import Fraction
+    import sympy
+    M = sympy.Matrix([[Fraction(float(c[j])) ** k for j in cols] for k in range(p)])
+    rhs = sympy.Matrix([sympy.Rational(1, k + 1) for k in range(p)])
+    return [float(x) for x in M.LUsolve(rhs)]
+
+
+def test_verner7_weights_are_the_quadrature_weights_of_its_nodes():
+    """With seven nonzero 7th-order weights (stages 1, 4..9) and six nonzero
+    6th-order weights (stages 1, 4..7, 10), the bushy-tree conditions
+    sum_j b_j c_j^k = 1/(k+1) alone fix b and bhat from the nodes: the pair's
+    weights must be those quadrature weights (to the rounding of the nodes)."""
+    tab = oracle.tableau(oracle.METHOD_VERNER7)
+    b, bh, c = tab["b"], tab["bhat"], tab["c"]
+    wb = _quadrature_weights(c, [0, 3, 4, 5, 6, 7, 8], 7)
+    wh = _quadrature_weights(c, [0, 3, 4, 5, 6, 9], 6)
+    np.testing.assert_allclose(b[[0, 3, 4, 5, 6, 7, 8]], wb, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(bh[[0, 3, 4, 5, 6, 9]], wh, rtol=0, atol=1e-15)
 
 
 def test_planted_coefficient_error_is_detected():
