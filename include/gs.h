@@ -72,9 +72,23 @@ enum {
   GS_NEURAL_ROBERTSON = 6
 };
 
-/* Arithmetic of the stage and adjoint work. GS_FP32_MIXED keeps FP64 for the
- * step-size control (t, h, the error norm and the controller). */
+/* Arithmetic of the stage and adjoint work. GS_FP32_MIXED keeps t and h in
+ * FP64; how the error norm and the controller are evaluated is gs_options.control. */
 enum { GS_FP64 = 0, GS_FP32_MIXED = 1 };
+
+/* Evaluation of the step-size control (the error norm, the accept test, the
+ * controller factor and the starting step of the paper's Sec. 2.1), which only
+ * chooses the mesh: the gradient is exact on whatever mesh is recorded.
+ *  GS_CONTROL_FAST (default): the forms' cheap evaluation. FP64: each norm
+ *    ratio e_c / (atol + rtol max(|y_c|, |ynew_c|)) to FP32 accuracy, squares
+ *    summed in FP64; controller factor and starting step in FP32 with the
+ *    hardware log2/exp2. FP32-mixed: the whole norm in FP32.
+ *  GS_CONTROL_FP64: norm, controller (0.9 err^(-1/(q+1)) clamped to [0.2, 10],
+ *    with pow), starting step and the step-size floor test all in FP64, as a
+ *    plain CPU implementation writes them; the recorded mesh then follows that
+ *    implementation's to rounding. Tsit5 only (no shared-weight problems);
+ *    other methods return GS_ERR_INVALID_ARG. */
+enum { GS_CONTROL_FAST = 0, GS_CONTROL_FP64 = 1 };
 
 /* One-step methods (paper Sec. 3.2): Tsit5 (Tsitouras 2011) for non-stiff
  * problems, Rodas5P (Steinebach 2023) for stiff ones, the second-order
@@ -114,6 +128,7 @@ typedef struct {
                            the device memory allows; the reverse sweep then reads the
                            stages instead of recomputing them, with identical results),
                            else 0 */
+  int control;          /* GS_CONTROL_FAST or GS_CONTROL_FP64 */
 } gs_options;
 
 /* A readable name for a status code (static storage, never NULL). */
@@ -332,6 +347,19 @@ gs_status gs_record_export_mesh(const gs_record* rec, int64_t* offsets, double* 
 
 /* Releases a record (NULL is accepted). */
 gs_status gs_record_free(gs_record* rec);
+
+/*
+ * Measured FMA throughput of the current device, in TFLOP/s (an FMA counts
+ * two flops): the denominator of the ALU roofline fractions of the record and
+ * reverse kernels, whose work is scalar FP64 or FP32 arithmetic per lane (the
+ * paper's method has no dense contraction outside the neural right-hand
+ * sides). kind 0: FP64 FMA; 1: FP32 FMA; 2: packed FP32x2 FMA (two single
+ * FMAs per instruction). A full-occupancy grid of independent FMA chains,
+ * best of five ~40 ms launches on the legacy default stream, which the call
+ * synchronises. Allocates and frees a small output buffer. Not part of the
+ * solve path.
+ */
+gs_status gs_measure_fma_peak(int kind, double* tflops);
 
 #ifdef __cplusplus
 }

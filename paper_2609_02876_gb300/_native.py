@@ -14,6 +14,7 @@ from . import build as _build
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_UNKNOWN_PROBLEM, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TRAJ_FAILED, \
     GS_ERR_TIMEOUT = range(7)
 GS_FP64, GS_FP32_MIXED = 0, 1
+GS_CONTROL_FAST, GS_CONTROL_FP64 = 0, 1
 GS_METHOD_AUTO, GS_METHOD_TSIT5, GS_METHOD_RODAS5P, GS_METHOD_ROSENBROCK23, GS_METHOD_VERNER7 = 0, 1, 2, 3, 4
 PROBLEMS = {"lorenz": 0, "vdp": 1, "robertson": 2, "hires": 3, "linear": 4, "lv_ude": 5, "nrob": 6}
 TRAJ_STATUS = {0: "ok", 1: "maxsteps", 2: "dt_underflow", 3: "nonfinite", 4: "singular"}
@@ -22,7 +23,7 @@ TRAJ_STATUS = {0: "ok", 1: "maxsteps", 2: "dt_underflow", 3: "nonfinite", 4: "si
 class GsOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("ckpt_k", C.c_int), ("max_steps", C.c_int64),
                 ("h0", C.c_double), ("step_counts", C.c_void_p), ("kernel_ms", C.POINTER(C.c_float)),
-                ("timeout_ms", C.c_double), ("record_info", C.POINTER(C.c_int32))]
+                ("timeout_ms", C.c_double), ("record_info", C.POINTER(C.c_int32)), ("control", C.c_int)]
 
 
 class GsError(RuntimeError):
@@ -56,6 +57,7 @@ def lib():
         L.gs_forward_record.argtypes = [i32, i64, vp, vp, vp, d, d, C.POINTER(C.c_double), i32, d, d,
                                         C.POINTER(GsOptions), vp, vp, vp, C.POINTER(vp)]
         L.gs_reverse.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.gs_measure_fma_peak.argtypes = [i32, C.POINTER(C.c_double)]
         L.gs_solve_grad.argtypes = [i32, i64, vp, vp, vp, d, d, C.POINTER(C.c_double), i32, d, d,
                                     C.POINTER(GsOptions), vp, vp, vp, vp, vp, vp]
         L.gs_solve.argtypes = [i32, i64, vp, vp, vp, d, d, C.POINTER(C.c_double), i32, d, d,

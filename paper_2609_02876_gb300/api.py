@@ -31,10 +31,11 @@ def problem_info(problem):
 
 
 def _opts(precision="fp64", method=None, ckpt_k=0, max_steps=0, h0=0.0, step_counts=None,
-          kernel_ms=None, timeout_ms=0.0, record_info=None) -> N.GsOptions:
+          kernel_ms=None, timeout_ms=0.0, record_info=None, control="fast") -> N.GsOptions:
     o = N.GsOptions()
     N.lib().gs_default_options(C.byref(o))
     o.precision = {"fp64": N.GS_FP64, "fp32_mixed": N.GS_FP32_MIXED}[precision]
+    o.control = {"fast": N.GS_CONTROL_FAST, "fp64": N.GS_CONTROL_FP64}[control]
     o.method = {None: N.GS_METHOD_AUTO, "tsit5": N.GS_METHOD_TSIT5, "rodas5p": N.GS_METHOD_RODAS5P,
                 "rosenbrock23": N.GS_METHOD_ROSENBROCK23, "verner7": N.GS_METHOD_VERNER7}[method]
     o.ckpt_k = int(ckpt_k)

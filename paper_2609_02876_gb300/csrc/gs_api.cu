@@ -239,6 +239,7 @@ struct Call {
   float* kernel_ms;
   double timeout_ms;
   int32_t* record_info;
+  int control;
 };
 
 // Kernel launches by method.
@@ -306,6 +307,9 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   if (!std::isfinite(o.timeout_ms) || o.timeout_ms < 0) return GS_ERR_INVALID_ARG;
   c->timeout_ms = o.timeout_ms;
   c->record_info = o.record_info;
+  if (o.control != GS_CONTROL_FAST && o.control != GS_CONTROL_FP64) return GS_ERR_INVALID_ARG;
+  if (o.control == GS_CONTROL_FP64 && (method != GS_METHOD_TSIT5 || c->pi.n_shared > 0)) return GS_ERR_INVALID_ARG;
+  c->control = o.control;
   if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_RODAS5P && !rodas_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_ROSENBROCK23 && !ros23_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
@@ -327,6 +331,7 @@ gs_status run_record(gs_record* r, const Call& c, int64_t n, const double* param
   a.rtol = r->rtol;
   a.atol = r->atol;
   a.h0 = c.h0;
+  a.control = c.control;
   a.max_steps = c.max_steps;
   a.n_save = r->n_save;
   std::memcpy(a.save_t, r->save_t, sizeof(double) * r->n_save);
@@ -975,6 +980,7 @@ gs_status gs_solve(int problem_id, int64_t n, const double* params, const double
   a.rtol = rtol;
   a.atol = atol;
   a.h0 = c.h0;
+  a.control = c.control;
   a.max_steps = c.max_steps;
   a.n_save = n_save;
   if (n_save) std::memcpy(a.save_t, save_t, sizeof(double) * n_save);

@@ -970,6 +970,78 @@ __device__ __forceinline__ double initial_step_f32(const float (&y0)[Pb::D], con
 }
 
 // ---------------------------------------------------------------------------
+// FP64 step control (GS_CONTROL_FP64): the error norm, the controller factor
+// and the starting step evaluated in FP64 in the order of the plain textbook
+// form (the paper's Sec. 2.1 norm and accept test; Hairer, Norsett & Wanner I,
+// Sec. II.4 for the starting step), with IEEE division, square root and the
+// library pow. The mesh it records follows a plain CPU evaluation of the same
+// rule up to the rounding of the stage arithmetic.
+// ---------------------------------------------------------------------------
+
+// err = sqrt((1/D) sum_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2); accept iff err <= 1.
+template <int D, class R>
+__device__ __forceinline__ double err_norm_f64(const R (&e)[D], const R (&y)[D], const R (&yn)[D], double rtol,
+                                               double atol) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const double sc = add_(atol, mul_(rtol, max_abs(to_d(y[c]), to_d(yn[c]))));
+    const double r = __ddiv_rn(to_d(e[c]), sc);
+    s = add_(s, mul_(r, r));
+  }
+  return __dsqrt_rn(__ddiv_rn(s, (double)D));
+}
+
+// clamp(0.9 err^(-1/(Q+1)), 0.2, 10); err = 0 gives 10.
+template <int Q>
+__device__ __forceinline__ double ctrl_factor_f64(double err) {
+  if (!(err > 0.0)) return 10.0;
+  const double f = mul_(0.9, pow(err, -1.0 / (Q + 1)));
+  return fmin(10.0, fmax(0.2, f));
+}
+
+// RMS of v_c / sc_c.
+template <int D>
+__device__ __forceinline__ double rms_scaled_f64(const double (&v)[D], const double (&sc)[D]) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const double r = __ddiv_rn(v[c], sc[c]);
+    s = add_(s, mul_(r, r));
+  }
+  return __dsqrt_rn(__ddiv_rn(s, (double)D));
+}
+
+// Starting step (Hairer, Norsett & Wanner I, Sec. II.4) in FP64 from y0, theta
+// and f(y0): d0 = ||y0||, d1 = ||f0||, h0 = 0.01 d0 / d1 (1e-6 if either is
+// below 1e-5), one explicit Euler probe y1 = y0 + h0 f0, d2 = ||f(y1) - f0|| / h0,
+// h1 = (0.01 / max(d1, d2))^(1/(p+1)) (max(1e-6, 1e-3 h0) if that max is at most
+// 1e-15), h = min(100 h0, h1, t1 - t0); the norm is the weighted RMS with
+// scale atol + rtol |y0_c|.
+template <class Pb, int ORDER>
+__device__ __forceinline__ double initial_step_f64(const double (&y0)[Pb::D], const double (&p)[Pb::NP],
+                                                   const double (&f0)[Pb::D], double t0, double t1, double rtol,
+                                                   double atol) {
+  constexpr int D = Pb::D;
+  double sc[D], y1[D], f1[D], df[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) sc[c] = add_(atol, mul_(rtol, fabs(y0[c])));
+  const double d0 = rms_scaled_f64<D>(y0, sc), d1 = rms_scaled_f64<D>(f0, sc);
+  const double span = sub_(t1, t0);
+  double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : __ddiv_rn(mul_(0.01, d0), d1);
+  h0 = fmin(h0, span);
+#pragma unroll
+  for (int c = 0; c < D; ++c) y1[c] = add_(y0[c], mul_(h0, f0[c]));
+  Pb::f(y1, p, f1);
+#pragma unroll
+  for (int c = 0; c < D; ++c) df[c] = sub_(f1[c], f0[c]);
+  const double d2 = __ddiv_rn(rms_scaled_f64<D>(df, sc), h0);
+  const double dm = fmax(d1, d2);
+  const double h1 = (dm <= 1e-15) ? fmax(1e-6, mul_(h0, 1e-3)) : pow(__ddiv_rn(0.01, dm), 1.0 / (ORDER + 1));
+  return fmin(fmin(mul_(100.0, h0), h1), span);
+}
+
+// ---------------------------------------------------------------------------
 // Warp helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }

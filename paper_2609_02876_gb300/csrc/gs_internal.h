@@ -50,6 +50,7 @@ struct FwdArgs {
   // save-time side step (plus its save state for the explicit methods).
   int stages;
   double* side_stg;
+  int control;  // 1: FP64 step control (GS_CONTROL_FP64)
   double save_t[MAX_SAVE_HOST];
 };
 

@@ -87,6 +87,7 @@ __device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bo
 struct Tsit5Method {
   static constexpr int ORDER = 5, ERR_ORDER = 4;  // solution order; lower order of the error estimate
   static constexpr bool kStages = true;           // records may store stage inputs
+  static constexpr bool kControl64 = true;        // record kernels with FP64 step control
   // Step of the lanes without work in a warp-collective unit (zero cotangent):
   // any value whose step stays finite.
   static constexpr double IDLE_H = 0.0;
@@ -241,6 +242,7 @@ struct Tsit5Method {
 };
 
 struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
+  static constexpr bool kControl64 = false;
   static constexpr int ORDER = 5, ERR_ORDER = 4;
   static constexpr bool kStages = true;
   template <class Pb, class R>
@@ -383,6 +385,7 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
 // Rosenbrock23 (FP64 only): second order, error estimate of order 2 (err^(-1/3)
 // controller), f at the accepted state carried to the next step.
 struct Ros23Method {
+  static constexpr bool kControl64 = false;
   static constexpr int ORDER = 2, ERR_ORDER = 2;
   static constexpr bool kStages = true;
   static constexpr double IDLE_H = 1.0;
@@ -524,6 +527,7 @@ struct Ros23Method {
 };
 
 struct Verner7Method {  // FP64 only
+  static constexpr bool kControl64 = false;
   static constexpr int ORDER = 7, ERR_ORDER = 6;
   static constexpr bool kStages = true;
   static constexpr double IDLE_H = 0.0;
@@ -684,8 +688,9 @@ constexpr bool stages_possible() {
 }
 
 // SAVES: save-time side steps run (for y_save, or for the stored side stages);
-// STAGES: the record stores stage inputs (k = 1).
-template <class M, class Pb, class R, bool SAVES, bool STAGES>
+// STAGES: the record stores stage inputs (k = 1); C64: FP64 step control
+// (GS_CONTROL_FP64: error norm, controller, starting step and step floor in FP64).
+template <class M, class Pb, class R, bool SAVES, bool STAGES, bool C64 = false>
 __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
   static_assert(!STAGES || (SAVES && M::kStages), "stored stages need side steps and a method that exposes stages");
   constexpr int D = Pb::D, NP = Pb::NP;
@@ -729,11 +734,13 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           k = got;
           bool fin = true;
           float yf[D], pf[NP], ff[D];
+          double yd[D], pd[NP];  // (FP64 step control: the inputs as given)
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const double v = a.params[q * n + k];
             p[q] = (R)v;
             pf[q] = (float)v;
+            pd[q] = v;
             fin = fin && isfinite(v);
           }
 #pragma unroll
@@ -741,6 +748,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
             const double v = a.y0[c * n + k];
             y[c] = (R)v;
             yf[c] = (float)v;
+            yd[c] = v;
             fin = fin && isfinite(v);
           }
           t = a.t0;
@@ -749,7 +757,13 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           rej = lastnf = lastsing = false;
           prev = -1;
           M::template start<Pb, R>(y, p, cy, ff);
-          h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
+          if constexpr (C64) {
+            double fd[D];
+            Pb::f(yd, pd, fd);
+            h = a.h0 > 0.0 ? a.h0 : initial_step_f64<Pb, M::ORDER>(yd, pd, fd, a.t0, t1, a.rtol, a.atol);
+          } else {
+            h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
+          }
           fin = fin && isfinite(h) && h > 0.0;
           ended = !fin;
           if (!fin) status = TRAJ_NONFINITE;
@@ -836,7 +850,12 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       }
       if (!is_side) {
         ++natt;
-        q = err_meansq<D>(e, y, yn, a.rtol, a.atol, rtf, atf);
+        // q: the mean square of the scaled error (fast control) or its root,
+        // err (FP64 control); either way q <= 1 accepts
+        if constexpr (C64)
+          q = err_norm_f64<D>(e, y, yn, a.rtol, a.atol);
+        else
+          q = err_meansq<D>(e, y, yn, a.rtol, a.atol, rtf, atf);
       }
     }
     if (SAVES && um == U_SIDE) {
@@ -883,14 +902,23 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       // rejection), rejected ones shrink by the same rule, x0.2 on a non-finite
       // error, x0.25 when the step's linear system is singular
       const bool nf = solved && !finite_nonneg(q);
-      float fac = !solved ? 0.25f : (nf ? 0.2f : ctrl_factor<M::ERR_ORDER>(q));
-      if (accept && rej) fac = fminf(fac, 1.0f);
-      h = mul_(h, to_d(fac));
+      bool under;
+      if constexpr (C64) {
+        double fac = !solved ? 0.25 : (nf ? 0.2 : ctrl_factor_f64<M::ERR_ORDER>(q));
+        if (accept && rej) fac = fmin(fac, 1.0);
+        h = mul_(h, fac);
+        under = fabs(h) < mul_(1e-14, fmax(1.0, fabs(t)));
+      } else {
+        float fac = !solved ? 0.25f : (nf ? 0.2f : ctrl_factor<M::ERR_ORDER>(q));
+        if (accept && rej) fac = fminf(fac, 1.0f);
+        h = mul_(h, to_d(fac));
+        // |h| < 1e-14 max(1, |t|), evaluated in FP32 (a threshold test, not arithmetic of the solution)
+        under = fabsf(to_f(h)) < 1e-14f * fmaxf(1.0f, fabsf(to_f(t)));
+      }
       rej = !accept;
       lastnf = !accept && nf;
       lastsing = !solved;
-      // |h| < 1e-14 max(1, |t|), evaluated in FP32 (a threshold test, not arithmetic of the solution)
-      if (fabsf(to_f(h)) < 1e-14f * fmaxf(1.0f, fabsf(to_f(t)))) {
+      if (under) {
         status = lastsing ? TRAJ_SINGULAR : (lastnf ? TRAJ_NONFINITE : TRAJ_DT_UNDERFLOW);
         ended = true;
       }
@@ -1448,6 +1476,20 @@ inline cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long 
 template <class M, class Pb, class R>
 inline cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)(((a.n_save + 1) & ~1) + a.segw * TPB_FWD) * sizeof(double);
+  if (a.control) {  // FP64 step control: Tsit5 without shared weights
+    if constexpr (M::kControl64 && !HasWeights<Pb>::value) {
+      if constexpr (stages_possible<M, Pb, R>()) {
+        if (a.stages)
+          return persistent_launch(record_kernel<M, Pb, R, true, true, true>, TPB_FWD, smem, a.n, s, &a);
+      } else {
+        if (a.stages) return cudaErrorInvalidValue;
+      }
+      if (a.y_save) return persistent_launch(record_kernel<M, Pb, R, true, false, true>, TPB_FWD, smem, a.n, s, &a);
+      return persistent_launch(record_kernel<M, Pb, R, false, false, true>, TPB_FWD, smem, a.n, s, &a);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if constexpr (stages_possible<M, Pb, R>()) {
     if (a.stages) return persistent_launch(record_kernel<M, Pb, R, true, true>, TPB_FWD, smem, a.n, s, &a);
   } else {

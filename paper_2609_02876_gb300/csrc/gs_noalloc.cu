@@ -78,6 +78,7 @@ extern "C" gs_status gs_solve_grad_noalloc(int problem_id, int64_t n, const doub
   gs_default_options(&o);
   if (opt) o = *opt;
   if (o.precision != GS_FP64 && o.precision != GS_FP32_MIXED) return GS_ERR_INVALID_ARG;
+  if (o.control != GS_CONTROL_FAST) return GS_ERR_INVALID_ARG;  // the default step control only
   const int method = o.method == GS_METHOD_AUTO ? (stiff ? GS_METHOD_RODAS5P : GS_METHOD_TSIT5) : o.method;
   if (method != GS_METHOD_TSIT5 || !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (o.ckpt_k < 0 || o.ckpt_k > KMAX_HOST || o.max_steps < 0 || !std::isfinite(o.h0) || o.h0 < 0)

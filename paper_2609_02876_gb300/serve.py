@@ -2,14 +2,22 @@
 
 A request is one ensemble: (problem, params (n, P), y0 (n, d), rtol), host
 arrays. The server keeps `slots` solve contexts (each its own device
-workspace and CUDA stream, driven by one host thread). Whenever a slot is
-free it takes the oldest waiting request and packs every other waiting
-request with the same (problem, rtol) behind it, up to `max_pack`
-trajectories, into ONE launch of the persistent record + reverse kernels;
-trajectories are independent, so each request's results are exactly those of
-solving it alone (tested). A batch is admitted only if the estimated record
-footprint of all batches in flight stays within `budget_bytes`; batches on
-different slots overlap on the device. Latency = completion - arrival.
+workspace and CUDA stream, driven by one host thread). Work is queued as
+items: a request of at most `max_chunk` trajectories is one item; a larger
+one is cut into chunks of `max_chunk` trajectories, its items queued in a
+second FIFO. Whenever a slot is free it takes, in this order:
+  - the oldest small request, packed with every other queued small request of
+    the same (problem, rtol) behind it, up to `max_pack` trajectories, into
+    ONE launch of the persistent record + reverse kernels;
+  - else the oldest chunk of a large request.
+So small requests pass large ones at chunk boundaries, and the chunks of the
+large requests run in arrival order, each request's chunks side by side on
+the free slots. Trajectories are independent, so each request's results are
+exactly those of solving it alone (tested). A launch is admitted only if the
+estimated record footprint of all launches in flight stays within
+`budget_bytes`; launches on different slots overlap on the device. Latency =
+completion of a request's last item - arrival. `max_chunk=None` turns the
+chunking off (every request one item, packed up to `max_pack`).
 
 Only argument marshalling and scheduling live here; every step of the
 solve runs in libgradsolve's kernels.
@@ -57,6 +65,7 @@ class Request:
     t_start: float = math.nan
     t_done: float = math.nan
     batch: int = -1
+    left: int = 0  # items not yet completed
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -72,6 +81,38 @@ class Request:
         return self.t_done - self.arrival
 
 
+@dataclass(eq=False)
+class Item:
+    """Trajectories [lo, hi) of one request: the unit the scheduler packs."""
+    req: Request
+    lo: int
+    hi: int
+
+    @property
+    def n(self) -> int:
+        return self.hi - self.lo
+
+    @property
+    def key(self):
+        return self.req.key
+
+
+def pack_batch(queue, limit):
+    """The oldest item of `queue` plus the queued items with its key behind it,
+    in arrival order, while the total stays within `limit` (an item larger than
+    the limit still runs, alone)."""
+    head = queue[0]
+    batch, total = [], 0
+    for it in list(queue):
+        if it.key != head.key:
+            continue
+        if batch and total + it.n > limit:
+            continue
+        batch.append(it)
+        total += it.n
+    return batch, total
+
+
 def _spec(problem):
     """Time span, save times and atol rule of a problem's workload."""
     wl = W.make(problem, 1)
@@ -81,17 +122,19 @@ def _spec(problem):
 
 class Server:
     def __init__(self, slots: int = 4, budget_bytes: int = 64 << 30, max_pack: int = 1 << 21,
-                 precision: str = "fp64", device: str = "cuda"):
+                 precision: str = "fp64", device: str = "cuda", max_chunk: int | None = None):
         self.slots = slots
         self.budget = budget_bytes
-        self.max_pack = max_pack
+        self.max_chunk = max_chunk
+        self.max_pack = max_pack if max_chunk is None else min(max_pack, max_chunk)
         self.precision = precision
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.clock0 = time.perf_counter()
         self._cv = threading.Condition()
-        self._queue: collections.deque[Request] = collections.deque()
+        self._small: collections.deque[Item] = collections.deque()
+        self._large: collections.deque[Item] = collections.deque()
         self._inflight_bytes = 0
         self._free = list(range(slots))
         self._closed = False
@@ -111,10 +154,22 @@ class Server:
         return time.perf_counter() - self.clock0
 
     def submit(self, req: Request) -> Request:
+        d, P = req.y0.shape[1], req.params.shape[1]
+        req.loss = np.empty(req.n)
+        req.params_bar = np.empty((req.n, P))
+        req.y0_bar = np.empty((req.n, d))
+        req.status = np.empty(req.n, np.int32)
+        req.t_start = math.nan
+        if self.max_chunk is not None and req.n > self.max_chunk:
+            items = [Item(req, lo, min(lo + self.max_chunk, req.n)) for lo in range(0, req.n, self.max_chunk)]
+            queue = self._large
+        else:
+            items, queue = [Item(req, 0, req.n)], self._small
+        req.left = len(items)
         with self._cv:
             if self._closed:
                 raise RuntimeError("server closed")
-            self._queue.append(req)
+            queue.extend(items)
             self._cv.notify_all()
         return req
 
@@ -130,25 +185,20 @@ class Server:
 
     # ---- scheduling -----------------------------------------------------
     def _take_batch(self):
-        """Oldest request plus queued ones with its key (FIFO within the key)."""
-        head = self._queue[0]
-        batch, total = [], 0
-        for r in list(self._queue):
-            if r.key != head.key:
-                continue
-            if batch and total + r.n > self.max_pack:
-                continue
-            batch.append(r)
-            total += r.n
-        return batch, total
+        """Small requests first (packed by key), else the oldest large-request chunk."""
+        if self._small:
+            return pack_batch(self._small, self.max_pack), self._small
+        return ([self._large[0]], self._large[0].n), self._large
 
     def _scheduler(self):
         with self._cv:
             while True:
-                while not self._closed and not (self._queue and self._free):
+                queued = bool(self._small or self._large)
+                while not self._closed and not (queued and self._free):
                     self._cv.wait()
-                if self._closed and not self._queue:
-                    if len(self._free) < self.slots:  # let the batches in flight finish first
+                    queued = bool(self._small or self._large)
+                if self._closed and not queued:
+                    if len(self._free) < self.slots:  # let the launches in flight finish first
                         self._cv.wait()
                         continue
                     for i in range(self.slots):
@@ -157,13 +207,13 @@ class Server:
                     return
                 if not self._free:
                     continue
-                batch, total = self._take_batch()
-                fp = record_footprint(batch[0].problem, total, batch[0].rtol)
+                (batch, total), queue = self._take_batch()
+                fp = record_footprint(batch[0].req.problem, total, batch[0].req.rtol)
                 if self._inflight_bytes > 0 and self._inflight_bytes + fp > self.budget:
                     self._cv.wait()  # wait for memory to free up (head of line)
                     continue
-                for r in batch:
-                    self._queue.remove(r)
+                for it in batch:
+                    queue.remove(it)
                 slot = self._free.pop(0)
                 self._inflight_bytes += fp
                 self._work[slot] = (batch, fp, self._batches)
@@ -187,11 +237,17 @@ class Server:
                 self._run_batch(batch, ctx, stream)
             finally:
                 t_done = self.now()
-                for r in batch:
-                    r.t_start, r.t_done, r.batch = t_start, t_done, bid
-                    r.done.set()
                 with self._cv:
-                    self.batch_log.append((bid, i, len(batch), sum(r.n for r in batch), t_start, t_done))
+                    for it in batch:
+                        r = it.req
+                        if not r.t_start <= t_start:
+                            r.t_start = t_start
+                        r.batch = bid
+                        r.left -= 1
+                        if r.left == 0:
+                            r.t_done = t_done
+                            r.done.set()
+                    self.batch_log.append((bid, i, len(batch), sum(it.n for it in batch), t_start, t_done))
                     self._inflight_bytes -= fp
                     self._free.append(i)
                     self._cv.notify_all()
@@ -200,8 +256,8 @@ class Server:
         problem, rtol = batch[0].key
         t0, t1, save_t, atol_fixed, ratio = _spec(problem)
         atol = rtol * ratio if ratio is not None else atol_fixed
-        params = np.concatenate([r.params for r in batch])
-        y0 = np.concatenate([r.y0 for r in batch])
+        params = np.concatenate([it.req.params[it.lo:it.hi] for it in batch])
+        y0 = np.concatenate([it.req.y0[it.lo:it.hi] for it in batch])
         with torch.cuda.stream(stream):
             P = torch.from_numpy(np.ascontiguousarray(params.T)).pin_memory().to(self.device, non_blocking=True)
             Y = torch.from_numpy(np.ascontiguousarray(y0.T)).pin_memory().to(self.device, non_blocking=True)
@@ -212,10 +268,13 @@ class Server:
             yb = res["y0_bar"].cpu().numpy()
             st = res["status"].cpu().numpy()
         o = 0
-        for r in batch:
-            s = slice(o, o + r.n)
-            r.loss, r.params_bar, r.y0_bar, r.status = loss[s], pb[:, s].T.copy(), yb[:, s].T.copy(), st[s]
-            o += r.n
+        for it in batch:
+            s, r = slice(o, o + it.n), it.req
+            r.loss[it.lo:it.hi] = loss[s]
+            r.params_bar[it.lo:it.hi] = pb[:, s].T
+            r.y0_bar[it.lo:it.hi] = yb[:, s].T
+            r.status[it.lo:it.hi] = st[s]
+            o += it.n
 
 
 def c4_stream(num: int, seed: int = 0, log2n=(6, 20), problems=("lorenz", "vdp", "robertson"),

@@ -54,3 +54,23 @@ def test_budget_admits_one_batch_at_a_time_when_tight():
     for (s0, e0), (s1, e1) in zip(spans, spans[1:]):
         assert s1 >= e0 - 1e-3, "batches overlapped although the budget admits one at a time"
     assert all((r.status == 0).all() for r in reqs)
+
+
+def test_chunked_large_requests_equal_results_alone():
+    """Requests larger than max_chunk run as several launches (chunks), small ones
+    pass them at chunk boundaries; every request's results still equal its own
+    solve alone bit for bit."""
+    reqs = serve.c4_stream(12, seed=9, log2n=(6, 12))
+    server = serve.Server(slots=3, budget_bytes=1 << 30, max_pack=1 << 13, max_chunk=700)
+    try:
+        serve.run_stream(server, reqs, rate=None)
+    finally:
+        server.close()
+    assert any(r.n > 700 for r in reqs)
+    assert len(server.batch_log) > len([r for r in reqs if r.n <= 700])
+    for r in reqs:
+        a = _alone(r)
+        assert (r.status == 0).all()
+        np.testing.assert_array_equal(r.loss, a["loss"])
+        np.testing.assert_array_equal(r.params_bar, a["params_bar"].T)
+        np.testing.assert_array_equal(r.y0_bar, a["y0_bar"].T)

@@ -222,17 +222,36 @@ def test_autograd_function_matches_oracle():
     assert_close(y0.grad.cpu().numpy(), o["y0_bar"], "y0_bar")
 
 
-def test_fp32_mixed_error_against_fp64_oracle():
-    """FP32 stages and adjoint, FP64 control. Its gradient error against the FP64
+# Bounds of the FP32-mixed gradient against the FP64 oracle on the run's own mesh,
+# normwise per trajectory vector (theta_bar, y0_bar): the FP32 unit roundoff 6e-8
+# carried through the adjoint recursion of S steps (Lorenz ~45, Van der Pol ~94 at
+# rtol 1e-6). Measured on 4096 trajectories: median 1.3e-6 / 1.0e-6, max 7.5e-6 /
+# 2.5e-5 (Van der Pol trajectories with a fast relaxation phase amplify it); the
+# bounds are 3-4x those figures, so a lost compensation or a component computed at
+# lower precision moves the median past them.
+FP32_MIXED_BOUND = {"lorenz": (4e-6, 3e-5), "vdp": (4e-6, 1e-4)}
+
+
+def fp32_mixed_errors(g_params_bar, g_y0_bar, o):
+    """Normwise relative error per trajectory; g_* are (n, P) / (n, d) arrays."""
+    a = np.concatenate([g_params_bar, g_y0_bar], 1)
+    b = np.concatenate([o["params_bar"], o["y0_bar"]], 1)
+    return np.abs(a - b).max(1) / np.abs(b).max(1)
+
+
+@pytest.mark.parametrize("name", ["lorenz", "vdp"])
+def test_fp32_mixed_error_against_fp64_oracle(name):
+    """FP32 stages and adjoint, FP64 t and h. Its gradient error against the FP64
     oracle (on the FP32 run's own mesh) is bounded by the FP32 roundoff carried
-    through ~50 steps of a Lorenz trajectory."""
-    wl = W.make("lorenz", 1024)
+    through the steps of a trajectory (FP32_MIXED_BOUND)."""
+    wl = W.make(name, 2048)
     rec, ysv, st = record(wl, precision="fp32_mixed")
     assert (st.cpu().numpy() == 0).all()
     g = reverse(rec, wl)
     o, _, _ = oracle_on_gpu_mesh(wl, rec)
-    e = np.abs(g["params_bar"].T - o["params_bar"]) / np.abs(o["params_bar"]).max(1, keepdims=True)
-    assert np.median(e) < 1e-4 and e.max() < 1e-2, (np.median(e), e.max())
+    e = fp32_mixed_errors(g["params_bar"].T, g["y0_bar"].T, o)
+    med, mx = FP32_MIXED_BOUND[name]
+    assert np.median(e) <= med and e.max() <= mx, (np.median(e), e.max())
 
 
 def test_full_size_sampled_parity():

@@ -31,23 +31,43 @@ def test_record_footprint_scales_with_size_and_tolerance():
 
 
 def take(queue, max_pack):
-    fake = types.SimpleNamespace(_queue=collections.deque(queue), max_pack=max_pack)
-    return serve.Server._take_batch(fake)
+    return serve.pack_batch(collections.deque(serve.Item(r, 0, r.n) for r in queue), max_pack)
 
 
 def test_packing_takes_the_oldest_key_in_arrival_order_up_to_the_limit():
     q = [req(0, "lorenz", 100, 1e-6), req(1, "vdp", 50, 1e-6), req(2, "lorenz", 300, 1e-6),
          req(3, "lorenz", 100, 1e-8), req(4, "lorenz", 700, 1e-6), req(5, "lorenz", 50, 1e-6)]
     batch, total = take(q, 1000)
-    assert [r.rid for r in batch] == [0, 2, 5]  # 4 would pass the limit; 1 and 3 have other keys
+    assert [it.req.rid for it in batch] == [0, 2, 5]  # 4 would pass the limit; 1 and 3 have other keys
     assert total == 450
     batch, total = take(q, 10 ** 6)
-    assert [r.rid for r in batch] == [0, 2, 4, 5] and total == 1150
+    assert [it.req.rid for it in batch] == [0, 2, 4, 5] and total == 1150
 
 
 def test_an_oversized_request_still_runs_alone():
     batch, total = take([req(7, "hires", 5000, 1e-6), req(8, "hires", 10, 1e-6)], 1000)
-    assert [r.rid for r in batch] == [7] and total == 5000
+    assert [it.req.rid for it in batch] == [7] and total == 5000
+
+
+def test_large_requests_are_chunked_and_small_ones_pass_them():
+    """Submitting splits a request beyond max_chunk into chunks queued in arrival
+    order; the scheduler's pick serves queued small requests first and then the
+    oldest chunk."""
+    fake = types.SimpleNamespace(max_chunk=1000, max_pack=1000, _small=collections.deque(),
+                                 _large=collections.deque(), _closed=False,
+                                 _cv=__import__("threading").Condition())
+    big, small, big2 = req(0, "lorenz", 2500, 1e-6), req(1, "vdp", 10, 1e-6), req(2, "lorenz", 1200, 1e-6)
+    for r in (big, small, big2):
+        serve.Server.submit(fake, r)
+    assert big.left == 3 and small.left == 1 and big2.left == 2
+    assert [(it.req.rid, it.lo, it.hi) for it in fake._large] == [(0, 0, 1000), (0, 1000, 2000), (0, 2000, 2500),
+                                                                  (2, 0, 1000), (2, 1000, 1200)]
+    (batch, total), q = serve.Server._take_batch(fake)
+    assert q is fake._small and [it.req.rid for it in batch] == [1] and total == 10
+    fake._small.clear()
+    (batch, total), q = serve.Server._take_batch(fake)
+    assert q is fake._large and [(it.req.rid, it.lo) for it in batch] == [(0, 0)] and total == 1000
+    assert big.params_bar.shape == (2500, 1) and big.y0_bar.shape == (2500, 2)  # results filled by slices
 
 
 def test_serving_stream_follows_its_distribution():
