@@ -415,24 +415,32 @@ def solve_grad_host(problem, params, y0, t0, t1, save_t, rtol, atol, *, shared_w
 
 class GsFunction(torch.autograd.Function):
     """y_save = ODE ensemble solve at the save times; backward = the discrete adjoint
-    on the recorded mesh (record in forward, replay sweep in backward)."""
+    on the recorded mesh (record in forward, replay sweep in backward). For the
+    shared-weight problems (LV UDE, neural Robertson) the FP32 weight vector is an
+    input too, and backward returns its gradient summed over the ensemble."""
 
     @staticmethod
-    def forward(ctx, params, y0, cfg):
+    def forward(ctx, params, y0, shared_w, cfg):
         rec, ysv, status = forward_record(cfg["problem"], params, y0, cfg["t0"], cfg["t1"], cfg["save_t"],
-                                          cfg["rtol"], cfg["atol"], **cfg.get("opts", {}))
+                                          cfg["rtol"], cfg["atol"], shared_w=shared_w, **cfg.get("opts", {}))
         ctx.rec = rec
-        ctx.save_for_backward(params, y0)
+        if shared_w is None:
+            ctx.save_for_backward(params, y0)
+        else:
+            ctx.save_for_backward(params, y0, shared_w)
         return ysv
 
     @staticmethod
     def backward(ctx, gy):
-        params, y0 = ctx.saved_tensors
-        g = reverse(ctx.rec, params, y0, y_save_bar=gy.contiguous())
-        return g["params_bar"], g["y0_bar"], None
+        saved = ctx.saved_tensors
+        params, y0 = saved[0], saved[1]
+        shared_w = saved[2] if len(saved) > 2 else None
+        g = reverse(ctx.rec, params, y0, y_save_bar=gy.contiguous(), shared_w=shared_w)
+        return g["params_bar"], g["y0_bar"], g.get("shared_w_bar"), None
 
 
-def odeint_ensemble(problem, params, y0, t0, t1, save_t, rtol, atol, **opts):
-    """Differentiable ensemble solve: returns y_save (n, n_save, d)."""
+def odeint_ensemble(problem, params, y0, t0, t1, save_t, rtol, atol, shared_w=None, **opts):
+    """Differentiable ensemble solve: returns y_save (n, n_save, d). `shared_w`
+    (FP32, the network weights of a shared-weight problem) may require grad."""
     cfg = dict(problem=problem, t0=t0, t1=t1, save_t=save_t, rtol=rtol, atol=atol, opts=opts)
-    return GsFunction.apply(params, y0, cfg)
+    return GsFunction.apply(params, y0, shared_w, cfg)

@@ -23,6 +23,15 @@ def shard_range(n: int, rank: int, world: int) -> tuple[int, int]:
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def sum_in_rank_order(parts) -> np.ndarray:
+    """The shards' shared-weight gradients added one after another in shard (rank)
+    order, in FP64: the reduction every rank performs on the gathered vectors."""
+    acc = np.zeros(np.asarray(parts[0]).shape, dtype=np.float64)
+    for p in parts:
+        acc += np.asarray(p, dtype=np.float64)
+    return acc
+
+
 def sum_shared_grad(local: np.ndarray, group=None) -> np.ndarray:
     """Deterministic all-reduce of a shared-weight gradient: every rank's vector is
     gathered and the vectors are added in rank order in FP64."""
@@ -32,10 +41,7 @@ def sum_shared_grad(local: np.ndarray, group=None) -> np.ndarray:
     world = dist.get_world_size(group)
     parts = [torch.empty_like(t) for _ in range(world)]
     dist.all_gather(parts, t, group=group)
-    acc = torch.zeros_like(t)
-    for p in parts:
-        acc += p
-    return acc.numpy()
+    return sum_in_rank_order([q.numpy() for q in parts])
 
 
 def max_over_ranks(x: float, group=None, device=None) -> float:

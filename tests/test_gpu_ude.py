@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2609_02876_gb300 import api, build
+from paper_2609_02876_gb300 import api, build, shard
 from paper_2609_02876_gb300 import workloads as W
 from tests.test_gpu_tsit5 import assert_close, dev
 
@@ -86,3 +86,55 @@ def test_ude_user_cotangent():
     assert_close(g["params_bar"].T, o["params_bar"], "params_bar", rtol=TOL)
     err = np.abs(g["shared_w_bar"] - o["w_bar"]).max() / np.abs(o["w_bar"]).max()
     assert err < TOL, err
+
+
+def test_autograd_returns_the_shared_weight_gradient():
+    """odeint_ensemble with the network weights as a differentiable input: a
+    user loss on the save states, backward through gs_reverse, gives the
+    per-trajectory (a, d) and y0 gradients and the ensemble-summed weight
+    gradient of the oracle's adjoint of the same loss on the GPU's mesh."""
+    wl, w = _setup(384)
+    p = dev(wl["params"]).requires_grad_(True)
+    y0 = dev(wl["y0"]).requires_grad_(True)
+    wr = w.clone().requires_grad_(True)
+    ysv = api.odeint_ensemble("lv_ude", p, y0, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                              shared_w=wr, precision="fp32_mixed")
+    target = torch.linspace(0.5, 1.5, ysv.numel(), dtype=torch.float64, device="cuda").reshape(ysv.shape)
+    loss = ((ysv - target) ** 2).sum()
+    loss.backward()
+    assert wr.grad is not None and wr.grad.dtype == torch.float32 and wr.grad.shape == w.shape
+    cot = 2 * (ysv.detach() - target).cpu().numpy()
+    rec, _, _ = _record(wl, w)
+    off, h = rec.export_mesh()
+    o = oracle.replay_grad("lv_ude", wl["params"], wl["y0"], wl["t0"], wl["t1"], wl["save_t"], off, h, w=wl["w"],
+                           ybar_save=cot)
+    assert_close(p.grad.cpu().numpy(), o["params_bar"], "params_bar", rtol=TOL)
+    assert_close(y0.grad.cpu().numpy(), o["y0_bar"], "y0_bar", rtol=TOL)
+    err = np.abs(wr.grad.cpu().numpy() - o["w_bar"]).max() / np.abs(o["w_bar"]).max()
+    assert err < TOL, err
+
+
+def test_sharded_weight_gradient_equals_unsharded():
+    """The multi-GPU partition of the UDE ensemble run as 4 shards one after another
+    on this GPU: each shard's gs_solve_grad weight gradient (FP32), added in shard
+    order in FP64 as the ranks' reduction does, equals the unsharded one to the
+    rounding of the FP32 results (each shard's sum and the whole one carry a
+    relative error of a few 1e-7 of the largest entry; bound 2e-6)."""
+    n = 6000
+    wl, w = _setup(n)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    whole = api.solve_grad("lv_ude", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], shared_w=w,
+                           layout="soa", precision="fp32_mixed")
+    parts, pbar = [], []
+    for r in range(4):
+        lo, hi = shard.shard_range(n, r, 4)
+        s = api.solve_grad("lv_ude", P[:, lo:hi].contiguous(), Y[:, lo:hi].contiguous(), wl["t0"], wl["t1"],
+                           wl["save_t"], wl["rtol"], wl["atol"], shared_w=w, layout="soa", precision="fp32_mixed")
+        parts.append(s["shared_w_bar"].cpu().numpy())
+        pbar.append(s["params_bar"].cpu().numpy())
+    # per-trajectory gradients do not depend on the partition
+    np.testing.assert_array_equal(np.concatenate(pbar, 1), whole["params_bar"].cpu().numpy())
+    summed = shard.sum_in_rank_order(parts)
+    ref = whole["shared_w_bar"].cpu().numpy().astype(np.float64)
+    err = np.abs(summed - ref).max() / np.abs(ref).max()
+    assert err < 2e-6, err
