@@ -675,7 +675,7 @@ def main():
     ap.add_argument("--forward-traj", type=int, default=1 << 24)
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-log2n-max", type=int, default=20)
-    ap.add_argument("--serve-chunk", type=int, default=1 << 18)
+    ap.add_argument("--serve-chunk", type=int, default=1 << 16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -129,6 +129,11 @@ typedef struct {
                            stages instead of recomputing them, with identical results),
                            else 0 */
   int control;          /* GS_CONTROL_FAST or GS_CONTROL_FP64 */
+  int record_stages;    /* gs_forward_record only: 1 lets the record also store every step's
+                           stage data when gs_solve_grad would (same rule: method, FP64, segment
+                           size, free memory), so that gs_reverse recomputes no stage; such a
+                           record cannot be refreshed (gs_record_refresh returns
+                           GS_ERR_INVALID_ARG). 0 (default): the compact record */
 } gs_options;
 
 /* A readable name for a status code (static storage, never NULL). */
@@ -192,7 +197,9 @@ gs_status gs_reverse(const gs_record* rec, const double* params, const double* y
  * as a fitting loop that reuses one record needs. The mesh, the save times and
  * the trajectory status words are unchanged; a step whose linear system is
  * singular at the new parameters leaves that trajectory's y(t1) NaN (its
- * gradient is then NaN). Enqueued on `stream`, not synchronised.
+ * gradient is then NaN). Enqueued on `stream`, not synchronised. A record that
+ * stores stage data (gs_options.record_stages) is refused with
+ * GS_ERR_INVALID_ARG: its stages belong to the recorded parameters.
  */
 gs_status gs_record_refresh(gs_record* rec, const double* params, const double* y0, const float* shared_w,
                             gs_stream stream);

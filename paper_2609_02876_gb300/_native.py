@@ -23,7 +23,8 @@ TRAJ_STATUS = {0: "ok", 1: "maxsteps", 2: "dt_underflow", 3: "nonfinite", 4: "si
 class GsOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("ckpt_k", C.c_int), ("max_steps", C.c_int64),
                 ("h0", C.c_double), ("step_counts", C.c_void_p), ("kernel_ms", C.POINTER(C.c_float)),
-                ("timeout_ms", C.c_double), ("record_info", C.POINTER(C.c_int32)), ("control", C.c_int)]
+                ("timeout_ms", C.c_double), ("record_info", C.POINTER(C.c_int32)), ("control", C.c_int),
+                ("record_stages", C.c_int)]
 
 
 class GsError(RuntimeError):

@@ -31,11 +31,12 @@ def problem_info(problem):
 
 
 def _opts(precision="fp64", method=None, ckpt_k=0, max_steps=0, h0=0.0, step_counts=None,
-          kernel_ms=None, timeout_ms=0.0, record_info=None, control="fast") -> N.GsOptions:
+          kernel_ms=None, timeout_ms=0.0, record_info=None, control="fast", record_stages=False) -> N.GsOptions:
     o = N.GsOptions()
     N.lib().gs_default_options(C.byref(o))
     o.precision = {"fp64": N.GS_FP64, "fp32_mixed": N.GS_FP32_MIXED}[precision]
     o.control = {"fast": N.GS_CONTROL_FAST, "fp64": N.GS_CONTROL_FP64}[control]
+    o.record_stages = 1 if record_stages else 0
     o.method = {None: N.GS_METHOD_AUTO, "tsit5": N.GS_METHOD_TSIT5, "rodas5p": N.GS_METHOD_RODAS5P,
                 "rosenbrock23": N.GS_METHOD_ROSENBROCK23, "verner7": N.GS_METHOD_VERNER7}[method]
     o.ckpt_k = int(ckpt_k)
@@ -441,6 +442,9 @@ class GsFunction(torch.autograd.Function):
 
 def odeint_ensemble(problem, params, y0, t0, t1, save_t, rtol, atol, shared_w=None, **opts):
     """Differentiable ensemble solve: returns y_save (n, n_save, d). `shared_w`
-    (FP32, the network weights of a shared-weight problem) may require grad."""
+    (FP32, the network weights of a shared-weight problem) may require grad.
+    The record keeps every step's stage data when the method and memory allow
+    (record_stages=True by default), so backward recomputes no stage."""
+    opts.setdefault("record_stages", True)
     cfg = dict(problem=problem, t0=t0, t1=t1, save_t=save_t, rtol=rtol, atol=atol, opts=opts)
     return GsFunction.apply(params, y0, shared_w, cfg)

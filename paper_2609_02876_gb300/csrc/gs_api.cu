@@ -240,6 +240,7 @@ struct Call {
   double timeout_ms;
   int32_t* record_info;
   int control;
+  int record_stages;
 };
 
 // Kernel launches by method.
@@ -310,6 +311,8 @@ gs_status check_common(int problem_id, int64_t n, const double* params, const do
   if (o.control != GS_CONTROL_FAST && o.control != GS_CONTROL_FP64) return GS_ERR_INVALID_ARG;
   if (o.control == GS_CONTROL_FP64 && (method != GS_METHOD_TSIT5 || c->pi.n_shared > 0)) return GS_ERR_INVALID_ARG;
   c->control = o.control;
+  if (o.record_stages != 0 && o.record_stages != 1) return GS_ERR_INVALID_ARG;
+  c->record_stages = o.record_stages;
   if (method == GS_METHOD_TSIT5 && !tsit5_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_RODAS5P && !rodas_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
   if (method == GS_METHOD_ROSENBROCK23 && !ros23_supports(problem_id, o.precision)) return GS_ERR_INVALID_ARG;
@@ -750,7 +753,7 @@ gs_status gs_forward_record(int problem_id, int64_t n, const double* params, con
   c.timeout_ms = 0.0;  // the record handle owns the work: wait for it
   gs_record* r = new (std::nothrow) gs_record();
   if (!r) return GS_ERR_OOM;
-  st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol);
+  st = setup_record(r, c, n, t0, t1, save_t, n_save, rtol, atol, c.record_stages == 1);
   if (st != GS_OK) { destroy(r); return st; }
   cudaStream_t s = (cudaStream_t)stream;
   if (n > 0) {
@@ -822,6 +825,7 @@ gs_status gs_record_refresh(gs_record* rec, const double* params, const double* 
   ProblemInfo pi;
   problem_info(rec->problem, &pi);
   if (pi.n_shared > 0 && !shared_w) return GS_ERR_INVALID_ARG;
+  if (rec->stages) return GS_ERR_INVALID_ARG;  // its stored stage data would go stale
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != rec->device) return GS_ERR_INVALID_ARG;

@@ -89,6 +89,11 @@ constexpr unsigned long long DBITS_INF = 0x7ff0000000000000ull;  // +inf
 __device__ __forceinline__ bool le_one(double q) { return dbits(q) <= DBITS_ONE; }      // q >= 0: q <= 1, NaN false
 __device__ __forceinline__ bool finite_nonneg(double q) { return dbits(q) < DBITS_INF; }  // q >= 0 finite
 __device__ __forceinline__ bool positive(double q) { return dbits(q) != 0ull && dbits(q) < 0x8000000000000000ull; }
+__device__ __forceinline__ bool finite_d(double x) { return abs_bits(x) < DBITS_INF; }  // not inf or NaN
+
+// The loss sum_s ||y(t_s)||^2 of one trajectory, accumulated in FP64.
+__device__ __forceinline__ double acc_loss(double loss, double v) { return add_(loss, v); }
+__device__ __forceinline__ double acc_loss(double loss, float v) { return add_(loss, to_d(v)); }
 
 template <class R>
 __device__ __forceinline__ R to_r(double x);

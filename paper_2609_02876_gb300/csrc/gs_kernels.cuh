@@ -54,6 +54,7 @@ constexpr int TPB_FWD = 128;
 constexpr int TPB_REV = 128;
 
 
+
 enum : int { U_NONE = 0, U_RECOMP = 1, U_STEP = 2, U_SIDE = 3, U_DONE = 4, U_FAIL = 5 };
 
 __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -78,7 +79,7 @@ __device__ __forceinline__ void unit_cotangent(const RevArgs& a, long long k, bo
     }
     cv[c] = active ? (side ? cs : lam[c]) : R(0);
   }
-  if (!USER_COT && active && side) loss = add_(loss, to_d(l2));
+  if (!USER_COT && active && side) loss = acc_loss(loss, l2);
 }
 
 // ---------------------------------------------------------------------------
@@ -88,6 +89,7 @@ struct Tsit5Method {
   static constexpr int ORDER = 5, ERR_ORDER = 4;  // solution order; lower order of the error estimate
   static constexpr bool kStages = true;           // records may store stage inputs
   static constexpr bool kControl64 = true;        // record kernels with FP64 step control
+  static constexpr int REV_MINB_F32 = 8, REV_MINB_STAGES = 6;  // reverse-sweep register caps (see rev_min_blocks)
   // Step of the lanes without work in a warp-collective unit (zero cotangent):
   // any value whose step stays finite.
   static constexpr double IDLE_H = 0.0;
@@ -243,6 +245,7 @@ struct Tsit5Method {
 
 struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
   static constexpr bool kControl64 = false;
+  static constexpr int REV_MINB_F32 = 0, REV_MINB_STAGES = 0;
   static constexpr int ORDER = 5, ERR_ORDER = 4;
   static constexpr bool kStages = true;
   template <class Pb, class R>
@@ -386,6 +389,7 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
 // controller), f at the accepted state carried to the next step.
 struct Ros23Method {
   static constexpr bool kControl64 = false;
+  static constexpr int REV_MINB_F32 = 0, REV_MINB_STAGES = 0;
   static constexpr int ORDER = 2, ERR_ORDER = 2;
   static constexpr bool kStages = true;
   static constexpr double IDLE_H = 1.0;
@@ -528,6 +532,7 @@ struct Ros23Method {
 
 struct Verner7Method {  // FP64 only
   static constexpr bool kControl64 = false;
+  static constexpr int REV_MINB_F32 = 0, REV_MINB_STAGES = 0;
   static constexpr int ORDER = 7, ERR_ORDER = 6;
   static constexpr bool kStages = true;
   static constexpr double IDLE_H = 0.0;
@@ -741,7 +746,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
             p[q] = (R)v;
             pf[q] = (float)v;
             pd[q] = v;
-            fin = fin && isfinite(v);
+            fin = fin && finite_d(v);
           }
 #pragma unroll
           for (int c = 0; c < D; ++c) {
@@ -749,7 +754,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
             y[c] = (R)v;
             yf[c] = (float)v;
             yd[c] = v;
-            fin = fin && isfinite(v);
+            fin = fin && finite_d(v);
           }
           t = a.t0;
           S = natt = slot = js = jp = je = 0;
@@ -764,7 +769,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           } else {
             h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
           }
-          fin = fin && isfinite(h) && h > 0.0;
+          fin = fin && positive(h) && finite_nonneg(h);
           ended = !fin;
           if (!fin) status = TRAJ_NONFINITE;
           if (a.k > 0) {
@@ -816,6 +821,17 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
     // the warp runs it once with all its busy lanes.
     __syncwarp();
     asm volatile("" : "+r"(um));
+    // a side step's length: in the FP64 form (bound by the FP64 pipe) the
+    // subtraction runs only in iterations that have a side step; the FP32-mixed
+    // kernels are bound by instruction issue, where a select is cheaper
+    double hx = h;
+    if constexpr (std::is_same<R, double>::value) {
+      if (SAVES && __any_sync(FULL_MASK, um == U_SIDE)) {
+        if (um == U_SIDE) hx = sub_(s_save[jp], tp);
+      }
+    } else {
+      hx = (SAVES && um == U_SIDE) ? s_save[jp] - tp : h;
+    }
     R yn[D], e[D];
     typename StageOf<M, Pb, R, STAGES>::type sd;  // stage data of this unit (stored-stage records)
     Carry next;
@@ -832,7 +848,6 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
 #pragma unroll
       for (int q2 = 0; q2 < NP; ++q2) pin[q2] = p[q2];
       const Carry cin = is_side ? cyp : cy;
-      const double hx = is_side ? s_save[jp] - tp : h;
       if constexpr (STAGES) {
         // the unit's stage data go out at once (a step's to its staging slot,
         // overwritten by the next trial if this one is rejected), so that they
@@ -1024,7 +1039,7 @@ __device__ __forceinline__ bool next_save(const RevArgs& a, const double* s_save
           lam[c] = add_(lam[c], to_r<R>(a.y_save_bar[((long long)js * D + c) * a.n + k]));
         } else {
           lam[c] = add_(lam[c], add_(yx[c], yx[c]));
-          loss = add_(loss, to_d(mul_(yx[c], yx[c])));
+          loss = acc_loss(loss, mul_(yx[c], yx[c]));
         }
       }
       --js;
@@ -1237,7 +1252,7 @@ __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
 // stage_segw<M, D>() doubles) and side_stg the side steps' ([save][payload][n]):
 // the units load them instead of recomputing the stages.
 template <class M, class Pb, class R, bool USER_COT, bool STAGES = false>
-__global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
+__device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
   constexpr int D = Pb::D, NP = Pb::NP;
   constexpr bool COLL = HasWeights<Pb>::value;
   using Acc = AccFor<Pb, R>;
@@ -1309,8 +1324,7 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
     typename StageOf<M, Pb, R, STAGES>::type sd;  // stored stage data of this unit (STAGES)
     if (k >= 0) {
       if (next_save<D, R, USER_COT>(a, s_save, k, js, tx, yx, lam, loss, us)) {
-        mode = U_SIDE;
-        uh = s_save[us] - tx;
+        mode = U_SIDE;  // (its length s - t is formed below, once per warp iteration)
         if constexpr (STAGES) {
           constexpr int SP = M::template side_payload<D>();
           const double* src = a.side_stg + (long long)us * SP * a.n + k;
@@ -1350,6 +1364,13 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
     }
 
     __syncwarp();
+    if constexpr (std::is_same<R, double>::value) {  // (as in the record kernel)
+      if (__any_sync(FULL_MASK, mode == U_SIDE)) {
+        if (mode == U_SIDE) uh = sub_(s_save[us], tx);
+      }
+    } else {
+      if (mode == U_SIDE) uh = s_save[us] - tx;
+    }
     const bool busy = (mode == U_STEP || mode == U_SIDE);
     if constexpr (STAGES) {
       if (busy && !M::template unit_stored<Pb, R, USER_COT, Acc>(a, k, mode, true, us, yx, uh, p, sd, lam, pacc, loss))
@@ -1375,6 +1396,39 @@ __global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
   if constexpr (COLL) {
     if (a.wpart) pacc.finish(a.wpart, (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
   }
+}
+
+// Minimum resident CTAs of 128 threads per SM requested from the compiler for
+// the k = 1 reverse sweep (0: no request, the compiler's own choice). A
+// request caps the registers per thread at 65536 / (128 x blocks) so that more
+// warps hide the latency of the dependent segment loads and arithmetic chains.
+// Measured at 2^24 Lorenz trajectories: the FP32-mixed sweep 3.4% faster at 8
+// blocks (64 registers) than at the compiler's 72, the FP64 stored-stage sweep
+// 1.2% faster at 6 (80) than at 122; the shared-weight kernels need more
+// registers than either cap and keep the compiler's choice.
+template <class M, class Pb, class R, bool STAGES>
+constexpr int rev_min_blocks() {
+  if constexpr (HasWeights<Pb>::value)
+    return 0;
+  else
+    return std::is_same<R, float>::value ? M::REV_MINB_F32 : (STAGES ? M::REV_MINB_STAGES : 0);
+}
+template <class M, class Pb, class R, bool USER_COT, bool STAGES = false>
+__global__ void __launch_bounds__(TPB_REV) reverse_k1_kernel(const RevArgs a) {
+  reverse_k1_body<M, Pb, R, USER_COT, STAGES>(a);
+}
+template <class M, class Pb, class R, bool USER_COT, bool STAGES, int MINB>
+__global__ void __launch_bounds__(TPB_REV, MINB) reverse_k1_kernel_mb(const RevArgs a) {
+  reverse_k1_body<M, Pb, R, USER_COT, STAGES>(a);
+}
+// The k = 1 reverse kernel of (M, Pb, R, USER_COT, STAGES), with its register cap.
+template <class M, class Pb, class R, bool USER_COT, bool STAGES = false>
+constexpr auto reverse_k1_entry() {
+  constexpr int mb = rev_min_blocks<M, Pb, R, STAGES>();
+  if constexpr (mb > 0)
+    return &reverse_k1_kernel_mb<M, Pb, R, USER_COT, STAGES, mb>;
+  else
+    return &reverse_k1_kernel<M, Pb, R, USER_COT, STAGES>;
 }
 
 // ---------------------------------------------------------------------------
@@ -1524,15 +1578,15 @@ inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
     if (a.stages) {
       if (a.k != 1 || a.segw != stage_segw<M, Pb::D>()) return cudaErrorInvalidValue;
       if (a.y_save_bar)
-        return persistent_launch(reverse_k1_kernel<M, Pb, R, true, true>, TPB_REV, smem, a.n, s, &a);
-      return persistent_launch(reverse_k1_kernel<M, Pb, R, false, true>, TPB_REV, smem, a.n, s, &a);
+        return persistent_launch(reverse_k1_entry<M, Pb, R, true, true>(), TPB_REV, smem, a.n, s, &a);
+      return persistent_launch(reverse_k1_entry<M, Pb, R, false, true>(), TPB_REV, smem, a.n, s, &a);
     }
   } else {
     if (a.stages) return cudaErrorInvalidValue;
   }
   if (a.k == 1) {
-    if (a.y_save_bar) return persistent_launch(reverse_k1_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a);
-    return persistent_launch(reverse_k1_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);
+    if (a.y_save_bar) return persistent_launch(reverse_k1_entry<M, Pb, R, true>(), TPB_REV, smem, a.n, s, &a);
+    return persistent_launch(reverse_k1_entry<M, Pb, R, false>(), TPB_REV, smem, a.n, s, &a);
   }
   if (a.y_save_bar) return persistent_launch(reverse_kernel<M, Pb, R, true>, TPB_REV, smem, a.n, s, &a);
   return persistent_launch(reverse_kernel<M, Pb, R, false>, TPB_REV, smem, a.n, s, &a);

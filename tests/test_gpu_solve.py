@@ -75,3 +75,32 @@ def test_forward_only_solve_without_saves_and_failed_trajectories():
     full = solve(wl)
     yf = s["y_final"].cpu().numpy()
     np.testing.assert_array_equal(np.delete(yf, 7, axis=1), np.delete(full["y_final"].cpu().numpy(), 7, axis=1))
+
+
+def test_forward_record_with_stored_stages():
+    """gs_forward_record with record_stages: the record keeps every step's stage
+    data, the reverse sweep reads them and returns the compact record's gradient
+    bit for bit; the mesh and forward mode are unchanged; refresh is refused
+    (its stored stages belong to the recorded parameters); autograd uses it."""
+    from paper_2609_02876_gb300 import _native as N
+    wl = W.make("lorenz", 3000)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    info = np.zeros(2, np.int32)
+    rs, _, _ = api.forward_record("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                  layout="soa", record_stages=True, record_info=info)
+    assert tuple(info) == (1, 1)
+    rc, _, _ = api.forward_record("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                  layout="soa")
+    gs, gc = api.reverse(rs, P, Y, layout="soa"), api.reverse(rc, P, Y, layout="soa")
+    for key in ("loss", "params_bar", "y0_bar"):
+        torch.testing.assert_close(gs[key], gc[key], rtol=0, atol=0)
+    for a, b in zip(rs.export_mesh(), rc.export_mesh()):
+        np.testing.assert_array_equal(a, b)
+    torch.testing.assert_close(api.forward_grad(rs, P, Y, wrt=("params",), layout="soa")["params_bar"],
+                               api.forward_grad(rc, P, Y, wrt=("params",), layout="soa")["params_bar"],
+                               rtol=0, atol=0)
+    with pytest.raises(N.GsError) as ei:
+        api.refresh(rs, P, Y, layout="soa")
+    assert ei.value.code == N.GS_ERR_INVALID_ARG
+    rs.free()
+    rc.free()
