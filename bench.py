@@ -70,15 +70,14 @@ STIFF = {"robertson", "hires", "nrob"}
 
 # DRAM bytes per accepted step, read + write, measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch of each kernel) on the first 2^20 trajectories of
-# the same FP64 workload (Lorenz: 45.15 accepted steps per trajectory; Robertson:
-# 101243901 accepted steps in all), per record layout; a launch's traffic grows in
-# proportion to its accepted steps.
-TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "compact"): (4625075712 + 71750656) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "record", "compact"): (66017280 + 2269651712) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "reverse", "stages"): (15005185536 + 89034752) / (45.15 * 2 ** 20),
-                    ("lorenz", "fp64", "record", "stages"): (1782274816 + 11522356736) / (45.15 * 2 ** 20),
-                    ("robertson", "fp64", "reverse", "stages"): (49914448640 + 67795200) / 101243901,
-                    ("robertson", "fp64", "record", "stages"): (3282266112 + 66818809344) / 101243901}
+# the same FP64 workload, stored-stage layout (Lorenz: 45.15 accepted steps per
+# trajectory; Robertson: 101243901 accepted steps in all); a launch's traffic grows
+# in proportion to its accepted steps. The Lorenz reverse sweep's writes are its
+# register spills (the kernel is capped at 80 registers).
+TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "stages"): (16687848448 + 998791168) / (45.15 * 2 ** 20),
+                    ("lorenz", "fp64", "record", "stages"): (1706418944 + 11498005760) / (45.15 * 2 ** 20),
+                    ("robertson", "fp64", "reverse", "stages"): (49572589824 + 67082496) / 101243901,
+                    ("robertson", "fp64", "record", "stages"): (3215133184 + 68319703296) / 101243901}
 
 # Nominal FMA lanes per SM per clock of this part (FP64 at 1/64 of FP32), for the
 # nominal peak printed beside the measured one.
