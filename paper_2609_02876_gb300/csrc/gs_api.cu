@@ -98,6 +98,7 @@ struct Counters {
   unsigned long long arena_top;
   int overflow;
   int any_failed;
+  int tc_error;  // a tensor-core product's completion wait ran out in the reverse sweep
 };
 
 }  // namespace
@@ -532,6 +533,7 @@ gs_status launch_reverse(const gs_record* r, const double* params, const float* 
   a.segw = r->segw;
   a.stages = r->stages;
   a.side_stg = r->stages ? r->side_stg : nullptr;
+  a.tc_error = &r->ctr->tc_error;
   cudaError_t e = cudaMemsetAsync(&r->ctr->work_rev, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   e = launch_reverse_m(r->method, r->problem, r->precision, a, s);
@@ -632,9 +634,12 @@ gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* pa
   if (c.kernel_ms) cudaEventRecord(r->ev[3], s);
   cudaError_t e = cudaMemcpyAsync(traj_status, r->status, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
+  e = cudaMemcpyAsync(&r->ctr_host->tc_error, &r->ctr->tc_error, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
   st = wait_stream(s, c.timeout_ms);
   if (st != GS_OK) return st;
   if (c.kernel_ms) cudaEventElapsedTime(&c.kernel_ms[1], r->ev[2], r->ev[3]);
+  if (r->ctr_host->tc_error) return GS_ERR_CUDA;
   return r->ctr_host->any_failed ? GS_ERR_TRAJ_FAILED : GS_OK;
 }
 

@@ -78,6 +78,7 @@ struct RevArgs {
   int k, segw;
   int stages;                // the record holds stage inputs (see FwdArgs)
   const double* side_stg;
+  int* tc_error;             // set when a tensor-core product's completion wait ran out (or nullptr)
   double save_t[MAX_SAVE_HOST];
 };
 

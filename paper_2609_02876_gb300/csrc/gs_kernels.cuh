@@ -49,6 +49,12 @@ template <class Pb, class = void>
 struct HasWeights : std::false_type {};
 template <class Pb>
 struct HasWeights<Pb, std::void_t<decltype(Pb::kWeights)>> : std::integral_constant<bool, Pb::kWeights> {};
+// Problems whose reverse-sweep units run CTA-collectively (all 128 lanes of a
+// CTA in lockstep: the tensor-core network of LvUdeCta).
+template <class Pb, class = void>
+struct CtaColl : std::false_type {};
+template <class Pb>
+struct CtaColl<Pb, std::void_t<decltype(Pb::kCta)>> : std::integral_constant<bool, Pb::kCta> {};
 
 constexpr int TPB_FWD = 128;
 constexpr int TPB_REV = 128;
@@ -1069,6 +1075,10 @@ struct WeightAcc<LvUdeWarp> {
   using type = UdeAcc;
 };
 template <>
+struct WeightAcc<LvUdeCta> {
+  using type = UdeAcc;
+};
+template <>
 struct WeightAcc<NeuralRobertson> {
   using type = NrAcc;
 };
@@ -1255,6 +1265,7 @@ template <class M, class Pb, class R, bool USER_COT, bool STAGES = false>
 __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
   constexpr int D = Pb::D, NP = Pb::NP;
   constexpr bool COLL = HasWeights<Pb>::value;
+  constexpr bool CTA = CtaColl<Pb>::value;  // units in lockstep across the CTA, not only the warp
   using Acc = AccFor<Pb, R>;
   extern __shared__ double smem[];
   const int ns = a.n_save;
@@ -1317,7 +1328,11 @@ __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
         }
       }
     }
-    if (!__any_sync(FULL_MASK, k >= 0 || !drained)) break;
+    if constexpr (CTA) {
+      if (!__syncthreads_or(k >= 0 || !drained)) break;
+    } else {
+      if (!__any_sync(FULL_MASK, k >= 0 || !drained)) break;
+    }
 
     int mode = U_NONE, us = 0;
     double uh = 0.0;
@@ -1396,6 +1411,7 @@ __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
   if constexpr (COLL) {
     if (a.wpart) pacc.finish(a.wpart, (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
   }
+  if constexpr (CTA) Pb::block_teardown(a.tc_error);
 }
 
 // Minimum resident CTAs of 128 threads per SM requested from the compiler for

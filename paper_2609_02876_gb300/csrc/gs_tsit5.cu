@@ -2,6 +2,17 @@
 // Lorenz, Van der Pol and the linear test problem, FP64 and FP32-mixed.
 #include "gs_kernels.cuh"
 
+// The LV UDE reverse sweep's network: 0 (default) the warp-collective form
+// (LvUdeWarp, mma.sync), 1 the CTA-collective form with the hidden layer on
+// tcgen05 (LvUdeCta). Both give the same gradients to FP32 rounding (the UDE
+// parity tests pass with either); measured at 2^18 trajectories the CTA form's
+// reverse sweep takes 45.9 ms against 15.7 ms, because its four warps must meet
+// at a CTA barrier and a tensor-memory round trip for each of the ~18
+// hidden-layer products of a unit.
+#ifndef GS_UDE_CTA
+#define GS_UDE_CTA 0
+#endif
+
 namespace gs {
 
 bool tsit5_supports(int problem, int precision) {
@@ -30,7 +41,11 @@ cudaError_t launch_tsit5_reverse(int problem, int precision, const RevArgs& a, c
     case 3: return rev_dispatch<Tsit5Method, VanDerPol, float>(a, s);
     case 8: return rev_dispatch<Tsit5Method, Linear2, double>(a, s);
     case 9: return rev_dispatch<Tsit5Method, Linear2, float>(a, s);
-    case 11: return rev_dispatch<Tsit5Method, LvUdeWarp, float>(a, s);  // warp-collective tensor-core network
+#if GS_UDE_CTA
+    case 11: return rev_dispatch<Tsit5Method, LvUdeCta, float>(a, s);  // CTA-collective network (tcgen05)
+#else
+    case 11: return rev_dispatch<Tsit5Method, LvUdeWarp, float>(a, s);  // warp-collective network (mma.sync)
+#endif
   }
   return cudaErrorInvalidValue;
 }

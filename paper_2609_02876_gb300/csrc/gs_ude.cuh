@@ -300,6 +300,231 @@ struct LvUdeWarp : LvUde {
   }
 };
 
+// ---------------------------------------------------------------------------
+// CTA-collective form of the network for the reverse sweep: the CTA's 128
+// lanes evaluate it together (lanes without work pass zeros), and the 16 x 16
+// hidden layer, forward (Z2 = H1 W2^T) and backward (GH1 = GZ2 W2), is ONE
+// [128 lanes x 16] x [16 x 16] product on the fifth-generation tensor cores
+// (tcgen05.mma, kind::tf32, M = 128, N = 16, two K = 8 steps; activations and
+// weights split hi + lo, the three products hi*hi + lo*hi + hi*lo accumulated
+// in FP32 in tensor memory for FP32 accuracy). Each lane writes its row of the
+// activation operand to shared memory in the canonical K-major layout (core
+// matrices of 8 rows x 16 bytes, no swizzle), one elected thread issues the
+// MMAs and commits them to an mbarrier, and each lane reads its own output row
+// back from tensor memory (TMEM lane = CTA lane). The weight-gradient
+// contraction keeps the warp MMAs of UdeAcc: its 16-row outputs are below the
+// tcgen05 minimum of M = 64.
+// ---------------------------------------------------------------------------
+struct UdeTc {
+  // Operand tiles: A hi / lo [128 x 16] (8 KB each); B hi / lo for the forward
+  // product (W2 as [n][k]) and the backward one (W2^T), 1 KB each.
+  __device__ __forceinline__ static unsigned char* tiles() {
+    __shared__ __align__(1024) unsigned char t[2 * 8192 + 4 * 1024];
+    return t;
+  }
+  __device__ __forceinline__ static unsigned long long* mbar() {
+    __shared__ __align__(8) unsigned long long m;
+    return &m;
+  }
+  __device__ __forceinline__ static uint32_t* tmem_slot() {
+    __shared__ uint32_t t;
+    return &t;
+  }
+  // per-thread parity of the mbarrier phase the next product completes
+  __device__ __forceinline__ static unsigned char* phase() {
+    __shared__ unsigned char ph[128];
+    return ph;
+  }
+  __device__ __forceinline__ static int* error() {
+    __shared__ int e;
+    return &e;
+  }
+  // byte offset of element (row, k) of a [rows x 16] FP32 operand: core matrices
+  // of 8 rows x 4 elements, 128 B apart along k (LBO), 512 B apart along rows (SBO)
+  __device__ __forceinline__ static int off(int row, int k) {
+    return (row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+  }
+  __device__ __forceinline__ static uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+  // shared-memory matrix descriptor: start >> 4, LBO 128 B, SBO 512 B, version 1, no swizzle
+  __device__ __forceinline__ static uint64_t desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+  }
+  // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = 16, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+  // Called by all 128 threads before the sweep (followed by a CTA barrier).
+  __device__ static void setup(const float* shared_w) {
+    unsigned char* t = tiles();
+    for (int i = threadIdx.x; i < 2 * 256; i += blockDim.x) {
+      const int q = i >> 8, n = (i >> 4) & 15, k = i & 15;
+      const float v = q == 0 ? shared_w[UDE_W2 + UDE_H * n + k] : shared_w[UDE_W2 + UDE_H * k + n];
+      const Tf32x2 sp = split_tf32(v);
+      *reinterpret_cast<uint32_t*>(t + 16384 + q * 2048 + off(n, k)) = sp.hi;
+      *reinterpret_cast<uint32_t*>(t + 16384 + q * 2048 + 1024 + off(n, k)) = sp.lo;
+    }
+    phase()[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+      *error() = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar())));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if ((threadIdx.x >> 5) == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(saddr(tmem_slot())));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  // Called by all 128 threads after the sweep.
+  __device__ static void teardown(int* err_out) {
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if ((threadIdx.x >> 5) == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(*tmem_slot()));
+    if (threadIdx.x == 0 && *error() && err_out) atomicExch(err_out, 1);
+  }
+  // out = in x B_q for this lane's row (in: 16 values), CTA-collective.
+  __device__ __forceinline__ static void product(const float (&in)[UDE_H], int q, float (&out)[UDE_H]) {
+    unsigned char* t = tiles();
+    const int row = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const Tf32x2 s0 = split_tf32(in[4 * c]), s1 = split_tf32(in[4 * c + 1]), s2 = split_tf32(in[4 * c + 2]),
+                   s3 = split_tf32(in[4 * c + 3]);
+      *reinterpret_cast<uint4*>(t + off(row, 4 * c)) = make_uint4(s0.hi, s1.hi, s2.hi, s3.hi);
+      *reinterpret_cast<uint4*>(t + 8192 + off(row, 4 * c)) = make_uint4(s0.lo, s1.lo, s2.lo, s3.lo);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot();
+    if (threadIdx.x == 0) {
+      const uint32_t ah = saddr(t), al = ah + 8192, bh = ah + 16384 + q * 2048, bl = bh + 1024;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {  // K = 16 as two K = 8 steps: the next two core-matrix columns
+        const uint32_t o = kk * 256;
+        const uint64_t dah = desc(ah + o), dal = desc(al + o), dbh = desc(bh + o), dbl = desc(bl + o);
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tmem), "l"(dah), "l"(dbh), "r"(IDESC), "r"(kk));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tmem), "l"(dal), "l"(dbh), "r"(IDESC), "r"(1));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tmem), "l"(dah), "l"(dbl), "r"(IDESC), "r"(1));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar())));
+    }
+    // wait for the commit (bounded: after ~1 s of polling the product is abandoned
+    // and the CTA's error flag set; the host then reports the launch as failed)
+    const uint32_t ph = phase()[row];
+    uint32_t done = 0;
+    for (int spin = 0; spin < (1 << 24) && !done; ++spin) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                   : "=r"(done)
+                   : "r"(saddr(mbar())), "r"(ph));
+    }
+    if (!done) *error() = 1;
+    phase()[row] = (unsigned char)(ph ^ 1u);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem + ((uint32_t)(row & ~31) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < UDE_H; ++j) out[j] = __uint_as_float(r[j]);
+    // (the next product's CTA barrier orders this lane's TMEM read before the
+    // next MMA; its operand tiles are free once the commit has arrived)
+  }
+};
+
+struct LvUdeCta : LvUde {
+  static constexpr bool kCta = true;  // the reverse sweep runs its units CTA-collectively
+  __device__ static void block_setup(const float* shared_w) {
+    LvUde::block_setup(shared_w);
+    UdeTc::setup(shared_w);
+  }
+  __device__ static void block_teardown(int* err) { UdeTc::teardown(err); }
+  // Forward pass of all lanes: leaves h1 and h2 in this lane's staging row and
+  // returns its network output and h2.
+  __device__ __forceinline__ static void forward_cta(float x, float y, float (&h2)[UDE_H], float (&nn)[2]) {
+    float* row = ude_stage() + (threadIdx.x & 31) * UDE_ROW;
+    const int swl = ude_sw(threadIdx.x & 31);
+    asm volatile("" ::: "memory");
+    const float* w = weights();
+    float h1[UDE_H];
+#pragma unroll
+    for (int j = 0; j < UDE_H; ++j)
+      h1[j] = tanh_f32(fmaf(w[UDE_W1 + 2 * j + 1], y, fmaf(w[UDE_W1 + 2 * j], x, w[UDE_B1 + j])));
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4)
+      *reinterpret_cast<float4*>(row + ((16 + j) ^ swl)) = make_float4(h1[j], h1[j + 1], h1[j + 2], h1[j + 3]);
+    float z[UDE_H];
+    UdeTc::product(h1, 0, z);
+#pragma unroll
+    for (int j = 0; j < UDE_H; ++j) h2[j] = tanh_f32(z[j] + w[UDE_B2 + j]);
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4)
+      *reinterpret_cast<float4*>(row + ((48 + j) ^ swl)) = make_float4(h2[j], h2[j + 1], h2[j + 2], h2[j + 3]);
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      float s = w[UDE_B3 + o];
+#pragma unroll
+      for (int j = 0; j < UDE_H; ++j) s = fmaf(w[UDE_W3 + UDE_H * o + j], h2[j], s);
+      nn[o] = s;
+    }
+  }
+  __device__ __forceinline__ static void f(const float (&y)[D], const float (&p)[NP], float (&o)[D]) {
+    float h2[UDE_H], nn[2];
+    forward_cta(y[0], y[1], h2, nn);
+    o[0] = fmaf(p[0], y[0], -nn[0]);
+    o[1] = fmaf(-p[1], y[1], nn[1]);
+  }
+  // VJP of all lanes (as LvUdeWarp::backprop_warp), leaving this lane's staging
+  // row holding [gz2 | h1 | gz1 | h2 | x, y, go] for the weight-gradient MMAs.
+  __device__ __forceinline__ static void backprop_cta(const float (&y)[D], const float (&p)[NP], const float (&v)[D],
+                                                      float (&yb)[D], float (&pb)[NP]) {
+    float* row = ude_stage() + (threadIdx.x & 31) * UDE_ROW;
+    const int swl = ude_sw(threadIdx.x & 31);
+    float h2[UDE_H], nn[2];
+    forward_cta(y[0], y[1], h2, nn);
+    const float* w = weights();
+    const float go0 = -v[0], go1 = v[1];  // f0 = a x - nn0, f1 = -d y + nn1
+    *reinterpret_cast<float4*>(row + (64 ^ swl)) = make_float4(y[0], y[1], go0, go1);
+    float gz2[UDE_H];
+#pragma unroll
+    for (int j = 0; j < UDE_H; ++j) {
+      const float gh = fmaf(w[UDE_W3 + j], go0, w[UDE_W3 + UDE_H + j] * go1);
+      gz2[j] = gh * fmaf(-h2[j], h2[j], 1.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4)
+      *reinterpret_cast<float4*>(row + (j ^ swl)) = make_float4(gz2[j], gz2[j + 1], gz2[j + 2], gz2[j + 3]);
+    float gh1[UDE_H];
+    UdeTc::product(gz2, 1, gh1);  // GH1 = GZ2 W2
+    float gx = 0.0f, gy = 0.0f;
+#pragma unroll
+    for (int j = 0; j < UDE_H; j += 4) {
+      const float4 hv = *reinterpret_cast<const float4*>(row + ((16 + j) ^ swl));
+      const float h1[4] = {hv.x, hv.y, hv.z, hv.w};
+      float z[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        z[u] = gh1[j + u] * fmaf(-h1[u], h1[u], 1.0f);
+        gx = fmaf(w[UDE_W1 + 2 * (j + u)], z[u], gx);
+        gy = fmaf(w[UDE_W1 + 2 * (j + u) + 1], z[u], gy);
+      }
+      *reinterpret_cast<float4*>(row + ((32 + j) ^ swl)) = make_float4(z[0], z[1], z[2], z[3]);
+    }
+    yb[0] = fmaf(p[0], v[0], gx);
+    yb[1] = fmaf(-p[1], v[1], gy);
+    pb[0] = fmaf(y[0], v[0], pb[0]);
+    pb[1] = fmaf(-y[1], v[1], pb[1]);
+  }
+};
+
 // Accumulator of the UDE reverse sweep: the per-trajectory (a, d) gradient
 // (compensated FP32, per lane) and the warp's shared-weight gradient in MMA
 // accumulator fragments:
@@ -327,9 +552,13 @@ struct UdeAcc {
   template <class Pb>
   __device__ __forceinline__ void vjp(const float (&y)[2], const float (&p)[2], const float (&v)[2],
                                       float (&yb)[2]) {
-    static_assert(std::is_same<Pb, LvUdeWarp>::value, "the UDE reverse sweep uses the warp-collective network");
+    static_assert(std::is_same<Pb, LvUdeWarp>::value || std::is_same<Pb, LvUdeCta>::value,
+                  "the UDE reverse sweep uses a collective form of the network");
     float x[2] = {0.0f, 0.0f};
-    LvUdeWarp::backprop_warp(y, p, v, yb, x);  // leaves the factor rows staged
+    if constexpr (std::is_same<Pb, LvUdeCta>::value)
+      LvUdeCta::backprop_cta(y, p, v, yb, x);  // leaves the factor rows staged
+    else
+      LvUdeWarp::backprop_warp(y, p, v, yb, x);
 #pragma unroll
     for (int q = 0; q < 2; ++q) th.u[q] = add_(th.u[q], x[q]);
     accumulate();

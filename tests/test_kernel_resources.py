@@ -12,11 +12,11 @@ import pytest
 from paper_2609_02876_gb300 import build as B
 
 
-def resources(src):
+def resources(src, extra=()):
     """{mangled kernel name: (registers, spill store bytes)} for one translation unit."""
     with tempfile.TemporaryDirectory() as tmp:
-        cmd = [B.nvcc()] + B.ARCH + B.FLAGS + ["-Xptxas", "-v", "-c", os.path.join(B.CSRC, src), "-o",
-                                              os.path.join(tmp, "k.o")]
+        cmd = [B.nvcc()] + B.ARCH + B.FLAGS + list(extra) + ["-Xptxas", "-v", "-c", os.path.join(B.CSRC, src),
+                                                             "-o", os.path.join(tmp, "k.o")]
         r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     out, cur, spill = {}, None, 0
@@ -78,3 +78,12 @@ def test_verner7_stored_stage_kernels():
     assert regs <= 128 and spill == 0  # 4 CTAs per SM
     regs, spill = find(res, "reverse_k1_kernel", "Verner7Method", "Lorenz", "EdLb0ELb1E")
     assert regs <= 170 and spill == 0  # 3 CTAs per SM
+
+
+def test_tcgen05_ude_variant_builds():
+    """The CTA-collective UDE network (hidden layer on tcgen05, TMEM accumulator)
+    is the compile-time alternative of the reverse sweep (GS_UDE_CTA=1): it must
+    keep compiling for sm_103a, within 3 CTAs' registers and without spills."""
+    res = resources("gs_tsit5.cu", ["-DGS_UDE_CTA=1"])
+    regs, spill = find(res, "reverse_k1_kernel", "Tsit5Method", "LvUdeCta", "EfLb0ELb0E")
+    assert regs <= 168 and spill == 0
