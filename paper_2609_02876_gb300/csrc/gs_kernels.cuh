@@ -249,9 +249,15 @@ struct Tsit5Method {
   }
 };
 
+#ifndef GS_RODAS_REV_MINB_STAGES
+#define GS_RODAS_REV_MINB_STAGES 0
+#endif
+#ifndef GS_VERN7_REV_MINB_STAGES
+#define GS_VERN7_REV_MINB_STAGES 0
+#endif
 struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay FP64
   static constexpr bool kControl64 = false;
-  static constexpr int REV_MINB_F32 = 0, REV_MINB_STAGES = 0;
+  static constexpr int REV_MINB_F32 = 0, REV_MINB_STAGES = GS_RODAS_REV_MINB_STAGES;
   static constexpr int ORDER = 5, ERR_ORDER = 4;
   static constexpr bool kStages = true;
   template <class Pb, class R>
@@ -538,7 +544,7 @@ struct Ros23Method {
 
 struct Verner7Method {  // FP64 only
   static constexpr bool kControl64 = false;
-  static constexpr int REV_MINB_F32 = 0, REV_MINB_STAGES = 0;
+  static constexpr int REV_MINB_F32 = 0, REV_MINB_STAGES = GS_VERN7_REV_MINB_STAGES;
   static constexpr int ORDER = 7, ERR_ORDER = 6;
   static constexpr bool kStages = true;
   static constexpr double IDLE_H = 0.0;
