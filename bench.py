@@ -258,7 +258,7 @@ def _normwise(a, b):
     return np.abs(a - b).max(1) / np.maximum(np.abs(b).max(1), 1e-300)
 
 
-def sample_accuracy(problem, wl, out, precision, method=None, control="fast", m=512, seed=12345,
+def sample_accuracy(problem, wl, out, precision, method=None, control="fast", m=4096, seed=12345,
                     converged=False, shared_w=None):
     """Gradient error of the timed run's own outputs (`out`, SoA device tensors of
     the whole ensemble) at m trajectories drawn at random from it, against the FP64
@@ -425,7 +425,7 @@ class Form:
 
 
 def leg(problem, n, peaks, precision="fp64", method=None, control="fast", steps=3, warmup=2, rtol=None,
-        acc_m=256, converged=False):
+        acc_m=1024, converged=False):
     """A secondary configuration: throughput, kernel times, roofline and sampled accuracy."""
     f = Form(problem, n, rtol=rtol, precision=precision, method=method, control=control)
     for _ in range(warmup):

@@ -1427,7 +1427,10 @@ __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
 // Measured at 2^24 Lorenz trajectories: the FP32-mixed sweep 3.4% faster at 8
 // blocks (64 registers) than at the compiler's 72, the FP64 stored-stage sweep
 // 1.2% faster at 6 (80) than at 122; the shared-weight kernels need more
-// registers than either cap and keep the compiler's choice.
+// registers than either cap and keep the compiler's choice. Capping the
+// Rodas5P (252 registers, 2 CTAs) and Verner7 (154, 3 CTAs) stored-stage sweeps
+// at 3 to 5 CTAs changed their time by under 2% (Robertson 2^20, Lorenz 2^23),
+// so they keep the compiler's choice too.
 template <class M, class Pb, class R, bool STAGES>
 constexpr int rev_min_blocks() {
   if constexpr (HasWeights<Pb>::value)
