@@ -22,15 +22,15 @@
 // replay, complex-step gradients, finite differences, invariants, Rosenbrock23's
 // stability function and error estimate, the neural term's weight derivatives;
 // the starting step and the controller against scipy's implementations of the
-// same textbook rules, with planted mistakes caught).
+// same textbook rules, for Tsit5 and for Verner7, with planted mistakes caught).
 //
 // Parity unpinned (no value outside this file fixes them; they only shape the
 // mesh, which the gradient treats as data): the end-of-span sliver 1e-12, the
 // quartered step after a singular linear system, the controller exponents of
-// the methods other than Tsit5 (1/(q+1) with q = 4 for Rodas5P, 2 for
-// Rosenbrock23, 6 for Verner7: the same function with the method's order),
-// and Rodas5P's coefficients beyond what its order conditions and stiff
-// accuracy fix.
+// the two Rosenbrock methods (1/(q+1) with q = 4 for Rodas5P, 2 for
+// Rosenbrock23: the function pinned for Tsit5 and Verner7, with the method's
+// order), and Rodas5P's coefficients beyond what its order conditions and
+// stiff accuracy fix.
 
 #include <algorithm>
 #include <cmath>

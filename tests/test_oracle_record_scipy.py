@@ -19,9 +19,15 @@ implementation that shares nothing with the oracle.
   7e-8 on Van der Pol), and the differences compound over ~200 steps to
   ~5e-8 in h. A changed control constant moves h by 1e-3 or more.
 
+The same driver run with Verner's 7(6) table (ten stages, the tenth used only
+by the sixth-order estimate; error_estimator_order 6, exponent -1/7, starting
+step of order 7) pins the oracle's Verner7 record: same counts, h to 3e-5
+(the seventh-order estimate cancels further, and Van der Pol's many rejected
+trials compound the rounding differences to 4e-6; measured).
+
 A plausible mistake in the oracle's control constants must fail these pins;
-the last test plants several, one at a time, in a copy of the oracle compiled
-here, and checks that each one is caught.
+the last tests plant several, one at a time, in a copy of the oracle compiled
+here, and check that each one is caught.
 """
 import contextlib
 import os
@@ -38,8 +44,10 @@ import oracle
 from paper_2609_02876_gb300 import workloads as W
 
 TSIT5 = oracle.METHOD_TSIT5
+VERN7 = oracle.METHOD_VERNER7
 H0_RTOL = 1e-12
 H_RTOL = 1e-6  # h agreement (see the module docstring)
+H_RTOL_V7 = 3e-5
 
 
 def _rhs(name, p):
@@ -73,34 +81,60 @@ def _tsit5_driver(order_for_first_step):
     return Tsit5Scipy
 
 
-def _scipy_mesh(name, p, y0, t0, t1, rtol, atol):
-    sol = solve_ivp(_rhs(name, p), (t0, t1), np.array(y0, dtype=np.float64), method=_tsit5_driver(5),
-                    rtol=rtol, atol=atol)
+def _vern7_driver():
+    tab = oracle.tableau(VERN7)
+
+    class Vern7Scipy(RungeKutta):
+        """scipy's RK driver with Verner's 7(6) table: all ten stages are computed
+        (b_10 = 0: the tenth enters only the estimate), then f(y_new) as K[-1],
+        which is the next step's first stage (the pair is not FSAL)."""
+        C = tab["c"]
+        A = tab["A"]
+        B = tab["b"]
+        E = np.append(tab["b"] - tab["bhat"], 0.0)
+        P = np.zeros((11, 1))
+        order = 7
+        error_estimator_order = 6
+        n_stages = 10
+
+        def __init__(self, fun, t0, y0, t_bound, **kw):
+            super().__init__(fun, t0, y0, t_bound, **kw)
+            self.h_abs = select_initial_step(self.fun, self.t, self.y, t_bound, np.inf, self.f, self.direction,
+                                             7, self.rtol, self.atol)
+
+    return Vern7Scipy
+
+
+def _scipy_mesh(name, p, y0, t0, t1, rtol, atol, method=TSIT5):
+    drv, per_att = (_tsit5_driver(5), 6) if method == TSIT5 else (_vern7_driver(), 10)
+    sol = solve_ivp(_rhs(name, p), (t0, t1), np.array(y0, dtype=np.float64), method=drv, rtol=rtol, atol=atol)
     assert sol.status == 0
     # nfev: f(y0), the starting-step probe (twice: scipy's own and the one above),
-    # then 6 evaluations per attempted step
-    return np.diff(sol.t), (sol.nfev - 3) // 6
+    # then per attempted step the stages after the first and f(y_new)
+    return np.diff(sol.t), (sol.nfev - 3) // per_att
 
 
-def _cases():
+def _cases(method=TSIT5):
     out = []
-    for name, rtol in (("lorenz", 1e-6), ("lorenz", 1e-4), ("vdp", 1e-6), ("vdp", 1e-3)):
+    sets = ((("lorenz", 1e-6), ("lorenz", 1e-4), ("vdp", 1e-6), ("vdp", 1e-3)) if method == TSIT5 else
+            (("lorenz", 1e-6), ("lorenz", 1e-4), ("lorenz", 1e-3), ("vdp", 1e-6)))
+    for name, rtol in sets:
         wl = W.make(name, 24, rtol=rtol, seed=3)
         out.append((name, wl))
     return out
 
 
-def _compare_meshes(cases):
+def _compare_meshes(cases, method=TSIT5):
     """Per trajectory: (equal accepted count, equal attempted count, max rel h diff
     over all steps but the last). Also returns the number of rejected trials seen."""
     res, rejected = [], 0
     for name, wl in cases:
         rec = oracle.record(name, wl["params"], wl["y0"], wl["t0"], wl["t1"], [], wl["rtol"], wl["atol"],
-                            method=TSIT5, want_saves=False)
+                            method=method, want_saves=False)
         for k in range(wl["params"].shape[0]):
             h_o = rec["h"][rec["offsets"][k]:rec["offsets"][k + 1]]
             h_s, att_s = _scipy_mesh(name, wl["params"][k], wl["y0"][k], wl["t0"], wl["t1"], wl["rtol"],
-                                     wl["atol"])
+                                     wl["atol"], method)
             rejected += int(rec["n_att"][k] - rec["S"][k])
             if h_o.size != h_s.size:
                 res.append((False, False, np.inf))
@@ -142,6 +176,15 @@ def test_accepted_mesh_equals_scipy_rk_driver_with_tsit5_table():
     assert rejected >= 20, rejected  # the cases exercise the rejection path and its cap
     assert same_s == 1.0 and same_att == 1.0, (same_s, same_att)
     assert worst <= H_RTOL, worst
+
+
+def test_verner7_accepted_mesh_equals_scipy_rk_driver_with_verner_table():
+    res, rejected = _compare_meshes(_cases(VERN7), VERN7)
+    same = all(r[0] and r[1] for r in res)
+    worst = max(r[2] for r in res)
+    assert rejected >= 50, rejected
+    assert same, [i for i, r in enumerate(res) if not (r[0] and r[1])]
+    assert worst <= H_RTOL_V7, worst
 
 
 # ----------------------------------------------------------------------------- planted mistakes
@@ -196,3 +239,19 @@ def test_planted_control_mistake_fails_the_scipy_pins(old, new):
         h0 = oracle.initial_step("lorenz", wl["params"][0], wl["y0"][0], 0.0, 1.0, wl["rtol"], wl["atol"], order=5)
         h0_ok = abs(h0 - ref) <= H0_RTOL * ref
     assert not (mesh_ok and h0_ok), f"planted mistake not detected: {new}"
+
+
+VERN7_MUTANTS = [
+    # Verner7's controller exponent from its solution order (-1/8) instead of its estimate's (-1/7)
+    ("method == M_VERN7 ? 6 : 4", "method == M_VERN7 ? 7 : 4"),
+    # Verner7's starting step with the estimate's order 6 instead of the solution's 7
+    ("method == M_VERN7 ? 7 : 5", "method == M_VERN7 ? 6 : 5"),
+]
+
+
+@pytest.mark.parametrize("old,new", VERN7_MUTANTS)
+def test_planted_verner7_control_mistake_fails_the_scipy_pin(old, new):
+    with _mutant_oracle(old, new):
+        res, _ = _compare_meshes(_cases(VERN7)[:2], VERN7)
+    worst = max(r[2] for r in res)
+    assert not (all(r[0] and r[1] for r in res) and worst <= H_RTOL_V7), f"planted mistake not detected: {new}"
