@@ -83,11 +83,14 @@ enum { GS_FP64 = 0, GS_FP32_MIXED = 1 };
  *    ratio e_c / (atol + rtol max(|y_c|, |ynew_c|)) to FP32 accuracy, squares
  *    summed in FP64; controller factor and starting step in FP32 with the
  *    hardware log2/exp2. FP32-mixed: the whole norm in FP32.
- *  GS_CONTROL_FP64: norm, controller (0.9 err^(-1/(q+1)) clamped to [0.2, 10],
- *    with pow), starting step and the step-size floor test all in FP64, as a
- *    plain CPU implementation writes them; the recorded mesh then follows that
- *    implementation's to rounding. Tsit5 only (no shared-weight problems);
- *    other methods return GS_ERR_INVALID_ARG. */
+ *  GS_CONTROL_FP64: norm, accept test, controller (0.9 err^(-1/(q+1))
+ *    clamped to [0.2, 10]), starting step and the step-size floor test all in
+ *    FP64 arithmetic: reciprocals and the controller's root to about 1e-14
+ *    and 1e-12 relative (single-precision estimates refined by FP64 Newton
+ *    steps), the starting step with IEEE division, square root and pow. The
+ *    recorded mesh then follows a plain CPU implementation's to the rounding
+ *    of the stage sums. Tsit5 only (no shared-weight problems); other methods
+ *    return GS_ERR_INVALID_ARG. */
 enum { GS_CONTROL_FAST = 0, GS_CONTROL_FP64 = 1 };
 
 /* One-step methods (paper Sec. 3.2): Tsit5 (Tsitouras 2011) for non-stiff

@@ -35,9 +35,6 @@ bool problem_info(int pid, ProblemInfo* out) {
   return false;
 }
 
-// Doubles per record segment [prev, t_start, y_start[d], h[k]], rounded up to a
-// 16-byte multiple for vector stores.
-int segw_of(int d, int k) { return ((2 + d + k) + 1) & ~1; }
 
 // Expected accepted steps per trajectory at rtol 1e-6, used for the first arena
 // size and the choice of the record layout; an underestimate costs one rerun.

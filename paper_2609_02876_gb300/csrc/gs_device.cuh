@@ -975,34 +975,74 @@ __device__ __forceinline__ double initial_step_f32(const float (&y0)[Pb::D], con
 }
 
 // ---------------------------------------------------------------------------
-// FP64 step control (GS_CONTROL_FP64): the error norm, the controller factor
-// and the starting step evaluated in FP64 in the order of the plain textbook
-// form (the paper's Sec. 2.1 norm and accept test; Hairer, Norsett & Wanner I,
-// Sec. II.4 for the starting step), with IEEE division, square root and the
-// library pow. The mesh it records follows a plain CPU evaluation of the same
-// rule up to the rounding of the stage arithmetic.
+// FP64 step control (GS_CONTROL_FP64): the error norm, the accept test, the
+// controller factor and the starting step evaluated in FP64 (the paper's
+// Sec. 2.1 norm and accept test; Hairer, Norsett & Wanner I, Sec. II.4 for the
+// starting step). The record works with the mean square m of the scaled error
+// instead of err = sqrt(m): the accept test is the exact equivalent of
+// sqrt(m) <= 1. Reciprocals and the controller's root come from
+// single-precision estimates refined by one FP64 Newton step, to about 1e-14
+// and 1e-12 relative: far below the ~1e-7 relative difference that the
+// rounding of the stage sums already makes in the error estimate of two codes
+// (the error estimate cancels), so the mesh follows a plain CPU evaluation of
+// the same rule up to that rounding.
 // ---------------------------------------------------------------------------
 
-// err = sqrt((1/D) sum_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2); accept iff err <= 1.
+// 1/x for 1e-30 < |x| < 1e30: the correctly rounded single-precision
+// reciprocal (relative error <= 2^-24) and one Newton step x0 + x0 (1 - x x0),
+// which squares the relative error; IEEE division outside that range.
+__device__ __forceinline__ double rcp_f64(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return __ddiv_rn(1.0, x);
+  const double x0 = (double)__frcp_rn((float)x);
+  return fma_(x0, fma_(-x, x0, 1.0), x0);
+}
+
+// m = (1/D) sum_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2 (err = sqrt(m)).
 template <int D, class R>
-__device__ __forceinline__ double err_norm_f64(const R (&e)[D], const R (&y)[D], const R (&yn)[D], double rtol,
-                                               double atol) {
+__device__ __forceinline__ double err_meansq_f64(const R (&e)[D], const R (&y)[D], const R (&yn)[D], double rtol,
+                                                 double atol) {
   double s = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const double sc = add_(atol, mul_(rtol, max_abs(to_d(y[c]), to_d(yn[c]))));
-    const double r = __ddiv_rn(to_d(e[c]), sc);
-    s = add_(s, mul_(r, r));
+    const double r = mul_(to_d(e[c]), rcp_f64(sc));
+    s = fma_(r, r, s);
   }
-  return __dsqrt_rn(__ddiv_rn(s, (double)D));
+  return mul_(s, 1.0 / D);
 }
 
-// clamp(0.9 err^(-1/(Q+1)), 0.2, 10); err = 0 gives 10.
+// sqrt(m) <= 1 with sqrt correctly rounded: m <= 1 + 2^-52 (the square root of
+// the next double after 1 rounds back to 1; of the one after that, it does not).
+// NaN rejects.
+__device__ __forceinline__ bool rms_le_one(double m) { return dbits(m) <= DBITS_ONE + 1ull; }
+
+template <int K>
+__device__ __forceinline__ double ipow_(double y) {  // y^K by repeated squaring
+  if constexpr (K == 1)
+    return y;
+  else if constexpr (K % 2 == 0) {
+    const double h = ipow_<K / 2>(y);
+    return mul_(h, h);
+  } else
+    return mul_(ipow_<K - 1>(y), y);
+}
+
+// Controller factor from the mean square m: clamp(0.9 m^(-1/K), 0.2, 10), K =
+// 2(Q+1), i.e. 0.9 err^(-1/(Q+1)); m = 0 gives 10. m^(-1/K) is the positive
+// root of g(y) = m y^K - 1: Newton's method, y <- y + y (1 - m y^K) / K, from a
+// single-precision estimate (relative error ~3e-7); the step squares the error
+// and scales it by about (K+1)/2, to ~5e-13 (checked over m in [1e-12, 1e7]).
+// Outside [1e-30, 1e30] the factor is clamped whatever m is, so m is held to
+// that range first.
 template <int Q>
-__device__ __forceinline__ double ctrl_factor_f64(double err) {
-  if (!(err > 0.0)) return 10.0;
-  const double f = mul_(0.9, pow(err, -1.0 / (Q + 1)));
-  return fmin(10.0, fmax(0.2, f));
+__device__ __forceinline__ double ctrl_factor_ms_f64(double m) {
+  constexpr int K = 2 * (Q + 1);
+  if (!(m > 0.0)) return 10.0;
+  const double mc = fmin(fmax(m, 1e-30), 1e30);
+  double y = (double)exp2f(log2f((float)mc) * (-1.0f / K));
+  y = fma_(y, mul_(fma_(-mc, ipow_<K>(y), 1.0), 1.0 / K), y);
+  return fmin(10.0, fmax(0.2, mul_(0.9, y)));
 }
 
 // RMS of v_c / sc_c.

@@ -708,7 +708,7 @@ constexpr bool stages_possible() {
 // STAGES: the record stores stage inputs (k = 1); C64: FP64 step control
 // (GS_CONTROL_FP64: error norm, controller, starting step and step floor in FP64).
 template <class M, class Pb, class R, bool SAVES, bool STAGES, bool C64 = false>
-__global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
+__device__ __forceinline__ void record_body(const FwdArgs& a) {
   static_assert(!STAGES || (SAVES && M::kStages), "stored stages need side steps and a method that exposes stages");
   constexpr int D = Pb::D, NP = Pb::NP;
   using Carry = typename M::template Carry<Pb, R>;
@@ -774,12 +774,16 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
           rej = lastnf = lastsing = false;
           prev = -1;
           M::template start<Pb, R>(y, p, cy, ff);
-          if constexpr (C64) {
+          if (a.h0 > 0.0) {
+            h = a.h0;
+          } else if (a.h0_pre) {
+            h = a.y_final[k];  // the starting-step pass's result (this slot is rewritten when k ends)
+          } else if constexpr (C64) {
             double fd[D];
             Pb::f(yd, pd, fd);
-            h = a.h0 > 0.0 ? a.h0 : initial_step_f64<Pb, M::ORDER>(yd, pd, fd, a.t0, t1, a.rtol, a.atol);
+            h = initial_step_f64<Pb, M::ORDER>(yd, pd, fd, a.t0, t1, a.rtol, a.atol);
           } else {
-            h = a.h0 > 0.0 ? a.h0 : initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
+            h = initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
           }
           fin = fin && positive(h) && finite_nonneg(h);
           ended = !fin;
@@ -877,10 +881,10 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       }
       if (!is_side) {
         ++natt;
-        // q: the mean square of the scaled error (fast control) or its root,
-        // err (FP64 control); either way q <= 1 accepts
+        // q: the mean square of the scaled error, in the fast control's FP32
+        // form or in FP64; q <= 1 (FP64: sqrt(q) <= 1) accepts
         if constexpr (C64)
-          q = err_norm_f64<D>(e, y, yn, a.rtol, a.atol);
+          q = err_meansq_f64<D>(e, y, yn, a.rtol, a.atol);
         else
           q = err_meansq<D>(e, y, yn, a.rtol, a.atol, rtf, atf);
       }
@@ -893,7 +897,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       ++jp;
     }
     const bool trial = (um == U_STEP);
-    const bool accept = trial && solved && le_one(q);  // q >= 0; NaN rejects
+    const bool accept = trial && solved && (C64 ? rms_le_one(q) : le_one(q));  // q >= 0; NaN rejects
     if (accept) {
       const double tn = last ? t1 : tsum;
       if (SAVES) {
@@ -931,7 +935,7 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       const bool nf = solved && !finite_nonneg(q);
       bool under;
       if constexpr (C64) {
-        double fac = !solved ? 0.25 : (nf ? 0.2 : ctrl_factor_f64<M::ERR_ORDER>(q));
+        double fac = !solved ? 0.25 : (nf ? 0.2 : ctrl_factor_ms_f64<M::ERR_ORDER>(q));
         if (accept && rej) fac = fmin(fac, 1.0);
         h = mul_(h, fac);
         under = fabs(h) < mul_(1e-14, fmax(1.0, fabs(t)));
@@ -1008,6 +1012,69 @@ __global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
       k = -1;
     }
   }
+}
+
+// Starting steps of all trajectories in one pass, before the record kernel
+// (problems without shared weights): y_final[k] = the h the record's refill
+// would compute for trajectory k, by the same function and inputs. In the
+// record this is per-trajectory code that one or two lanes of a warp run while
+// the others wait; here every lane computes one.
+template <class M, class Pb, class R, bool C64>
+__global__ void __launch_bounds__(256) init_step_kernel(const FwdArgs a) {
+  constexpr int D = Pb::D, NP = Pb::NP;
+  using Carry = typename M::template Carry<Pb, R>;
+  const long long n = a.n;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    R y[D], p[NP];
+    float yf[D], pf[NP], ff[D];
+    double yd[D], pd[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const double v = a.params[q * n + k];
+      p[q] = (R)v;
+      pf[q] = (float)v;
+      pd[q] = v;
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const double v = a.y0[c * n + k];
+      y[c] = (R)v;
+      yf[c] = (float)v;
+      yd[c] = v;
+    }
+    double h;
+    if constexpr (C64) {
+      double fd[D];
+      Pb::f(yd, pd, fd);
+      h = initial_step_f64<Pb, M::ORDER>(yd, pd, fd, a.t0, a.t1, a.rtol, a.atol);
+    } else {
+      Carry cy;
+      M::template start<Pb, R>(y, p, cy, ff);
+      h = initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, a.t1, a.rtol, a.atol);
+    }
+    a.y_final[k] = h;
+  }
+}
+
+template <class M, class Pb, class R, bool SAVES, bool STAGES, bool C64 = false>
+__global__ void __launch_bounds__(TPB_FWD) record_kernel(const FwdArgs a) {
+  record_body<M, Pb, R, SAVES, STAGES, C64>(a);
+}
+template <class M, class Pb, class R, bool SAVES, bool STAGES, bool C64, int MINB>
+__global__ void __launch_bounds__(TPB_FWD, MINB) record_kernel_mb(const FwdArgs a) {
+  record_body<M, Pb, R, SAVES, STAGES, C64>(a);
+}
+#ifndef GS_FWD_C64_MINB
+#define GS_FWD_C64_MINB 0
+#endif
+// The record kernel of (M, Pb, R, SAVES, STAGES, C64); the FP64-control forms
+// with a register cap of GS_FWD_C64_MINB resident CTAs per SM (0: none).
+template <class M, class Pb, class R, bool SAVES, bool STAGES, bool C64>
+constexpr auto record_entry() {
+  if constexpr (C64 && GS_FWD_C64_MINB > 0)
+    return &record_kernel_mb<M, Pb, R, SAVES, STAGES, C64, GS_FWD_C64_MINB>;
+  else
+    return &record_kernel<M, Pb, R, SAVES, STAGES, C64>;
 }
 
 // ---------------------------------------------------------------------------
@@ -1358,10 +1425,10 @@ __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
       } else {
         // segment i: [prev, t_{i-1}, y_{i-1}[D], h_i (, Y_1..Y_5 of step i)]
         const double* sp = a.arena + seg * a.segw;
-        const double2 w0 = *reinterpret_cast<const double2*>(sp);
-        seg = __double_as_longlong(w0.x);
-        tx = w0.y;
         if constexpr (STAGES) {
+          const double2 w0 = *reinterpret_cast<const double2*>(sp);
+          seg = __double_as_longlong(w0.x);
+          tx = w0.y;
           constexpr int SW = stage_segw<M, D>();
           double buf[SW];
 #pragma unroll
@@ -1375,9 +1442,19 @@ __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
           uh = buf[2 + D];
           M::template unpack<Pb, R>(false, yx, [&](int i) { return buf[3 + D + i]; }, sd);
         } else {
+          constexpr int CW = ((3 + D) + 1) & ~1;  // [prev, t, y[D], h] in whole double2
+          double buf[CW];
 #pragma unroll
-          for (int c = 0; c < D; ++c) yx[c] = to_r<R>(sp[2 + c]);
-          uh = sp[2 + D];
+          for (int w = 0; w < CW / 2; ++w) {
+            const double2 v = reinterpret_cast<const double2*>(sp)[w];
+            buf[2 * w] = v.x;
+            buf[2 * w + 1] = v.y;
+          }
+          seg = __double_as_longlong(buf[0]);
+          tx = buf[1];
+#pragma unroll
+          for (int c = 0; c < D; ++c) yx[c] = to_r<R>(buf[2 + c]);
+          uh = buf[2 + D];
         }
         --segs_left;
         mode = U_STEP;
@@ -1552,19 +1629,52 @@ inline cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long 
   return cudaLaunchKernel((const void*)kern, dim3((unsigned)blocks), dim3(tpb), args, smem, s);
 }
 
+#ifndef GS_INIT_STEP_PASS
+#define GS_INIT_STEP_PASS 1
+#endif
+// Launches the starting-step pass when the record would compute starting steps
+// (no h0 given) and the problem has no shared weights; returns whether it ran.
+template <class M, class Pb, class R, bool C64>
+inline bool init_step_pass(const FwdArgs& a, cudaStream_t s, cudaError_t* err) {
+  *err = cudaSuccess;
+  if constexpr (HasWeights<Pb>::value || !GS_INIT_STEP_PASS) {
+    return false;
+  } else {
+    if (a.h0 > 0.0 || a.n <= 0) return false;
+    long long blocks = (a.n + 255) / 256;
+    const long long cap = (long long)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    init_step_kernel<M, Pb, R, C64><<<(unsigned)blocks, 256, 0, s>>>(a);
+    *err = cudaGetLastError();
+    return *err == cudaSuccess;
+  }
+}
+
 template <class M, class Pb, class R>
-inline cudaError_t fwd_dispatch(const FwdArgs& a, cudaStream_t s) {
+inline cudaError_t fwd_dispatch(const FwdArgs& a_in, cudaStream_t s) {
+  FwdArgs a = a_in;
+  {
+    cudaError_t e = cudaSuccess;
+    bool pre = false;
+    if constexpr (M::kControl64) {
+      pre = a.control ? init_step_pass<M, Pb, R, true>(a, s, &e) : init_step_pass<M, Pb, R, false>(a, s, &e);
+    } else {
+      pre = init_step_pass<M, Pb, R, false>(a, s, &e);
+    }
+    if (e != cudaSuccess) return e;
+    a.h0_pre = pre ? 1 : 0;
+  }
   const size_t smem = (size_t)(((a.n_save + 1) & ~1) + a.segw * TPB_FWD) * sizeof(double);
   if (a.control) {  // FP64 step control: Tsit5 without shared weights
     if constexpr (M::kControl64 && !HasWeights<Pb>::value) {
       if constexpr (stages_possible<M, Pb, R>()) {
         if (a.stages)
-          return persistent_launch(record_kernel<M, Pb, R, true, true, true>, TPB_FWD, smem, a.n, s, &a);
+          return persistent_launch(record_entry<M, Pb, R, true, true, true>(), TPB_FWD, smem, a.n, s, &a);
       } else {
         if (a.stages) return cudaErrorInvalidValue;
       }
-      if (a.y_save) return persistent_launch(record_kernel<M, Pb, R, true, false, true>, TPB_FWD, smem, a.n, s, &a);
-      return persistent_launch(record_kernel<M, Pb, R, false, false, true>, TPB_FWD, smem, a.n, s, &a);
+      if (a.y_save) return persistent_launch(record_entry<M, Pb, R, true, false, true>(), TPB_FWD, smem, a.n, s, &a);
+      return persistent_launch(record_entry<M, Pb, R, false, false, true>(), TPB_FWD, smem, a.n, s, &a);
     } else {
       return cudaErrorInvalidValue;
     }

@@ -91,7 +91,7 @@ extern "C" gs_status gs_solve_grad_noalloc(int problem_id, int64_t n, const doub
 
   // Carve the scratch: counters | head | S | attempts | status | y(t1) | arena.
   const int k = o.ckpt_k > 0 ? o.ckpt_k : (14 - d > 1 ? 14 - d : 1);
-  const int segw = ((2 + d + k) + 1) & ~1;
+  const int segw = segw_of(d, k);
   const size_t N = (size_t)GS_NOALLOC_MAX_TRAJ;
   size_t off = 0;
   ScratchCounters* ctr = reinterpret_cast<ScratchCounters*>(base + off);
