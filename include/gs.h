@@ -284,7 +284,10 @@ gs_status gs_solve_grad_host(int problem_id, int64_t n, const double* params, co
  * gs_forward_record, bit for bit, but nothing is stored for a reverse sweep.
  * Arguments as gs_forward_record; y_save_out [n_save][d][n] may be NULL;
  * y_final_out [d][n] (device) receives y(t1) and traj_status [n] (device) the
- * trajectory status, both required when n > 0. ckpt_k is ignored.
+ * trajectory status, both required when n > 0; y_final_out may be the y0
+ * buffer itself (y0 is then replaced by y(t1)). Before its trajectory ends,
+ * y_final_out's first row holds the trajectory's starting step. ckpt_k is
+ * ignored.
  * Uses only the small counter block of the per-device workspace of
  * gs_solve_grad (no record arena). Synchronises `stream`; returns
  * GS_ERR_TRAJ_FAILED if any trajectory ended with a non-OK status.

@@ -477,8 +477,19 @@ __device__ __forceinline__ void tsit5_stages(const R (&y)[Pb::D], const R (&p)[P
 // Embedded error estimate e = y_new - yhat_new = h sum_j (b_j - bhat_j) k_j.
 template <class Pb, class R>
 __device__ __forceinline__ void tsit5_error(const R (&K)[7][Pb::D], R h, R (&e)[Pb::D]) {
+  // FP32: components 0, 1 as FP32x2 (the same per-component IEEE operations)
+  constexpr bool PACK = std::is_same<R, float>::value && Pb::D >= 2 && !HasNet<Pb>::value;
+  if constexpr (PACK) {
+    float2 s = __fmul2_rn(make_float2(tsit5::Btilde(0), tsit5::Btilde(0)), make_float2(K[0][0], K[0][1]));
 #pragma unroll
-  for (int c = 0; c < Pb::D; ++c) {
+    for (int j = 1; j < 7; ++j)
+      s = __ffma2_rn(make_float2(tsit5::Btilde(j), tsit5::Btilde(j)), make_float2(K[j][0], K[j][1]), s);
+    const float2 e2 = __fmul2_rn(make_float2(h, h), s);
+    e[0] = e2.x;
+    e[1] = e2.y;
+  }
+#pragma unroll
+  for (int c = PACK ? 2 : 0; c < Pb::D; ++c) {
     R s = mul_(R(tsit5::Btilde(0)), K[0][c]);
 #pragma unroll
     for (int j = 1; j < 7; ++j) s = fma_(R(tsit5::Btilde(j)), K[j][c], s);

@@ -1641,6 +1641,14 @@ inline bool init_step_pass(const FwdArgs& a, cudaStream_t s, cudaError_t* err) {
     return false;
   } else {
     if (a.h0 > 0.0 || a.n <= 0) return false;
+    // y_final is the scratch: not when it overlaps the inputs (an in-place call)
+    const char* yf = reinterpret_cast<const char*>(a.y_final);
+    const size_t yf_bytes = (size_t)a.n * sizeof(double);
+    auto overlaps = [&](const double* p, int rows) {
+      const char* b = reinterpret_cast<const char*>(p);
+      return b < yf + yf_bytes && yf < b + (size_t)rows * a.n * sizeof(double);
+    };
+    if (overlaps(a.params, Pb::NP) || overlaps(a.y0, Pb::D)) return false;
     long long blocks = (a.n + 255) / 256;
     const long long cap = (long long)sm_count() * 8;
     if (blocks > cap) blocks = cap;

@@ -104,3 +104,27 @@ def test_forward_record_with_stored_stages():
     assert ei.value.code == N.GS_ERR_INVALID_ARG
     rs.free()
     rc.free()
+
+
+@pytest.mark.parametrize("control", ["fast", "fp64"])
+def test_forward_only_solve_in_place_final_state(control):
+    """y_final may be the y0 buffer itself (an in-place call): the starting-step
+    pass, which keeps its results in y_final until each trajectory ends, is then
+    skipped and the record computes the starting steps itself, with the same
+    results as an out-of-place call."""
+    from paper_2609_02876_gb300 import _native as N
+    import ctypes as C
+    wl = W.make("lorenz", 1000)
+    ref = solve(wl, want_saves=False, control=control)
+    p = dev(wl["params"].T).contiguous()
+    y = dev(wl["y0"].T).contiguous()
+    st = torch.empty(wl["params"].shape[0], dtype=torch.int32, device="cuda")
+    save = np.ascontiguousarray(wl["save_t"], dtype=np.float64)
+    o = api._opts(control=control)
+    rc = N.lib().gs_solve(N.PROBLEMS["lorenz"], p.shape[1], p.data_ptr(), y.data_ptr(), None, float(wl["t0"]),
+                          float(wl["t1"]), save.ctypes.data_as(C.POINTER(C.c_double)), save.size, float(wl["rtol"]),
+                          float(wl["atol"]), C.byref(o), api._stream(), None, y.data_ptr(), st.data_ptr())
+    torch.cuda.synchronize()
+    assert rc == N.GS_OK
+    assert torch.equal(st, ref["status"])
+    assert torch.equal(y, ref["y_final"])
