@@ -999,24 +999,36 @@ __device__ __forceinline__ double initial_step_f32(const float (&y0)[Pb::D], con
 // the same rule up to that rounding.
 // ---------------------------------------------------------------------------
 
+// Bit patterns of positive doubles order as their values: range tests and
+// clamps of positive values run on the integer pipe.
+constexpr unsigned long long DBITS_1EM30 = 0x39b4484bfeebc2a0ull;  // 1e-30
+constexpr unsigned long long DBITS_1E30 = 0x46293e5939a08ceaull;   // 1e30
+constexpr unsigned long long DBITS_0P2 = 0x3fc999999999999aull;    // 0.2
+constexpr unsigned long long DBITS_TEN = 0x4024000000000000ull;    // 10
+__device__ __forceinline__ double clamp_pos_bits(double x, unsigned long long lo, unsigned long long hi) {
+  const unsigned long long b = dbits(x);  // x > 0
+  return __longlong_as_double((long long)(b < lo ? lo : (b > hi ? hi : b)));
+}
+
 // 1/x for 1e-30 < |x| < 1e30: the correctly rounded single-precision
 // reciprocal (relative error <= 2^-24) and one Newton step x0 + x0 (1 - x x0),
 // which squares the relative error; IEEE division outside that range.
 __device__ __forceinline__ double rcp_f64(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-30 && ax < 1e30)) return __ddiv_rn(1.0, x);
+  const unsigned long long ax = abs_bits(x);
+  if (!(ax > DBITS_1EM30 && ax < DBITS_1E30)) return __ddiv_rn(1.0, x);
   const double x0 = (double)__frcp_rn((float)x);
   return fma_(x0, fma_(-x, x0, 1.0), x0);
 }
 
-// m = (1/D) sum_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2 (err = sqrt(m)).
+// m = (1/D) sum_c (e_c / (atol + rtol max(|y_c|, |ynew_c|)))^2 (err = sqrt(m));
+// the scale with one rounding (a fused multiply-add).
 template <int D, class R>
 __device__ __forceinline__ double err_meansq_f64(const R (&e)[D], const R (&y)[D], const R (&yn)[D], double rtol,
                                                  double atol) {
   double s = 0.0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const double sc = add_(atol, mul_(rtol, max_abs(to_d(y[c]), to_d(yn[c]))));
+    const double sc = fma_(rtol, max_abs(to_d(y[c]), to_d(yn[c])), atol);
     const double r = mul_(to_d(e[c]), rcp_f64(sc));
     s = fma_(r, r, s);
   }
@@ -1047,13 +1059,13 @@ __device__ __forceinline__ double ipow_(double y) {  // y^K by repeated squaring
 // Outside [1e-30, 1e30] the factor is clamped whatever m is, so m is held to
 // that range first.
 template <int Q>
-__device__ __forceinline__ double ctrl_factor_ms_f64(double m) {
+__device__ __forceinline__ double ctrl_factor_ms_f64(double m) {  // m >= 0, not NaN
   constexpr int K = 2 * (Q + 1);
-  if (!(m > 0.0)) return 10.0;
-  const double mc = fmin(fmax(m, 1e-30), 1e30);
+  if (!positive(m)) return 10.0;
+  const double mc = clamp_pos_bits(m, DBITS_1EM30, DBITS_1E30);
   double y = (double)exp2f(log2f((float)mc) * (-1.0f / K));
   y = fma_(y, mul_(fma_(-mc, ipow_<K>(y), 1.0), 1.0 / K), y);
-  return fmin(10.0, fmax(0.2, mul_(0.9, y)));
+  return clamp_pos_bits(mul_(0.9, y), DBITS_0P2, DBITS_TEN);
 }
 
 // RMS of v_c / sc_c.

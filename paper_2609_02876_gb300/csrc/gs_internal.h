@@ -85,6 +85,8 @@ struct RevArgs {
   int stages;                // the record holds stage inputs (see FwdArgs)
   const double* side_stg;
   int* tc_error;             // set when a tensor-core product's completion wait ran out (or nullptr)
+  int t1_pre;                // set by the launcher: y0_bar (and loss) hold lambda (and the loss) after
+                             // the save at t1, which the reverse sweep then starts from
   double save_t[MAX_SAVE_HOST];
 };
 

@@ -32,6 +32,7 @@
 // unit_stored (the stored-stage record and reverse unit).
 #pragma once
 
+#include <cstring>
 #include <type_traits>
 
 #include "gs_device.cuh"
@@ -1334,6 +1335,35 @@ __global__ void __launch_bounds__(TPB_REV) reverse_kernel(const RevArgs a) {
 // STAGES: the record holds every step's stage data after h (segments of
 // stage_segw<M, D>() doubles) and side_stg the side steps' ([save][payload][n]):
 // the units load them instead of recomputing the stages.
+// The cotangent of the save at t1 for every trajectory in one pass before the
+// k = 1 reverse sweep (FP64): y0_bar[., k] = lambda after that save (2 y(t1)
+// for the built-in loss, else the caller's dL/dy(t1)), loss[k] = ||y(t1)||^2
+// for the built-in loss; the sweep starts from them. In the sweep this is
+// per-trajectory code that one or two lanes of a warp run while the others
+// wait; the arithmetic is the same (next_save's), so the results are too.
+template <class Pb, bool USER_COT>
+__global__ void __launch_bounds__(256) t1_save_kernel(const RevArgs a) {
+  constexpr int D = Pb::D;
+  const long long n = a.n;
+  const int js = a.n_save - 1;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    double loss = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const double y = a.y_final[c * n + k];
+      double lam = 0.0;
+      if (USER_COT) {
+        lam = add_(lam, a.y_save_bar[((long long)js * D + c) * n + k]);
+      } else {
+        lam = add_(lam, add_(y, y));
+        loss = acc_loss(loss, mul_(y, y));
+      }
+      a.y0_bar[c * n + k] = lam;
+    }
+    if (!USER_COT && a.loss) a.loss[k] = loss;
+  }
+}
+
 template <class M, class Pb, class R, bool USER_COT, bool STAGES = false>
 __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
   constexpr int D = Pb::D, NP = Pb::NP;
@@ -1395,6 +1425,14 @@ __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
             seg = hd;
             segs_left = a.S[k];
             js = ns - 1;
+            if constexpr (std::is_same<R, double>::value) {
+              if (a.t1_pre) {  // the save at t1, taken by the pass before this kernel
+#pragma unroll
+                for (int c = 0; c < D; ++c) lam[c] = a.y0_bar[c * n + k];
+                if (!USER_COT && a.loss) loss = a.loss[k];
+                js = ns - 2;
+              }
+            }
           }
         } else {
           drained = true;
@@ -1696,8 +1734,49 @@ inline cudaError_t fwd_dispatch(const FwdArgs& a_in, cudaStream_t s) {
   return persistent_launch(record_kernel<M, Pb, R, false, false>, TPB_FWD, smem, a.n, s, &a);
 }
 
+#ifndef GS_T1_SAVE_PASS
+#define GS_T1_SAVE_PASS 1
+#endif
+// Launches the t1-save pass for the FP64 k = 1 reverse sweep when the last save
+// time is t1 and y0_bar is given (and overlaps none of the sweep's inputs);
+// returns whether it ran.
+template <class Pb, class R>
+inline bool t1_save_pass(const RevArgs& a, cudaStream_t s, cudaError_t* err) {
+  *err = cudaSuccess;
+  if constexpr (!std::is_same<R, double>::value || HasWeights<Pb>::value || !GS_T1_SAVE_PASS) {
+    return false;
+  } else {
+    const int ns = a.n_save;
+    if (a.n <= 0 || !a.y0_bar || ns < 1 || a.k != 1) return false;
+    if (std::memcmp(&a.save_t[ns - 1], &a.t1, sizeof(double)) != 0) return false;
+    auto overlaps = [](const void* x, size_t xb, const void* y, size_t yb) {
+      const char *p = static_cast<const char*>(x), *q = static_cast<const char*>(y);
+      return p && q && p < q + yb && q < p + xb;
+    };
+    const size_t nb = (size_t)a.n * sizeof(double);
+    const void* outs[2] = {a.y0_bar, a.loss};
+    const size_t outb[2] = {nb * Pb::D, nb};
+    const void* ins[3] = {a.params, a.y_save_bar, a.y_final};
+    const size_t inb[3] = {nb * Pb::NP, nb * Pb::D * (size_t)ns, nb * Pb::D};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j)
+        if (overlaps(outs[i], outb[i], ins[j], inb[j])) return false;
+    long long blocks = (a.n + 255) / 256;
+    const long long cap = (long long)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    if (a.y_save_bar)
+      t1_save_kernel<Pb, true><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else
+      t1_save_kernel<Pb, false><<<(unsigned)blocks, 256, 0, s>>>(a);
+    *err = cudaGetLastError();
+    return *err == cudaSuccess;
+  }
+}
+
 template <class M, class Pb, class R>
-inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
+inline cudaError_t rev_dispatch(const RevArgs& a_in, cudaStream_t s) {
+  RevArgs a = a_in;
+  a.t1_pre = 0;
   size_t smem = (size_t)((a.n_save + 1) & ~1) * sizeof(double);
   if constexpr (HasWeights<Pb>::value) {
     using Acc = AccFor<Pb, R>;
@@ -1717,6 +1796,11 @@ inline cudaError_t rev_dispatch(const RevArgs& a, cudaStream_t s) {
                                                                       (int)(blocks * (TPB_REV / 32)), a.shared_w_bar);
     return cudaGetLastError();
   } else {
+  if (a.k == 1) {
+    cudaError_t e;
+    a.t1_pre = t1_save_pass<Pb, R>(a, s, &e) ? 1 : 0;
+    if (e != cudaSuccess) return e;
+  }
   if constexpr (stages_possible<M, Pb, R>()) {
     if (a.stages) {
       if (a.k != 1 || a.segw != stage_segw<M, Pb::D>()) return cudaErrorInvalidValue;
