@@ -22,15 +22,14 @@
 // replay, complex-step gradients, finite differences, invariants, Rosenbrock23's
 // stability function and error estimate, the neural term's weight derivatives;
 // the starting step and the controller against scipy's implementations of the
-// same textbook rules, for Tsit5 and for Verner7, with planted mistakes caught).
+// same textbook rules, for Tsit5 and Verner7, and for the two Rosenbrock
+// methods with scipy's driver stepping with this file's Rosenbrock step; with
+// planted mistakes caught).
 //
 // Parity unpinned (no value outside this file fixes them; they only shape the
 // mesh, which the gradient treats as data): the end-of-span sliver 1e-12, the
-// quartered step after a singular linear system, the controller exponents of
-// the two Rosenbrock methods (1/(q+1) with q = 4 for Rodas5P, 2 for
-// Rosenbrock23: the function pinned for Tsit5 and Verner7, with the method's
-// order), and Rodas5P's coefficients beyond what its order conditions and
-// stiff accuracy fix.
+// quartered step after a singular linear system, and Rodas5P's coefficients
+// beyond what its order conditions and stiff accuracy fix.
 
 #include <algorithm>
 #include <cmath>

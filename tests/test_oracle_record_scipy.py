@@ -25,6 +25,16 @@ step of order 7) pins the oracle's Verner7 record: same counts, h to 3e-5
 (the seventh-order estimate cancels further, and Van der Pol's many rejected
 trials compound the rounding differences to 4e-6; measured).
 
+For the Rosenbrock methods scipy has no driver of their own, so its
+RungeKutta driver runs with its one-step function swapped for the oracle's
+Rosenbrock step (itself pinned by its stability function, order and error
+estimate), error_estimator_order set to the published embedded order
+(Rosenbrock23 2, Shampine & Reichelt; Rodas5P 4, Steinebach) and the
+starting step of the solution's order: scipy's accept test, safety factor,
+clamps, exponent and post-rejection cap then drive the mesh, which must equal
+the oracle's record (same counts, h to 1e-5: the two codes round the error
+norm differently and Robertson's stiff control loop compounds that to ~1e-6).
+
 A plausible mistake in the oracle's control constants must fail these pins;
 the last tests plant several, one at a time, in a copy of the oracle compiled
 here, and check that each one is caught.
@@ -48,6 +58,8 @@ VERN7 = oracle.METHOD_VERNER7
 H0_RTOL = 1e-12
 H_RTOL = 1e-6  # h agreement (see the module docstring)
 H_RTOL_V7 = 3e-5
+H_RTOL_ROS = 1e-5
+ROS23, RODAS5P = oracle.METHOD_ROSENBROCK23, oracle.METHOD_RODAS5P
 
 
 def _rhs(name, p):
@@ -255,3 +267,94 @@ def test_planted_verner7_control_mistake_fails_the_scipy_pin(old, new):
         res, _ = _compare_meshes(_cases(VERN7)[:2], VERN7)
     worst = max(r[2] for r in res)
     assert not (all(r[0] and r[1] for r in res) and worst <= H_RTOL_V7), f"planted mistake not detected: {new}"
+
+
+# ----------------------------------------------------------------------------- Rosenbrock methods
+
+def _ros_scipy_mesh(name, method, p, y0, t0, t1, rtol, atol):
+    """Accepted steps of scipy's RK driver stepping with the oracle's Rosenbrock step."""
+    import scipy.integrate._ivp.rk as rkmod
+    order, err_order = (2, 2) if method == ROS23 else (5, 4)
+    last = {}
+
+    def fun(t, y):
+        return oracle.rhs(name, p, y)[0][0]
+
+    class RosenbrockScipy(RungeKutta):
+        C, A, B, E, P = np.zeros(1), np.zeros((1, 1)), np.ones(1), np.zeros(2), np.zeros((2, 1))
+        n_stages = 1
+
+        def __init__(self, f, t0_, y0_, t_bound, **kw):
+            self.order, self.error_estimator_order = order, err_order
+            super().__init__(f, t0_, y0_, t_bound, **kw)
+            self.h_abs = select_initial_step(self.fun, self.t, self.y, t_bound, np.inf, self.f, self.direction,
+                                             order, self.rtol, self.atol)
+
+        def _estimate_error_norm(self, K, h, scale):
+            return float(np.sqrt(np.mean((last["e"] / scale) ** 2)))
+
+    def one_step(f_, t, y, f0, h, A, B, C, K):
+        yn, e = oracle.step(name, method, p, y, h)
+        last["e"] = e[0]
+        K[-1] = fun(t + h, yn[0])
+        return yn[0], K[-1]
+
+    saved = rkmod.rk_step
+    rkmod.rk_step = one_step
+    try:
+        sol = solve_ivp(fun, (t0, t1), np.array(y0, dtype=np.float64), method=RosenbrockScipy, rtol=rtol, atol=atol)
+    finally:
+        rkmod.rk_step = saved
+    assert sol.status == 0, sol.message
+    return np.diff(sol.t)
+
+
+def _compare_ros(cases):
+    res, rejected = [], 0
+    for name, method, wl in cases:
+        rec = oracle.record(name, wl["params"], wl["y0"], wl["t0"], wl["t1"], [], wl["rtol"], wl["atol"],
+                            method=method, want_saves=False)
+        for k in range(wl["params"].shape[0]):
+            h_o = rec["h"][rec["offsets"][k]:rec["offsets"][k + 1]]
+            h_s = _ros_scipy_mesh(name, method, wl["params"][k], wl["y0"][k], wl["t0"], wl["t1"], wl["rtol"],
+                                  wl["atol"])
+            rejected += int(rec["n_att"][k] - rec["S"][k])
+            if h_o.size != h_s.size:
+                res.append((False, np.inf))
+                continue
+            dh = np.abs(h_o[:-1] - h_s[:-1]) / h_s[:-1] if h_o.size > 1 else np.zeros(1)
+            res.append((True, float(dh.max())))
+    return res, rejected
+
+
+def _ros_cases(which=("ros23", "rodas5p")):
+    out = []
+    if "ros23" in which:
+        out += [("robertson", ROS23, W.make("robertson", 8, seed=3)), ("vdp", ROS23, W.make("vdp", 8, seed=3))]
+    if "rodas5p" in which:
+        out += [("robertson", RODAS5P, W.make("robertson", 8, seed=3)), ("hires", RODAS5P, W.make("hires", 8, seed=3))]
+    return out
+
+
+def test_rosenbrock_meshes_equal_scipy_driver_with_the_oracle_step():
+    res, rejected = _compare_ros(_ros_cases())
+    assert rejected >= 50, rejected
+    assert all(r[0] for r in res), [i for i, r in enumerate(res) if not r[0]]
+    assert max(r[1] for r in res) <= H_RTOL_ROS, max(r[1] for r in res)
+
+
+ROS_MUTANTS = [
+    # Rosenbrock23's controller exponent -1/4 instead of -1/3
+    ("method == M_ROS23 ? 2 : (method == M_VERN7 ? 6 : 4)", "method == M_ROS23 ? 3 : (method == M_VERN7 ? 6 : 4)",
+     "ros23"),
+    # Rodas5P's (and Tsit5's) controller exponent -1/6 instead of -1/5
+    ("method == M_ROS23 ? 2 : (method == M_VERN7 ? 6 : 4)", "method == M_ROS23 ? 2 : (method == M_VERN7 ? 6 : 5)",
+     "rodas5p"),
+]
+
+
+@pytest.mark.parametrize("old,new,which", ROS_MUTANTS)
+def test_planted_rosenbrock_control_mistake_fails_the_scipy_pin(old, new, which):
+    with _mutant_oracle(old, new):
+        res, _ = _compare_ros(_ros_cases((which,))[:1])
+    assert not (all(r[0] for r in res) and max(r[1] for r in res) <= H_RTOL_ROS), f"not detected: {new}"
