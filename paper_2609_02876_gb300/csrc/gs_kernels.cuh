@@ -1015,15 +1015,17 @@ __device__ __forceinline__ void record_body(const FwdArgs& a) {
   }
 }
 
-// Starting steps of all trajectories in one pass, before the record kernel
-// (problems without shared weights): y_final[k] = the h the record's refill
-// would compute for trajectory k, by the same function and inputs. In the
-// record this is per-trajectory code that one or two lanes of a warp run while
-// the others wait; here every lane computes one.
+// Starting steps of all trajectories in one pass, before the record kernel:
+// y_final[k] = the h the record's refill would compute for trajectory k, by the
+// same function and inputs (shared-weight problems stage their weights first,
+// as the record does). In the record this is per-trajectory code that one or
+// two lanes of a warp run while the others wait; here every lane computes one.
 template <class M, class Pb, class R, bool C64>
 __global__ void __launch_bounds__(256) init_step_kernel(const FwdArgs a) {
   constexpr int D = Pb::D, NP = Pb::NP;
   using Carry = typename M::template Carry<Pb, R>;
+  if constexpr (HasWeights<Pb>::value) Pb::block_setup(a.shared_w);
+  __syncthreads();
   const long long n = a.n;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     R y[D], p[NP];
@@ -1671,11 +1673,11 @@ inline cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long 
 #define GS_INIT_STEP_PASS 1
 #endif
 // Launches the starting-step pass when the record would compute starting steps
-// (no h0 given) and the problem has no shared weights; returns whether it ran.
+// (no h0 given); returns whether it ran.
 template <class M, class Pb, class R, bool C64>
 inline bool init_step_pass(const FwdArgs& a, cudaStream_t s, cudaError_t* err) {
   *err = cudaSuccess;
-  if constexpr (HasWeights<Pb>::value || !GS_INIT_STEP_PASS) {
+  if constexpr (!GS_INIT_STEP_PASS) {
     return false;
   } else {
     if (a.h0 > 0.0 || a.n <= 0) return false;
@@ -1702,7 +1704,7 @@ inline cudaError_t fwd_dispatch(const FwdArgs& a_in, cudaStream_t s) {
   {
     cudaError_t e = cudaSuccess;
     bool pre = false;
-    if constexpr (M::kControl64) {
+    if constexpr (M::kControl64 && !HasWeights<Pb>::value) {  // (FP64 control: no shared weights)
       pre = a.control ? init_step_pass<M, Pb, R, true>(a, s, &e) : init_step_pass<M, Pb, R, false>(a, s, &e);
     } else {
       pre = init_step_pass<M, Pb, R, false>(a, s, &e);
