@@ -56,7 +56,8 @@ struct FwdArgs {
   int stages;
   double* side_stg;
   int control;  // 1: FP64 step control (GS_CONTROL_FP64)
-  int h0_pre;   // set by the launcher: y_final[k] holds trajectory k's starting step until k ends
+  int h0_pre;   // set by the launcher: 1: y_final[k] holds trajectory k's starting step until k ends;
+                // 2: head[k] holds it (as bits) and y_final[., k] the method's carry f(y0)
   double save_t[MAX_SAVE_HOST];
 };
 

@@ -104,6 +104,16 @@ struct Tsit5Method {
   struct Carry {
     R k1[Pb::D];  // FSAL: f(y) of the current accepted state
   };
+  static constexpr bool kCarryIsF = true;  // the carry is f(y) (start() computes it)
+  template <class Pb, class R, class Get>
+  __device__ __forceinline__ static void set_carry_f(Carry<Pb, R>& cy, Get f) {
+#pragma unroll
+    for (int c = 0; c < Pb::D; ++c) cy.k1[c] = f(c);
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static R carry_f(const Carry<Pb, R>& cy, int c) {
+    return cy.k1[c];
+  }
   template <class Pb, class R>
   __device__ __forceinline__ static void start(const R (&y)[Pb::D], const R (&p)[Pb::NP], Carry<Pb, R>& cy,
                                                float (&f0)[Pb::D]) {
@@ -263,6 +273,7 @@ struct Rodas5PMethod {  // FP64 only: the stiff W-matrix LU and its solves stay 
   static constexpr bool kStages = true;
   template <class Pb, class R>
   struct Carry {};
+  static constexpr bool kCarryIsF = false;
   // ---- stored stages: a step stores U_0..U_7 and the LU of W (factors, pivot
   // reciprocals, pivots). The stage inputs Y_i = y + sum_j a_ij U_j and the
   // new state are rebuilt from them by the same operations as the step.
@@ -410,6 +421,16 @@ struct Ros23Method {
   struct Carry {
     R F0[Pb::D];  // f(y) of the current accepted state
   };
+  static constexpr bool kCarryIsF = true;  // the carry is f(y) (start() computes it)
+  template <class Pb, class R, class Get>
+  __device__ __forceinline__ static void set_carry_f(Carry<Pb, R>& cy, Get f) {
+#pragma unroll
+    for (int c = 0; c < Pb::D; ++c) cy.F0[c] = f(c);
+  }
+  template <class Pb, class R>
+  __device__ __forceinline__ static R carry_f(const Carry<Pb, R>& cy, int c) {
+    return cy.F0[c];
+  }
   // ---- stored stages: a step stores k1, u2 and the LU of W (factors, pivot
   // reciprocals, pivots); Y1 = y + h/2 k1 and a side step's save state
   // y + h (u2 + k1) are rebuilt from them by the step's own operations.
@@ -551,6 +572,7 @@ struct Verner7Method {  // FP64 only
   static constexpr double IDLE_H = 0.0;
   template <class Pb, class R>
   struct Carry {};  // not FSAL: every step evaluates f(y)
+  static constexpr bool kCarryIsF = false;
   // ---- stored stages: a step stores the stage inputs Y_1..Y_8 (Y_0 is the
   // segment's state); a side step also its save state.
   template <class Pb, class R>
@@ -705,6 +727,16 @@ constexpr bool stages_possible() {
     return false;
 }
 
+// Whether the starting-step pass also hands the record its carry f(y0)
+// (FP64 methods whose carry is f(y0)): measured at Lorenz / Van der Pol 2^24,
+// FP64 records 0.3% / 2.3% faster (3% with FP64 step control), FP32-mixed
+// records 5% / 2.6% slower (their f(y0) in FP32 costs less than the exact
+// conversions of the carried values), so FP64 only.
+template <class M, class R>
+constexpr bool carry_from_pass() {
+  return M::kCarryIsF && std::is_same<R, double>::value;
+}
+
 // SAVES: save-time side steps run (for y_save, or for the stored side stages);
 // STAGES: the record stores stage inputs (k = 1); C64: FP64 step control
 // (GS_CONTROL_FP64: error norm, controller, starting step and step floor in FP64).
@@ -774,17 +806,27 @@ __device__ __forceinline__ void record_body(const FwdArgs& a) {
           status = TRAJ_OK;
           rej = lastnf = lastsing = false;
           prev = -1;
-          M::template start<Pb, R>(y, p, cy, ff);
-          if (a.h0 > 0.0) {
-            h = a.h0;
-          } else if (a.h0_pre) {
-            h = a.y_final[k];  // the starting-step pass's result (this slot is rewritten when k ends)
-          } else if constexpr (C64) {
-            double fd[D];
-            Pb::f(yd, pd, fd);
-            h = initial_step_f64<Pb, M::ORDER>(yd, pd, fd, a.t0, t1, a.rtol, a.atol);
-          } else {
-            h = initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
+          bool carried = false;
+          if constexpr (carry_from_pass<M, R>()) {
+            if (a.h0_pre == 2) {  // the pass's starting step and f(y0) (slots rewritten when k ends)
+              M::template set_carry_f<Pb, R>(cy, [&](int c) { return to_r<R>(a.y_final[c * n + k]); });
+              h = __longlong_as_double(a.head[k]);
+              carried = true;
+            }
+          }
+          if (!carried) {
+            M::template start<Pb, R>(y, p, cy, ff);
+            if (a.h0 > 0.0) {
+              h = a.h0;
+            } else if (a.h0_pre) {
+              h = a.y_final[k];  // the starting-step pass's result (this slot is rewritten when k ends)
+            } else if constexpr (C64) {
+              double fd[D];
+              Pb::f(yd, pd, fd);
+              h = initial_step_f64<Pb, M::ORDER>(yd, pd, fd, a.t0, t1, a.rtol, a.atol);
+            } else {
+              h = initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, t1, a.rtol, a.atol);
+            }
           }
           fin = fin && positive(h) && finite_nonneg(h);
           ended = !fin;
@@ -1018,8 +1060,10 @@ __device__ __forceinline__ void record_body(const FwdArgs& a) {
 // Starting steps of all trajectories in one pass, before the record kernel:
 // y_final[k] = the h the record's refill would compute for trajectory k, by the
 // same function and inputs (shared-weight problems stage their weights first,
-// as the record does). In the record this is per-trajectory code that one or
-// two lanes of a warp run while the others wait; here every lane computes one.
+// as the record does). With h0_pre = 2 (a record, whose head[k] is free until
+// k ends, and carry_from_pass) head[k] holds h and y_final[., k] the carry
+// f(y0). In the record this is per-trajectory code that one or two lanes of a
+// warp run while the others wait; here every lane computes one.
 template <class M, class Pb, class R, bool C64>
 __global__ void __launch_bounds__(256) init_step_kernel(const FwdArgs a) {
   constexpr int D = Pb::D, NP = Pb::NP;
@@ -1046,14 +1090,22 @@ __global__ void __launch_bounds__(256) init_step_kernel(const FwdArgs a) {
       yd[c] = v;
     }
     double h;
+    Carry cy;
+    M::template start<Pb, R>(y, p, cy, ff);
     if constexpr (C64) {
       double fd[D];
       Pb::f(yd, pd, fd);
       h = initial_step_f64<Pb, M::ORDER>(yd, pd, fd, a.t0, a.t1, a.rtol, a.atol);
     } else {
-      Carry cy;
-      M::template start<Pb, R>(y, p, cy, ff);
       h = initial_step_f32<Pb, M::ORDER>(yf, pf, ff, a.t0, a.t1, a.rtol, a.atol);
+    }
+    if constexpr (carry_from_pass<M, R>()) {
+      if (a.h0_pre == 2) {  // f(y0), the record's carry, too: h then goes to head[k]
+#pragma unroll
+        for (int c = 0; c < D; ++c) a.y_final[c * n + k] = to_d(M::template carry_f<Pb, R>(cy, c));
+        a.head[k] = __double_as_longlong(h);
+        continue;
+      }
     }
     a.y_final[k] = h;
   }
@@ -1675,7 +1727,7 @@ inline cudaError_t persistent_launch(Kern kern, int tpb, size_t smem, long long 
 // Launches the starting-step pass when the record would compute starting steps
 // (no h0 given); returns whether it ran.
 template <class M, class Pb, class R, bool C64>
-inline bool init_step_pass(const FwdArgs& a, cudaStream_t s, cudaError_t* err) {
+inline bool init_step_pass(FwdArgs& a, cudaStream_t s, cudaError_t* err) {
   *err = cudaSuccess;
   if constexpr (!GS_INIT_STEP_PASS) {
     return false;
@@ -1692,8 +1744,10 @@ inline bool init_step_pass(const FwdArgs& a, cudaStream_t s, cudaError_t* err) {
     long long blocks = (a.n + 255) / 256;
     const long long cap = (long long)sm_count() * 8;
     if (blocks > cap) blocks = cap;
+    a.h0_pre = (carry_from_pass<M, R>() && a.head) ? 2 : 1;
     init_step_kernel<M, Pb, R, C64><<<(unsigned)blocks, 256, 0, s>>>(a);
     *err = cudaGetLastError();
+    if (*err != cudaSuccess) a.h0_pre = 0;
     return *err == cudaSuccess;
   }
 }
@@ -1703,14 +1757,16 @@ inline cudaError_t fwd_dispatch(const FwdArgs& a_in, cudaStream_t s) {
   FwdArgs a = a_in;
   {
     cudaError_t e = cudaSuccess;
-    bool pre = false;
+    a.h0_pre = 0;
     if constexpr (M::kControl64 && !HasWeights<Pb>::value) {  // (FP64 control: no shared weights)
-      pre = a.control ? init_step_pass<M, Pb, R, true>(a, s, &e) : init_step_pass<M, Pb, R, false>(a, s, &e);
+      if (a.control)
+        init_step_pass<M, Pb, R, true>(a, s, &e);
+      else
+        init_step_pass<M, Pb, R, false>(a, s, &e);
     } else {
-      pre = init_step_pass<M, Pb, R, false>(a, s, &e);
+      init_step_pass<M, Pb, R, false>(a, s, &e);
     }
     if (e != cudaSuccess) return e;
-    a.h0_pre = pre ? 1 : 0;
   }
   const size_t smem = (size_t)(((a.n_save + 1) & ~1) + a.segw * TPB_FWD) * sizeof(double);
   if (a.control) {  // FP64 step control: Tsit5 without shared weights
