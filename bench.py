@@ -555,6 +555,42 @@ def forward_measure(args, peaks, steps=5):
     return res
 
 
+def launches_per_step(problem, precision, k, wl):
+    """Kernels one gs_solve_grad call launches: the starting-step pass, the record, the
+    t1-save pass (FP64, no shared weights, k = 1, last save time t1), the reverse sweep,
+    and for shared-weight problems the weight-gradient reduction."""
+    weights = problem in ("lv_ude", "nrob")
+    st = np.asarray(wl["save_t"], dtype=np.float64)
+    t1_pass = (precision == "fp64" and not weights and k == 1 and st.size > 0
+               and st[-1].tobytes() == np.float64(wl["t1"]).tobytes())
+    return 3 + int(t1_pass) + int(weights)
+
+
+def record_memory_measure():
+    """Device memory of the record (gs_record_bytes) for the paper's memory case, the
+    neural Robertson at B = 128 trajectories (Rodas5P, compact record), and for a 2^20
+    Lorenz ensemble in both record layouts (compact and stored stages)."""
+    import torch
+    from paper_2609_02876_gb300 import api
+    out = {}
+    for key, name, n, opts in (("nrob_B128", "nrob", 128, {}),
+                               ("lorenz_2^20_compact", "lorenz", 1 << 20, {"ckpt_k": 1}),
+                               ("lorenz_2^20_stored_stages", "lorenz", 1 << 20, {"ckpt_k": 1, "record_stages": True})):
+        wl = W.make(name, n)
+        P = torch.as_tensor(np.ascontiguousarray(wl["params"].T), device="cuda")
+        Y = torch.as_tensor(np.ascontiguousarray(wl["y0"].T), device="cuda")
+        w = None if wl["w"] is None else torch.as_tensor(np.asarray(wl["w"], dtype=np.float32), device="cuda")
+        rec, _, _ = api.forward_record(name, P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"],
+                                       layout="soa", shared_w=w, want_saves=False, **opts)
+        st = rec.stats()
+        out[key] = {"n": n, "record_bytes": rec.bytes(), "accepted_steps": st["accepted"],
+                    "bytes_per_accepted_step": rec.bytes() / max(st["accepted"], 1)}
+        rec.free()
+        del P, Y
+        torch.cuda.empty_cache()
+    return out
+
+
 def forward_mode_measure(problem, P, Y, wl, steps=3):
     """The gradient with respect to theta by forward mode (gs_forward_grad: one pass
     carrying the P unit directions) against the reverse sweep (gs_reverse) on the same
@@ -749,8 +785,6 @@ def main():
            "calls": args.steps}
     del hP, hY, hout
 
-    # kernels per timed step: the starting-step pass, the record and the reverse sweep (shared-weight
-    # problems: the record, the reverse sweep and the weight-gradient reduction)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -758,7 +792,8 @@ def main():
             "config": dict(config_of(args.problem, args.rtol, args.precision, n, args.method), control=args.control),
             "roofline": roof, "kernels_ms": {"record": f.rec_s * 1e3, "reverse": f.rev_s * 1e3},
             "work": work, "peaks_measured": peaks,
-            "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": clocks}
+            "e2e": e2e, "gpu_launches": launches_per_step(args.problem, args.precision, int(f.rinfo[0]),
+                                                          f.wl) * args.steps, "clocks": clocks}
     solo = rank == 0 and ws == 1
     if rank == 0:
         line["accuracy"] = sample_accuracy(args.problem, wl, f.out, args.precision, args.method, args.control,
@@ -795,6 +830,8 @@ def main():
     if solo and not args.no_forward:
         line["forward_only"] = forward_measure(args, peaks)
         torch.cuda.empty_cache()
+    if solo and not args.no_legs:
+        line["record_memory"] = record_memory_measure()
     if solo and not args.no_legs:
         # the other configurations: Lorenz at the small size, the Van der Pol part of the
         # non-stiff sweep, the stiff kinetics with Rodas5P at their largest sizes, the LV UDE
