@@ -119,7 +119,7 @@ struct gs_record {
   double* y_final = nullptr;
   void* wpart = nullptr;  // per-warp shared-weight gradient partials (shared-weight problems)
   // Stored stages (gs_solve_grad's workspace, Tsit5 FP64, k = 1): segments also
-  // hold each step's stage inputs, side_stg [n_save][6][d][n] the side steps'.
+  // hold each step's stage data, side_stg (n x n_save x payload) the side steps'.
   int stages = 0;
   double* side_stg = nullptr;
   size_t side_cap = 0;  // doubles

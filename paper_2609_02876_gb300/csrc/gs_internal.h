@@ -51,8 +51,9 @@ struct FwdArgs {
   // Stored stages (k = 1, FP64): each segment also holds its step's stage
   // data after h (Tsit5: Y_1..Y_5; Verner7: Y_1..Y_8; Rodas5P: U_0..U_7 and
   // the LU of W with pivot reciprocals and pivots; Rosenbrock23: k1, u2 and the
-  // LU of W), and side_stg [n_save][payload][n] receives the same for every
-  // save-time side step (plus its save state for the explicit methods).
+  // LU of W), and side_stg (n x n_save x payload doubles; layout: side_blocks
+  // in gs_kernels.cuh) receives the same for every save-time side step (plus
+  // its save state for the explicit methods).
   int stages;
   double* side_stg;
   int control;  // 1: FP64 step control (GS_CONTROL_FP64)
