@@ -81,6 +81,11 @@ def _call(lib, **kw):
     (dict(pid=6, w=1, opt=dict(precision=1)), N.GS_ERR_INVALID_ARG),  # stiff: FP64 only
     (dict(pid=6, w=1, opt=dict(method=1)), N.GS_ERR_INVALID_ARG),  # no Tsit5 kernel for it
     (dict(pid=6, w=1, opt=dict(ckpt_k=4)), N.GS_ERR_INVALID_ARG),  # shared weights: every state stored
+    (dict(opt=dict(control=2)), N.GS_ERR_INVALID_ARG),  # no such step control
+    (dict(pid=2, opt=dict(control=1)), N.GS_ERR_INVALID_ARG),  # FP64 step control: Tsit5 only
+    (dict(pid=0, opt=dict(control=1, method=4)), N.GS_ERR_INVALID_ARG),  # ... not Verner7
+    (dict(pid=5, w=1, opt=dict(control=1, precision=1)), N.GS_ERR_INVALID_ARG),  # ... nor shared weights
+    (dict(opt=dict(record_stages=2)), N.GS_ERR_INVALID_ARG),
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, kw, code):
     assert _call(lib, **kw) == code
