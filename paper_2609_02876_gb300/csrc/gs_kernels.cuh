@@ -96,7 +96,7 @@ struct Tsit5Method {
   static constexpr int ORDER = 5, ERR_ORDER = 4;  // solution order; lower order of the error estimate
   static constexpr bool kStages = true;           // records may store stage inputs
   static constexpr bool kControl64 = true;        // record kernels with FP64 step control
-  static constexpr int REV_MINB_F32 = 8, REV_MINB_STAGES = 6;  // reverse-sweep register caps (see rev_min_blocks)
+  static constexpr int REV_MINB_F32 = 8, REV_MINB_STAGES = 5;  // reverse-sweep register caps (see rev_min_blocks)
   // Step of the lanes without work in a warp-collective unit (zero cotangent):
   // any value whose step stays finite.
   static constexpr double IDLE_H = 0.0;
@@ -1627,7 +1627,8 @@ __device__ __forceinline__ void reverse_k1_body(const RevArgs& a) {
 // warps hide the latency of the dependent segment loads and arithmetic chains.
 // Measured at 2^24 Lorenz trajectories: the FP32-mixed sweep 3.4% faster at 8
 // blocks (64 registers) than at the compiler's 72, the FP64 stored-stage sweep
-// 1.2% faster at 6 (80) than at 122; the shared-weight kernels need more
+// 1.5% faster at 5 (96 registers) than at 122 (at 6, 80 registers: 1.2%; at 7,
+// 72: 1.0%); the shared-weight kernels need more
 // registers than either cap and keep the compiler's choice. Capping the
 // Rodas5P (252 registers, 2 CTAs) and Verner7 (154, 3 CTAs) stored-stage sweeps
 // at 3 to 5 CTAs changed their time by under 2% (Robertson 2^20, Lorenz 2^23),

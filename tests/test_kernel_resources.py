@@ -50,9 +50,9 @@ def test_lorenz_fp64_stored_stage_kernels_fit_four_ctas_without_spills(tsit5):
     # 128 threads per CTA: at most 128 registers for 4 CTAs (16 warps) per SM
     regs, spill = find(tsit5, "record_kernel", "Tsit5Method", "Lorenz", "EdLb1ELb1ELb0E")
     assert regs <= 128 and spill == 0
-    # the stored-stage reverse sweep is capped at 6 CTAs per SM (80 registers; a small spill)
-    regs, spill = find(tsit5, "reverse_k1_kernel_mb", "Tsit5Method", "Lorenz", "EdLb0ELb1ELi6E")
-    assert regs <= 80 and spill <= 512
+    # the stored-stage reverse sweep is capped at 5 CTAs per SM (96 registers; a small spill)
+    regs, spill = find(tsit5, "reverse_k1_kernel_mb", "Tsit5Method", "Lorenz", "EdLb0ELb1ELi5E")
+    assert regs <= 96 and spill <= 512
     # the same record with FP64 step control (the library pow and division)
     regs, spill = find(tsit5, "record_kernel", "Tsit5Method", "Lorenz", "EdLb1ELb1ELb1E")
     assert regs <= 128 and spill == 0
