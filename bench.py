@@ -73,8 +73,8 @@ STIFF = {"robertson", "hires", "nrob"}
 # the same FP64 workload, stored-stage layout (Lorenz: 45.15 accepted steps per
 # trajectory; Robertson: 101243901 accepted steps in all); a launch's traffic grows
 # in proportion to its accepted steps. The Lorenz reverse sweep's writes are its
-# register spills (the kernel is capped at 80 registers).
-TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "stages"): (15341381632 + 635977216) / (45.15 * 2 ** 20),
+# register spills (the kernel is capped at 96 registers).
+TRAFFIC_PER_STEP = {("lorenz", "fp64", "reverse", "stages"): (14935465472 + 328079616) / (45.15 * 2 ** 20),
                     ("lorenz", "fp64", "record", "stages"): (291875328 + 9850115584) / (45.15 * 2 ** 20),
                     ("robertson", "fp64", "reverse", "stages"): (49664537600 + 67086336) / 101243901,
                     ("robertson", "fp64", "record", "stages"): (2908891648 + 67400810240) / 101243901}
