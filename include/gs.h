@@ -248,7 +248,11 @@ gs_status gs_forward_grad(const gs_record* rec, const double* params, const doub
  * Record then reverse in one call with the built-in loss (the hot path):
  * loss_out [n], params_bar [P][n], y0_bar [d][n], traj_status [n]. The record
  * lives in a library-owned workspace that is reused by later calls on the same
- * device. Synchronises `stream`.
+ * device. An FP32-mixed call of more than 2^21 trajectories (no shared
+ * weights, no step_counts, no timeout_ms) runs in chunks of 2^20 trajectories
+ * through device staging, with a record sized for one chunk; every result
+ * equals the one-piece call's bit for bit, kernel_ms sums the chunks' kernel
+ * times and record_info describes the last chunk. Synchronises `stream`.
  */
 gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const double* y0,
                         const float* shared_w, double t0, double t1, const double* save_t, int n_save,

@@ -123,6 +123,9 @@ struct gs_record {
   int stages = 0;
   double* side_stg = nullptr;
   size_t side_cap = 0;  // doubles
+  // chunk staging of a chunked FP32-mixed gs_solve_grad (inputs and outputs of one chunk)
+  double* chunk_buf = nullptr;
+  size_t chunk_cap = 0;  // doubles
   Counters* ctr = nullptr;
   Counters* ctr_host = nullptr;  // pinned
   int64_t n_cap = 0;             // capacity of the per-trajectory arrays
@@ -221,6 +224,7 @@ void destroy(gs_record* r) {
   cudaFree(r->fwd_base);
   cudaFree(r->fwd_seg);
   cudaFree(r->side_stg);
+  cudaFree(r->chunk_buf);
   cudaFree(r->ctr);
   cudaFree(r->wpart);
   cudaFreeHost(r->ctr_host);
@@ -640,6 +644,78 @@ gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* pa
   return r->ctr_host->any_failed ? GS_ERR_TRAJ_FAILED : GS_OK;
 }
 
+// An FP32-mixed gs_solve_grad of more than two chunks runs chunk by chunk
+// (shared-weight problems, step_counts and a wait deadline excepted): the
+// compact record of 2^20 Lorenz trajectories takes ~2.8 GB against ~44 GB at
+// 2^24, and the reverse sweep's scattered per-lane segment reads run faster
+// over the smaller arena (Lorenz 2^24, rtol 1e-6: 40.7 ms in chunks of 2^20
+// against 44.0 ms in one piece, measured; the FP64 form, bound by the FP64
+// pipe, is slower in chunks and never takes this path). Trajectories are
+// independent, so the results equal the one-piece call bit for bit.
+constexpr int64_t MIXED_CHUNK = int64_t(1) << 20;
+
+bool chunked_mixed(const Call& c, int64_t n) {
+  return c.precision == GS_FP32_MIXED && c.pi.n_shared == 0 && !c.step_counts && !(c.timeout_ms > 0.0) &&
+         n > 2 * MIXED_CHUNK;
+}
+
+gs_status solve_grad_chunked(gs_record* r, const Call& c, int64_t n, const double* params, const double* y0,
+                             double t0, double t1, const double* save_t, int n_save, double rtol, double atol,
+                             cudaStream_t s, double* loss_out, double* params_bar, double* y0_bar,
+                             int32_t* traj_status, bool allow_stages) {
+  const int P = c.pi.P, d = c.pi.d;
+  const int64_t ch = MIXED_CHUNK;
+  const size_t need = (size_t)(2 * (P + d)) * (size_t)ch;  // [P + d][ch] in, [P + d][ch] out
+  if (r->chunk_cap < need) {
+    cudaFree(r->chunk_buf);
+    r->chunk_buf = nullptr;
+    r->chunk_cap = 0;
+    if (cudaMalloc(&r->chunk_buf, need * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();  // no staging: the one-piece call
+      return solve_grad_in(r, c, n, params, y0, nullptr, t0, t1, save_t, n_save, rtol, atol, s, loss_out,
+                           params_bar, y0_bar, nullptr, traj_status, allow_stages);
+    }
+    r->chunk_cap = need;
+  }
+  double* in_p = r->chunk_buf;             // [P][ch]
+  double* in_y = in_p + (size_t)P * ch;    // [d][ch]
+  double* out_p = in_y + (size_t)d * ch;   // [P][ch]
+  double* out_y = out_p + (size_t)P * ch;  // [d][ch]
+  float kms[2] = {0.0f, 0.0f}, sum[2] = {0.0f, 0.0f};
+  Call cc = c;
+  if (c.kernel_ms) cc.kernel_ms = kms;
+  bool failed = false;
+  const size_t pitch = (size_t)n * sizeof(double);
+  for (int64_t k0 = 0; k0 < n; k0 += ch) {
+    const int64_t nc = std::min(ch, n - k0);
+    const size_t w = (size_t)nc * sizeof(double);
+    if (cudaMemcpy2DAsync(in_p, w, params + k0, pitch, w, P, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpy2DAsync(in_y, w, y0 + k0, pitch, w, d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return GS_ERR_CUDA;
+    const gs_status st = solve_grad_in(r, cc, nc, in_p, in_y, nullptr, t0, t1, save_t, n_save, rtol, atol, s,
+                                       loss_out ? loss_out + k0 : nullptr, params_bar ? out_p : nullptr,
+                                       y0_bar ? out_y : nullptr, nullptr, traj_status + k0, allow_stages);
+    if (st == GS_ERR_TRAJ_FAILED)
+      failed = true;
+    else if (st != GS_OK)
+      return st;
+    if (params_bar &&
+        cudaMemcpy2DAsync(params_bar + k0, pitch, out_p, w, w, P, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return GS_ERR_CUDA;
+    if (y0_bar && cudaMemcpy2DAsync(y0_bar + k0, pitch, out_y, w, w, d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return GS_ERR_CUDA;
+    sum[0] += kms[0];
+    sum[1] += kms[1];
+  }
+  const gs_status ws = wait_stream(s, 0.0);
+  if (ws != GS_OK) return ws;
+  if (c.kernel_ms) {
+    c.kernel_ms[0] = sum[0];
+    c.kernel_ms[1] = sum[1];
+  }
+  return failed ? GS_ERR_TRAJ_FAILED : GS_OK;
+}
+
 // gs_solve_grad's reusable record, one per device.
 std::mutex g_ws_mu;
 std::vector<gs_record*> g_ws;
@@ -869,6 +945,9 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
   std::lock_guard<std::mutex> lock(g_ws_mu);
   gs_record* r = workspace(dev);
   if (!r) return GS_ERR_OOM;
+  if (chunked_mixed(c, n))
+    return solve_grad_chunked(r, c, n, params, y0, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
+                              loss_out, params_bar, y0_bar, traj_status, true);
   return solve_grad_in(r, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
                        loss_out, params_bar, y0_bar, shared_w_bar, traj_status, true);
 }
@@ -1060,6 +1139,9 @@ gs_status gs_solve_grad_ctx(gs_context* ctx, int problem_id, int64_t n, const do
   cudaGetDevice(&dev);
   if (dev != ctx->device) return GS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(ctx->mu);
+  if (chunked_mixed(c, n))
+    return solve_grad_chunked(ctx->ws, c, n, params, y0, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
+                              loss_out, params_bar, y0_bar, traj_status, false);
   return solve_grad_in(ctx->ws, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol,
                        (cudaStream_t)stream, loss_out, params_bar, y0_bar, shared_w_bar, traj_status, false);
 }

@@ -128,3 +128,19 @@ def test_forward_only_solve_in_place_final_state(control):
     assert rc == N.GS_OK
     assert torch.equal(st, ref["status"])
     assert torch.equal(y, ref["y_final"])
+
+
+def test_chunked_fp32_mixed_solve_grad_equals_the_one_piece_call():
+    """An FP32-mixed gs_solve_grad above 2^21 trajectories runs in chunks of
+    2^20 (a smaller record); asking for step counts keeps it in one piece. The
+    two must agree bit for bit, ragged last chunk included."""
+    n = (1 << 21) + 12345
+    wl = W.make("lorenz", n)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    args = ("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"])
+    kms = np.zeros(2, np.float32)
+    a = api.solve_grad(*args, layout="soa", precision="fp32_mixed", kernel_ms=kms)
+    b = api.solve_grad(*args, layout="soa", precision="fp32_mixed", step_counts=True)
+    for key in ("loss", "params_bar", "y0_bar", "status"):
+        assert torch.equal(a[key], b[key]), key
+    assert kms[0] > 0 and kms[1] > 0
