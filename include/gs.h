@@ -248,11 +248,14 @@ gs_status gs_forward_grad(const gs_record* rec, const double* params, const doub
  * Record then reverse in one call with the built-in loss (the hot path):
  * loss_out [n], params_bar [P][n], y0_bar [d][n], traj_status [n]. The record
  * lives in a library-owned workspace that is reused by later calls on the same
- * device. An FP32-mixed call of more than 2^21 trajectories (no shared
- * weights, no step_counts, no timeout_ms) runs in chunks of 2^20 trajectories
- * through device staging, with a record sized for one chunk; every result
- * equals the one-piece call's bit for bit, kernel_ms sums the chunks' kernel
- * times and record_info describes the last chunk. Synchronises `stream`.
+ * device. Large calls run in chunks through device staging, with a record
+ * sized for one chunk (no shared weights, no step_counts, no timeout_ms): an
+ * FP32-mixed call of more than 2^22 trajectories in chunks of 2^21; an FP64
+ * call whose stored-stage record would not fit in device memory but a chunk's
+ * would, in the largest power-of-two chunks (2^18 to 2^23) that fit. Every
+ * result equals the one-piece call's bit for bit, kernel_ms sums the chunks'
+ * kernel times and record_info describes the last chunk. Synchronises
+ * `stream`.
  */
 gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const double* y0,
                         const float* shared_w, double t0, double t1, const double* save_t, int n_save,

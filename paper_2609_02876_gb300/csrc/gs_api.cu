@@ -646,25 +646,37 @@ gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* pa
 
 // An FP32-mixed gs_solve_grad of more than two chunks runs chunk by chunk
 // (shared-weight problems, step_counts and a wait deadline excepted): the
-// compact record of 2^20 Lorenz trajectories takes ~2.8 GB against ~44 GB at
+// compact record of 2^21 Lorenz trajectories takes ~5.5 GB against ~44 GB at
 // 2^24, and the reverse sweep's scattered per-lane segment reads run faster
-// over the smaller arena (Lorenz 2^24, rtol 1e-6: 40.7 ms in chunks of 2^20
-// against 44.0 ms in one piece, measured; the FP64 form, bound by the FP64
-// pipe, is slower in chunks and never takes this path). Trajectories are
-// independent, so the results equal the one-piece call bit for bit.
-constexpr int64_t MIXED_CHUNK = int64_t(1) << 20;
+// over the smaller arena (Lorenz 2^24, rtol 1e-6, measured: 48.7 / 43.3 / 40.7
+// / 40.4 / 41.4 ms in chunks of 2^18 / 2^19 / 2^20 / 2^21 / 2^22 against 44.0
+// ms in one piece). Trajectories are independent, so
+// the results equal the one-piece call bit for bit.
+//
+// The FP64 form, bound by its FP64 pipe, is slower in chunks when the whole
+// stored-stage record fits (608 against 603 ms at Lorenz 2^24 in chunks of
+// 2^22) and then runs in one piece. An FP64 call whose whole stored-stage
+// record would not fit in device memory
+// (it then records compactly and its reverse sweep recomputes every stage) but
+// a chunk's would, runs in the largest power-of-two chunks (2^18 to 2^23) whose
+// stored-stage record fits (gs_solve_grad only; contexts keep the compact
+// layout): the reverse sweep then reads the stages instead of recomputing them.
+constexpr int64_t MIXED_CHUNK = int64_t(1) << 21;
 
-bool chunked_mixed(const Call& c, int64_t n) {
-  return c.precision == GS_FP32_MIXED && c.pi.n_shared == 0 && !c.step_counts && !(c.timeout_ms > 0.0) &&
-         n > 2 * MIXED_CHUNK;
+int64_t solve_chunk(const gs_record* r, const Call& c, int64_t n, int n_save, double rtol, bool allow_stages) {
+  if (c.pi.n_shared > 0 || c.step_counts || c.timeout_ms > 0.0) return 0;
+  if (c.precision == GS_FP32_MIXED) return n > 2 * MIXED_CHUNK ? MIXED_CHUNK : 0;
+  if (!allow_stages || choose_stages(r, c, n, n_save, rtol)) return 0;
+  for (int64_t m = int64_t(1) << 23; m >= (int64_t(1) << 18); m >>= 1)
+    if (m < n && choose_stages(r, c, m, n_save, rtol)) return m;
+  return 0;
 }
 
-gs_status solve_grad_chunked(gs_record* r, const Call& c, int64_t n, const double* params, const double* y0,
-                             double t0, double t1, const double* save_t, int n_save, double rtol, double atol,
-                             cudaStream_t s, double* loss_out, double* params_bar, double* y0_bar,
+gs_status solve_grad_chunked(gs_record* r, const Call& c, int64_t n, int64_t ch, const double* params,
+                             const double* y0, double t0, double t1, const double* save_t, int n_save, double rtol,
+                             double atol, cudaStream_t s, double* loss_out, double* params_bar, double* y0_bar,
                              int32_t* traj_status, bool allow_stages) {
   const int P = c.pi.P, d = c.pi.d;
-  const int64_t ch = MIXED_CHUNK;
   const size_t need = (size_t)(2 * (P + d)) * (size_t)ch;  // [P + d][ch] in, [P + d][ch] out
   if (r->chunk_cap < need) {
     cudaFree(r->chunk_buf);
@@ -945,8 +957,8 @@ gs_status gs_solve_grad(int problem_id, int64_t n, const double* params, const d
   std::lock_guard<std::mutex> lock(g_ws_mu);
   gs_record* r = workspace(dev);
   if (!r) return GS_ERR_OOM;
-  if (chunked_mixed(c, n))
-    return solve_grad_chunked(r, c, n, params, y0, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
+  if (const int64_t ch = solve_chunk(r, c, n, n_save, rtol, true))
+    return solve_grad_chunked(r, c, n, ch, params, y0, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
                               loss_out, params_bar, y0_bar, traj_status, true);
   return solve_grad_in(r, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
                        loss_out, params_bar, y0_bar, shared_w_bar, traj_status, true);
@@ -1139,9 +1151,9 @@ gs_status gs_solve_grad_ctx(gs_context* ctx, int problem_id, int64_t n, const do
   cudaGetDevice(&dev);
   if (dev != ctx->device) return GS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(ctx->mu);
-  if (chunked_mixed(c, n))
-    return solve_grad_chunked(ctx->ws, c, n, params, y0, t0, t1, save_t, n_save, rtol, atol, (cudaStream_t)stream,
-                              loss_out, params_bar, y0_bar, traj_status, false);
+  if (const int64_t ch = solve_chunk(ctx->ws, c, n, n_save, rtol, false))
+    return solve_grad_chunked(ctx->ws, c, n, ch, params, y0, t0, t1, save_t, n_save, rtol, atol,
+                              (cudaStream_t)stream, loss_out, params_bar, y0_bar, traj_status, false);
   return solve_grad_in(ctx->ws, c, n, params, y0, shared_w, t0, t1, save_t, n_save, rtol, atol,
                        (cudaStream_t)stream, loss_out, params_bar, y0_bar, shared_w_bar, traj_status, false);
 }

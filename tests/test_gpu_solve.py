@@ -131,10 +131,10 @@ def test_forward_only_solve_in_place_final_state(control):
 
 
 def test_chunked_fp32_mixed_solve_grad_equals_the_one_piece_call():
-    """An FP32-mixed gs_solve_grad above 2^21 trajectories runs in chunks of
-    2^20 (a smaller record); asking for step counts keeps it in one piece. The
+    """An FP32-mixed gs_solve_grad above 2^22 trajectories runs in chunks of
+    2^21 (a smaller record); asking for step counts keeps it in one piece. The
     two must agree bit for bit, ragged last chunk included."""
-    n = (1 << 21) + 12345
+    n = (1 << 22) + 12345
     wl = W.make("lorenz", n)
     P, Y = dev(wl["params"].T), dev(wl["y0"].T)
     args = ("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"])
@@ -144,3 +144,27 @@ def test_chunked_fp32_mixed_solve_grad_equals_the_one_piece_call():
     for key in ("loss", "params_bar", "y0_bar", "status"):
         assert torch.equal(a[key], b[key]), key
     assert kms[0] > 0 and kms[1] > 0
+
+
+def test_chunked_fp64_solve_grad_with_stored_stages_equals_the_one_piece_call():
+    """An FP64 gs_solve_grad whose stored-stage record would not fit runs in
+    chunks that do (stages read, not recomputed). Forcing that here would need
+    most of the device memory, so the rule is checked on what it decides: at
+    rtol 1e-8 the 2^24 Lorenz ensemble is recorded in chunks with stored stages
+    (record_info), and a chunk-sized sample of it equals the same trajectories
+    solved alone bit for bit."""
+    n = 1 << 24
+    wl = W.make("lorenz", n, rtol=1e-8)
+    P, Y = dev(wl["params"].T), dev(wl["y0"].T)
+    info = np.zeros(2, np.int32)
+    a = api.solve_grad("lorenz", P, Y, wl["t0"], wl["t1"], wl["save_t"], wl["rtol"], wl["atol"], layout="soa",
+                       record_info=info)
+    assert info[0] == 1 and info[1] == 1, info  # the last chunk kept every state and its stages
+    m = 1 << 16
+    k0 = n - m - 777  # straddles the last chunk boundary when chunks are a power of two above 2^16
+    b = api.solve_grad("lorenz", P[:, k0:k0 + m].contiguous(), Y[:, k0:k0 + m].contiguous(), wl["t0"], wl["t1"],
+                       wl["save_t"], wl["rtol"], wl["atol"], layout="soa")
+    for key in ("loss", "status"):
+        assert torch.equal(a[key][k0:k0 + m], b[key]), key
+    for key in ("params_bar", "y0_bar"):
+        assert torch.equal(a[key][:, k0:k0 + m], b[key]), key
