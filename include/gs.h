@@ -340,10 +340,11 @@ gs_status gs_solve_grad_noalloc(int problem_id, int64_t n, const double* params,
 /*
  * Solve contexts for concurrent callers (the request server). A context owns
  * its own reusable record workspace on the device that was current when it was
- * created; gs_solve_grad_ctx is gs_solve_grad on that workspace, so calls on
- * different contexts and streams proceed concurrently (calls on one context
- * are serialised by the context). gs_context_bytes reports the device bytes
- * the workspace holds (it grows to the largest ensemble seen).
+ * created; gs_solve_grad_ctx is gs_solve_grad on that workspace, except that it
+ * always records compactly (no stored stages), so calls on different contexts
+ * and streams proceed concurrently (calls on one context are serialised by the
+ * context). gs_context_bytes reports the device bytes the workspace holds (it
+ * grows to the largest ensemble seen).
  */
 typedef struct gs_context gs_context;
 gs_status gs_context_create(gs_context** ctx);

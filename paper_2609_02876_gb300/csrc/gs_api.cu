@@ -659,8 +659,8 @@ gs_status solve_grad_in(gs_record* r, const Call& c, int64_t n, const double* pa
 // record would not fit in device memory
 // (it then records compactly and its reverse sweep recomputes every stage) but
 // a chunk's would, runs in the largest power-of-two chunks (2^18 to 2^23) whose
-// stored-stage record fits (gs_solve_grad only; contexts keep the compact
-// layout): the reverse sweep then reads the stages instead of recomputing them.
+// stored-stage record fits (gs_solve_grad only; contexts record compactly):
+// the reverse sweep then reads the stages instead of recomputing them.
 constexpr int64_t MIXED_CHUNK = int64_t(1) << 21;
 
 int64_t solve_chunk(const gs_record* r, const Call& c, int64_t n, int n_save, double rtol, bool allow_stages) {
@@ -1151,6 +1151,10 @@ gs_status gs_solve_grad_ctx(gs_context* ctx, int problem_id, int64_t n, const do
   cudaGetDevice(&dev);
   if (dev != ctx->device) return GS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(ctx->mu);
+  // contexts record compactly: with stored stages the request server's
+  // latencies measured worse (0.8 load, 1000 requests: p50 60 / p99 1015 ms
+  // against 43 / 865 ms), the stage records of concurrent small launches
+  // costing more than their faster reverse sweeps save
   if (const int64_t ch = solve_chunk(ctx->ws, c, n, n_save, rtol, false))
     return solve_grad_chunked(ctx->ws, c, n, ch, params, y0, t0, t1, save_t, n_save, rtol, atol,
                               (cudaStream_t)stream, loss_out, params_bar, y0_bar, traj_status, false);
