@@ -36,3 +36,19 @@ def test_reference_arm_runs_on_rank_zero_only():
     out = run(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-sample", "64"],
               {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert out == ""
+
+
+def test_kernel_count_per_step_follows_the_launch_rules():
+    """gpu_launches counts the kernels one gs_solve_grad call launches: the
+    starting-step pass, the record, the t1-save pass (FP64, no shared weights,
+    k = 1, last save at t1), the reverse sweep, and the weight reduction of
+    shared-weight problems."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2609_02876_gb300 import workloads as W
+    lor = W.make("lorenz", 4)
+    assert bench.launches_per_step("lorenz", "fp64", 1, lor) == 4
+    assert bench.launches_per_step("lorenz", "fp32_mixed", 1, lor) == 3
+    assert bench.launches_per_step("lorenz", "fp64", 11, lor) == 3  # k > 1: no t1-save pass
+    assert bench.launches_per_step("lorenz", "fp64", 1, dict(lor, save_t=lor["save_t"][:-1])) == 3
+    assert bench.launches_per_step("lv_ude", "fp32_mixed", 1, W.make("lv_ude", 4)) == 4
